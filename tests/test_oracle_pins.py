@@ -1,0 +1,541 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+None of these tests retypes an oracle formula and compares with it.  Each
+checks a closed form, an invariant, a special case or a geometric property,
+chosen so that a dropped term, a wrong sign, a wrong weight or a wrong index
+in the oracle fails at least one of them:
+
+* lattice tables: isotropy identities of the weights; D2Q9 order fixed by
+  the moment matrix M of Sec. 2 (tests/golden/d2q9_mrt_matrix.txt);
+* equilibrium (Sec. 2, Eq. feq): its first three moments in closed form;
+* collision: mass conserved, momentum raised by exactly g (Guo forcing),
+  non-equilibrium relaxed by (1 - 1/tau) (BGK) or (1 - s_k) (MRT);
+* streaming + collision: shear-wave decay rate nu k^2, nu = (tau - 1/2)/3;
+  exact mass and momentum budgets in periodic boxes;
+* link rules (Sec. 3): exactness of the VIBB reconstruction and of Bouzidi's
+  interpolation for fields that are linear along the link (departure point
+  x_d = 2q - 1 in link units); Bouzidi at q = 1/2 equals half-way bit for
+  bit; VIBB at q = 1/2 does not (the paper says so in Sec. 3.1); rest and
+  sliding-wall uniform flows are exact fixed points of every rule;
+* whole runs: Poiseuille (Sec. 4.1, Eq. exact) bulk curvature -g/nu, half-way
+  exact at tau = 1/2 + sqrt(3)/4, second-order convergence of Bouzidi and
+  VIBB with walls at off-node q, the moving-wall case of Sec. 4.1; circular
+  Couette (Sec. 4.2, Eq. exact2) convergence; momentum-exchange force equal
+  to the momentum budget at every step; zero lift on a mirror-symmetric body.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1903_01111_gb300 import geometry as G
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _golden_mrt():
+    rows, s = [], None
+    mode = None
+    with open(os.path.join(HERE, "golden", "d2q9_mrt_matrix.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            if line in ("M", "S"):
+                mode = line
+                continue
+            if mode == "M":
+                rows.append([float(v) for v in line.split()])
+            else:
+                s = line.split()
+    return np.array(rows), s
+
+
+# ------------------------------------------------------------------ tables --
+
+@pytest.mark.parametrize("stencil", [0, 1])
+def test_weights_isotropy(stencil):
+    e, w = O.velocity_set(stencil)
+    e = e.astype(float)
+    d = np.eye(3)[:2 + stencil, :2 + stencil]
+    ee = e[:, :2 + stencil]
+    assert abs(w.sum() - 1) < 1e-15
+    assert np.abs(w @ ee).max() < 1e-15
+    np.testing.assert_allclose(np.einsum("i,ia,ib->ab", w, ee, ee), d / 3, atol=1e-15)
+    assert np.abs(np.einsum("i,ia,ib,ic->abc", w, ee, ee, ee)).max() < 1e-15
+    four = np.einsum("i,ia,ib,ic,id->abcd", w, ee, ee, ee, ee)
+    iso = (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d) + np.einsum("ad,bc->abcd", d, d)) / 9
+    np.testing.assert_allclose(four, iso, atol=1e-15)
+    # every direction has its opposite
+    for i in range(len(e)):
+        assert sum(np.all(e[j] == -e[i]) for j in range(len(e))) == 1
+
+
+def test_d2q9_order_matches_moment_matrix():
+    M, _ = _golden_mrt()
+    e, _ = O.velocity_set(0)
+    np.testing.assert_array_equal(M[0], np.ones(9))
+    np.testing.assert_array_equal(M[3], e[:, 0])  # j_x row
+    np.testing.assert_array_equal(M[5], e[:, 1])  # j_y row
+    G_ = M @ M.T
+    assert np.abs(G_ - np.diag(np.diag(G_))).max() == 0  # rows orthogonal
+
+
+# ------------------------------------------------------------- equilibrium --
+
+@pytest.mark.parametrize("stencil", [0, 1])
+def test_equilibrium_moments(stencil):
+    rng = np.random.default_rng(1)
+    e, _ = O.velocity_set(stencil)
+    D = 2 + stencil
+    for _ in range(20):
+        rho = rng.uniform(0.8, 1.2)
+        u = np.zeros(3)
+        u[:D] = rng.uniform(-0.1, 0.1, D)
+        f = O.feq(stencil, rho, u)
+        assert abs(f.sum() - rho) < 1e-14
+        np.testing.assert_allclose(f @ e, rho * u, atol=1e-15)
+        P = np.einsum("i,ia,ib->ab", f, e, e)[:D, :D]
+        np.testing.assert_allclose(P, rho * (np.outer(u[:D], u[:D]) + np.eye(D) / 3), atol=1e-15)
+
+
+# --------------------------------------------------------------- collision --
+
+@pytest.mark.parametrize("stencil,collision", [(0, 0), (1, 0), (0, 1)])
+def test_collision_budget(stencil, collision):
+    rng = np.random.default_rng(2)
+    e, w = O.velocity_set(stencil)
+    g = np.array([1.3e-4, -0.7e-4, 0.4e-4 if stencil else 0.0])
+    cfg = O.make_config(stencil=stencil, collision=collision, tau=0.73, g=g)
+    for _ in range(10):
+        f = w * rng.uniform(0.9, 1.1, len(w))
+        fp, rho, u = O.collide(cfg, f)
+        assert abs(fp.sum() - f.sum()) < 1e-15
+        np.testing.assert_allclose(fp @ e, f @ e + g, atol=1e-16)  # momentum + g per step
+        np.testing.assert_allclose(u, (f @ e + g / 2) / f.sum(), rtol=1e-13, atol=1e-17)
+
+
+@pytest.mark.parametrize("stencil", [0, 1])
+def test_bgk_relaxation_factor(stencil):
+    """A mass- and momentum-free perturbation of feq decays by (1 - 1/tau)."""
+    rng = np.random.default_rng(3)
+    e, w = O.velocity_set(stencil)
+    tau = 0.61
+    cfg = O.make_config(stencil=stencil, tau=tau)
+    u = np.array([0.03, -0.02, 0.01 if stencil else 0.0])
+    fe = O.feq(stencil, 1.02, u)
+    d = rng.normal(size=len(w)) * 1e-3
+    A = np.vstack([np.ones(len(w)), e.T.astype(float)])  # remove mass/momentum
+    d -= A.T @ np.linalg.lstsq(A.T, d, rcond=None)[0]
+    fp, _, _ = O.collide(cfg, fe + d)
+    np.testing.assert_allclose(fp - fe, (1 - 1 / tau) * d, atol=1e-16)
+
+
+def test_mrt_relaxation_rates():
+    """MRT (Eq. mrt): moment k of a perturbation of feq relaxes by (1 - s_k),
+    with M and s_k as printed (golden fixture)."""
+    M, s_txt = _golden_mrt()
+    tau = 0.8
+    nu = (tau - 0.5) / 3
+    s = np.array([1 / (3 * nu + 0.5) if v == "nu" else float(v) for v in s_txt])
+    cfg = O.make_config(stencil=0, collision=1, tau=tau)
+    fe = O.feq(0, 1.0, [0.0, 0.0])
+    Minv = np.linalg.inv(M)
+    for k in (1, 2, 4, 6, 7, 8):  # non-conserved moments
+        d = Minv[:, k] * 1e-4
+        fp, _, _ = O.collide(cfg, fe + d)
+        dm = M @ (fp - fe)
+        expect = np.zeros(9)
+        expect[k] = (1 - s[k]) * 1e-4
+        np.testing.assert_allclose(dm, expect, atol=2e-15)
+
+
+# ---------------------------------------------------------- link rules ----
+
+def _dirs(stencil):
+    e, w = O.velocity_set(stencil)
+    return e.astype(float), w
+
+
+@pytest.mark.parametrize("stencil", [0, 1])
+@pytest.mark.parametrize("q", [0.05, 0.25, 0.5, 0.5 + 1e-12, 0.63, 0.9, 1.0])
+def test_vibb_exact_for_linear_fields(stencil, q):
+    """With rho, u and the non-equilibrium part linear along the link, and the
+    wall velocity the linear field's value at the wall, VIBB returns feq and
+    fneq of the departure point x_d = x_f + (2q - 1) e_i' (Sec. 3.1, Fig. 1)
+    plus the moving-wall term."""
+    e, w = _dirs(stencil)
+    cfg = O.make_config(stencil=stencil, tau=0.8, rho0=1.0)
+    rng = np.random.default_rng(int(q * 1000) + stencil)
+    Q = len(w)
+    opp = [int(np.flatnonzero((e == -e[i]).all(1))[0]) for i in range(Q)]
+    for ip in range(1, Q):
+        i = opp[ip]
+        u0, du = rng.uniform(-0.05, 0.05, 3), rng.uniform(-0.02, 0.02, 3)
+        if stencil == 0:
+            u0[2] = du[2] = 0.0
+        # position along the link in units of |e|: f at 0, ff at -1, wall at q
+        ufield = lambda s: u0 + du * s
+        uw = ufield(q)
+        wall = 6 * w[ip] * 1.0 * float(e[i] @ uw)
+        # (a) density and velocity linear, no non-equilibrium part
+        r0, dr = 1.0 + rng.uniform(-0.01, 0.01), rng.uniform(-0.01, 0.01)
+        rfield = lambda s: r0 + dr * s
+        fpf = O.feq(stencil, rfield(0), ufield(0))
+        fpff = O.feq(stencil, rfield(-1), ufield(-1))
+        got = O.link_value(cfg, 2, ip, q, uw, fpf, fpff, rfield(0), ufield(0), rfield(-1), ufield(-1))
+        expect = O.feq(stencil, rfield(2 * q - 1), ufield(2 * q - 1))[ip] + wall
+        assert abs(got - expect) < 5e-15, (ip, got, expect)
+        # (b) uniform density, non-equilibrium part linear along the link
+        nf, nff = rng.normal(size=Q) * 1e-3, rng.normal(size=Q) * 1e-3
+        fpf = O.feq(stencil, 1.0, ufield(0)) + nf
+        fpff = O.feq(stencil, 1.0, ufield(-1)) + nff
+        got = O.link_value(cfg, 2, ip, q, uw, fpf, fpff, 1.0, ufield(0), 1.0, ufield(-1))
+        n_at_d = nf[ip] + (nf[ip] - nff[ip]) * (2 * q - 1)
+        expect = O.feq(stencil, 1.0, ufield(2 * q - 1))[ip] + n_at_d + wall
+        assert abs(got - expect) < 5e-15
+        # (c) non-equilibrium proportional to density: the density-ratio
+        #     rescaling keeps fneq/rho linear
+        af, aff = rng.normal() * 1e-3, rng.normal() * 1e-3
+        fpf = O.feq(stencil, rfield(0), ufield(0))
+        fpff = O.feq(stencil, rfield(-1), ufield(-1))
+        fpf[ip] += af * rfield(0)
+        fpff[ip] += aff * rfield(-1)
+        got = O.link_value(cfg, 2, ip, q, uw, fpf, fpff, rfield(0), ufield(0), rfield(-1), ufield(-1))
+        rd = rfield(2 * q - 1)
+        expect = (O.feq(stencil, rd, ufield(2 * q - 1))[ip] + rd * (af + (af - aff) * (2 * q - 1)) + wall)
+        assert abs(got - expect) < 5e-15
+
+
+@pytest.mark.parametrize("q", [0.1, 0.3, 0.5, 0.6, 0.8, 1.0])
+def test_bouzidi_linear_interpolation_geometry(q):
+    """Bouzidi (Eqs. q_less, q_larger) is linear interpolation along the
+    link: for q <= 1/2 of f+_i' between x_ff (-1) and x_f (0) at x_d = 2q - 1;
+    for q > 1/2 of the population travelling back in direction i, known at
+    the bounce-back point 2q - 1 (f+_i'(x_f) + wall term) and at x_ff, where
+    it is f+_i(x_f, t), evaluated at x_f."""
+    e, w = _dirs(0)
+    cfg = O.make_config(stencil=0)
+    rng = np.random.default_rng(7)
+    ip, i = 2, 4  # towards +y, back along -y
+    uw = np.array([0.02, 0.0, 0.0])
+    wall = 6 * w[ip] * float(e[i] @ uw)
+    A, B = rng.uniform(0.05, 0.2), rng.uniform(-0.05, 0.05)
+    phi = lambda s: A + B * s
+    fpf = rng.uniform(0.05, 0.2, 9)
+    fpff = rng.uniform(0.05, 0.2, 9)
+    if q <= 0.5:
+        fpf[ip], fpff[ip] = phi(0), phi(-1)
+        expect = phi(2 * q - 1) + wall
+    else:
+        fpf[ip] = phi(2 * q - 1) - wall
+        fpf[i] = phi(-1)
+        expect = phi(0)
+    got = O.link_value(cfg, 1, ip, q, uw, fpf, fpff, 1.0, [0, 0], 1.0, [0, 0])
+    assert abs(got - expect) < 5e-16
+
+
+# ------------------------------------------------------------------ runs ---
+
+def _cfg_for(geo, **kw):
+    g = geo
+    return O.make_config(stencil=g.stencil, nx=g.nx, ny=g.ny, nz=g.nz, periodic=g.periodic,
+                         inlet=g.open_x[0], outlet=g.open_x[1], **kw)
+
+
+def _small_cylinder(bc=-1, stencil=0):
+    if stencil == 0:
+        bodies = [G.ball((12.3, 9.6, 0), 4.2, force_id=0, bc=bc)]
+        return G.build(0, (28, 20, 1), (1, 1, 1), bodies)
+    bodies = [G.ball((7.3, 6.6, 5.2), 3.1, force_id=0, bc=bc)]
+    return G.build(1, (14, 12, 10), (1, 1, 1), bodies)
+
+
+@pytest.mark.parametrize("stencil", [0, 1])
+@pytest.mark.parametrize("bc", [0, 1, 2])
+def test_rest_state_is_fixed_point(stencil, bc):
+    g = _small_cylinder(stencil=stencil)
+    cfg = _cfg_for(g, tau=0.7, bc=bc)
+    st = O.init(cfg, g.solid)
+    O.run(cfg, g.solid, g.links, st, 30)
+    _, w = O.velocity_set(stencil)
+    fl = g.solid == 0
+    assert np.abs(st.fp[:, fl] - w[:, None]).max() < 1e-15
+
+
+@pytest.mark.parametrize("stencil", [0, 1])
+@pytest.mark.parametrize("bc", [0, 1, 2])
+def test_sliding_walls_keep_uniform_flow(stencil, bc):
+    """Walls at generic q moving tangentially at U carry a uniform flow U
+    unchanged (Galilean fixed point): pins the sign and size of the wall
+    term and that the u*, u** weights sum to one in both q branches."""
+    U = (0.04, 0.0, 0.0) if stencil == 0 else (0.04, 0.0, -0.03)
+    g = G.channel(stencil, 6, 7, nz=1 if stencil == 0 else 4, q_lo=0.23, q_hi=0.71, u_lo=U, u_hi=U)
+    cfg = _cfg_for(g, tau=0.66, bc=bc)
+    u0 = np.tile(np.array(U), (g.N, 1))
+    st = O.init(cfg, g.solid, u=u0)
+    O.run(cfg, g.solid, g.links, st, 40)
+    fe = O.feq(stencil, 1.0, U)
+    fl = g.solid == 0
+    assert np.abs(st.fp[:, fl] - fe[:, None]).max() < 1e-13
+
+
+def _poiseuille(bc, q_lo, q_hi, H, tau, g0=1e-6, steps=None, u_top=0.0, bc_lo=-1):
+    g = G.channel(0, 2, H, q_lo=q_lo, q_hi=q_hi, u_hi=(u_top, 0, 0), bc_lo=bc_lo)
+    cfg = _cfg_for(g, tau=tau, g=(g0, 0, 0), bc=bc)
+    st = O.init(cfg, g.solid)
+    nu = (tau - 0.5) / 3
+    Hw = g.info["y_hi"] - g.info["y_lo"]
+    if steps is None:
+        steps = int(32 * Hw * Hw / (nu * np.pi ** 2))
+    F = O.run(cfg, g.solid, g.links, st, steps)
+    y = np.arange(1, H + 1)
+    ux = st.u.reshape(g.ny, g.nx, 3)[1:H + 1, 0, 0]
+    ex = G.poiseuille_profile(y, g.info["y_lo"], g.info["y_hi"], g0, nu, u_top)
+    return ux, ex, F, g
+
+
+def test_poiseuille_bulk_curvature_and_force_balance():
+    ux, ex, F, g = _poiseuille(2, 0.3, 0.3, 24, 0.8)
+    nu = 0.1
+    d2 = ux[2:] - 2 * ux[1:-1] + ux[:-2]
+    np.testing.assert_allclose(d2[2:-2], -1e-6 / nu, rtol=1e-7)
+    # steady state: wall force equals the body force on the fluid
+    assert abs(F[0, 0] - g.fluid_count() * 1e-6) < 1e-9 * g.fluid_count() * 1e-6
+
+
+def test_poiseuille_halfway_exact_at_magic_tau():
+    """Half-way bounce-back puts the wall exactly half a link out for BGK
+    when (tau - 1/2)^2 = 3/16."""
+    ux, ex, _, _ = _poiseuille(0, 0.5, 0.5, 12, 0.5 + np.sqrt(3) / 4)
+    assert np.abs(ux - ex).max() / ex.max() < 1e-9
+
+
+@pytest.mark.parametrize("bc", [1, 2])
+@pytest.mark.parametrize("q", [0.3, 0.7])
+def test_poiseuille_second_order(bc, q):
+    errs = []
+    for H in (8, 16, 32):
+        ux, ex, _, _ = _poiseuille(bc, q, q, H, 0.8)
+        errs.append(np.sqrt(((ux - ex) ** 2).sum() / (ex ** 2).sum()))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert orders.min() > 1.8, (errs, orders)
+    assert errs[-1] < 2.5e-3
+
+
+def test_poiseuille_moving_wall_paper_case():
+    """Sec. 4.1: bottom wall fixed with half-way bounce-back, top wall moving
+    at u_top at distance q = 0.8 above the top row.  Without body force the
+    flow is linear shear, which every rule reproduces exactly; with the body
+    force the error against Eq. (exact), measured against the amplitude
+    g H^2 / (8 nu) of the force-driven part, falls at second order (the
+    half-way wall's slip is an absolute, viscosity-dependent constant)."""
+    for bc in (0, 1, 2):
+        q = 0.5 if bc == 0 else 0.8
+        ux, ex, _, _ = _poiseuille(bc, 0.5, q, 10, 0.8, g0=0.0, u_top=0.01, bc_lo=0)
+        assert np.abs(ux - ex).max() < 1e-11 * 0.01
+    nu = 0.1
+    errs = []
+    for H in (10, 20, 40):
+        ux, ex, _, g = _poiseuille(2, 0.5, 0.8, H, 0.8, g0=1e-6, u_top=0.01, bc_lo=0)
+        Hw = g.info["y_hi"] - g.info["y_lo"]
+        errs.append(np.abs(ux - ex).max() / (1e-6 * Hw * Hw / (8 * nu)))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert orders.min() > 1.8, (errs, orders)
+
+
+def test_vibb_at_half_differs_from_halfway():
+    """Sec. 3.1: VIBB does not reduce to bounce-back at q = 1/2."""
+    a, _, _, _ = _poiseuille(2, 0.5, 0.5, 10, 0.8, steps=400)
+    b, _, _, _ = _poiseuille(0, 0.5, 0.5, 10, 0.8, steps=400)
+    assert np.abs(a - b).max() > 1e-3 * np.abs(b).max()
+
+
+def test_bouzidi_at_half_is_halfway_bitwise():
+    g = _small_cylinder()
+    links = g.links.copy()
+    links["q"] = 0.5
+    fields = []
+    for bc in (0, 1):
+        cfg = _cfg_for(g, tau=0.7, bc=bc, g=(1e-4, 3e-5, 0))
+        st = O.init(cfg, g.solid)
+        O.run(cfg, g.solid, links, st, 60)
+        fields.append(st.fp.copy())
+    assert np.array_equal(fields[0], fields[1])
+
+
+@pytest.mark.parametrize("stencil", [0, 1])
+def test_periodic_mass_and_momentum_budget(stencil):
+    if stencil == 0:
+        shape = (16, 12, 1)
+    else:
+        shape = (8, 6, 5)
+    N = int(np.prod(shape))
+    rng = np.random.default_rng(11)
+    solid = np.zeros(N, np.uint8)
+    gvec = np.array([2e-5, -1e-5, 3e-5 if stencil else 0.0])
+    cfg = O.make_config(stencil=stencil, nx=shape[0], ny=shape[1], nz=shape[2], tau=0.9, g=gvec)
+    u0 = rng.uniform(-0.03, 0.03, (N, 3))
+    if stencil == 0:
+        u0[:, 2] = 0
+    st = O.init(cfg, solid, rho=rng.uniform(0.98, 1.02, N), u=u0)
+    m0 = st.rho.sum()
+    P0 = (st.rho[:, None] * st.u).sum(0)
+    for k in range(1, 6):
+        O.run(cfg, solid, np.zeros(0, O.LINK_DTYPE), st, 1)
+        assert abs(st.rho.sum() - m0) < 1e-12
+        P = (st.rho[:, None] * st.u).sum(0)
+        np.testing.assert_allclose(P - P0, k * N * gvec, atol=1e-13)
+
+
+@pytest.mark.parametrize("stencil,collision", [(0, 0), (1, 0), (0, 1)])
+def test_shear_wave_decay_rate(stencil, collision):
+    """u_x = U sin(k y) decays as exp(-nu k^2 t), nu = (tau - 1/2)/3 (BGK)
+    and nu = (1/s_7 - 1/2)/3 (MRT)."""
+    L = 48
+    shape = (2, L, 1) if stencil == 0 else (2, L, 2)
+    N = int(np.prod(shape))
+    tau = 0.8
+    cfg = O.make_config(stencil=stencil, collision=collision, nx=shape[0], ny=shape[1], nz=shape[2], tau=tau)
+    k = 2 * np.pi / L
+    y = (np.arange(N) // shape[0]) % L
+    u0 = np.zeros((N, 3))
+    u0[:, 0] = 1e-4 * np.sin(k * y)
+    solid = np.zeros(N, np.uint8)
+    st = O.init(cfg, solid, u=u0)
+    O.run(cfg, solid, np.zeros(0, O.LINK_DTYPE), st, 50)  # let the initial layer decay
+    a0 = (st.u[:, 0] * np.sin(k * y)).sum()
+    T = 200
+    O.run(cfg, solid, np.zeros(0, O.LINK_DTYPE), st, T)
+    a1 = (st.u[:, 0] * np.sin(k * y)).sum()
+    rate = -np.log(a1 / a0) / T
+    nu = (tau - 0.5) / 3
+    # the lattice dispersion correction is O(k^2) ~ 1e-2 relative here
+    assert abs(rate / (nu * k * k) - 1) < 1e-2
+
+
+def test_force_equals_momentum_budget_every_step():
+    """Momentum exchange (Ladd) is the momentum the link rule removes from the
+    fluid: J(t+1) - J(t) = N_f g - F(t) at every step, for every rule."""
+    for bc in (0, 1, 2):
+        g = _small_cylinder(bc=-1)
+        gvec = np.array([3e-5, 1e-5, 0.0])
+        cfg = _cfg_for(g, tau=0.75, bc=bc, g=gvec)
+        st = O.init(cfg, g.solid)
+        O.run(cfg, g.solid, g.links, st, 20)
+        fl = g.solid == 0
+        nf = fl.sum()
+        for _ in range(5):
+            P0 = (st.rho[fl, None] * st.u[fl]).sum(0)
+            F = O.run(cfg, g.solid, g.links, st, 1)[0]
+            P1 = (st.rho[fl, None] * st.u[fl]).sum(0)
+            np.testing.assert_allclose(P1 - P0, nf * gvec - F, atol=1e-15)
+
+
+def test_halfway_conserves_mass_exactly():
+    g = _small_cylinder()
+    cfg = _cfg_for(g, tau=0.75, bc=0, g=(3e-5, 1e-5, 0))
+    st = O.init(cfg, g.solid)
+    m0 = st.rho.sum()
+    O.run(cfg, g.solid, g.links, st, 50)
+    assert abs(st.rho.sum() - m0) < 1e-11  # roundoff only (506 nodes x 50 steps)
+    # the interpolated rules exchange mass with the wall by construction
+    for bc in (1, 2):
+        cfg = _cfg_for(g, tau=0.75, bc=bc, g=(3e-5, 1e-5, 0))
+        st = O.init(cfg, g.solid)
+        O.run(cfg, g.solid, g.links, st, 50)
+        assert abs(st.rho.sum() - m0) > 1e-9
+
+
+@pytest.mark.parametrize("bc", [0, 1, 2])
+def test_mirror_symmetric_body_has_no_lift(bc):
+    # circle centred on the mid-plane of a channel with half-way walls
+    ny_f = 15
+    cy = (1 + ny_f) / 2.0  # mid-plane between rows 1 and ny_f
+    g0 = G.channel(0, 30, ny_f, q_lo=0.5, q_hi=0.5)
+    bodies = list(g0.bodies) + [G.ball((11.37, cy, 0), 3.7, force_id=1)]
+    bodies[0]["bc"] = bodies[1]["bc"] = 0
+    g = G.build(0, (30, ny_f + 2, 1), (1, 0, 1), bodies)
+    cfg = _cfg_for(g, tau=0.7, bc=bc, g=(1e-5, 0, 0))
+    st = O.init(cfg, g.solid)
+    F = O.run(cfg, g.solid, g.links, st, 200, nbody=2)
+    assert abs(F[1, 1]) < 1e-12 * abs(F[1, 0])
+    assert F[1, 0] > 0
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("bc", [1, 2])
+def test_couette_convergence(bc):
+    """Sec. 4.2, Eq. (exact2): the azimuthal velocity converges to the
+    analytic profile; over L = 20 -> 80 at fixed tau the mean order is at
+    least 1.8 (the paper reports second order, slightly better for VIBB)."""
+    errs = []
+    tau = 0.8
+    nu = (tau - 0.5) / 3
+    for L in (20, 40, 80):
+        r1 = L / 4.8
+        om = 0.01 / r1
+        g = G.couette(L, om)
+        cfg = _cfg_for(g, tau=tau, bc=bc)
+        st = O.init(cfg, g.solid)
+        steps = int(22 * (g.info["r2"] - r1) ** 2 / (nu * np.pi ** 2))
+        O.run(cfg, g.solid, g.links, st, steps)
+        fl = np.flatnonzero(g.solid == 0)
+        x, y, _ = g.coords(fl)
+        dx, dy = x - g.info["center"][0], y - g.info["center"][1]
+        r = np.hypot(dx, dy)
+        ut = (-dy * st.u[fl, 0] + dx * st.u[fl, 1]) / r
+        ex = G.couette_profile(r, r1, g.info["r2"], om)
+        errs.append(np.sqrt(((ut - ex) ** 2).sum() / (ex ** 2).sum()))
+    assert np.log2(errs[0] / errs[2]) / 2 > 1.8, errs
+    assert errs[2] < 2e-3
+
+
+def test_open_boundaries_keep_uniform_plug_flow():
+    """Sec. 4.3 inlet (non-equilibrium extrapolation of a prescribed
+    velocity) and zero-gradient outlet (copy of the closest fluid column):
+    a uniform stream through a channel periodic in y is an exact fixed point.
+    The inflow parabola is made flat by putting its walls far away."""
+    nx, ny = 24, 6
+    U = 0.03
+    g = G.build(0, (nx, ny, 1), (False, True, True), [], open_x=(True, True))
+    cfg = _cfg_for(g, tau=0.7, bc=0, inlet_umax=U, inlet_y0=-1e7, inlet_y1=1e7)
+    u0 = np.zeros((g.N, 3))
+    u0[:, 0] = U
+    st = O.init(cfg, g.solid, u=u0)
+    O.run(cfg, g.solid, g.links, st, 300)
+    inner = np.zeros((ny, nx), bool)
+    inner[:, 1:nx - 1] = True
+    inner = inner.reshape(-1)
+    assert np.abs(st.u[inner, 0] - U).max() < 1e-12
+    assert np.abs(st.rho[inner] - 1.0).max() < 1e-12
+
+
+def test_open_boundaries_keep_developed_poiseuille():
+    """Fully developed body-force Poiseuille flow between half-way walls at
+    tau = 1/2 + sqrt(3)/4 is exact in every column, so the inlet fed with the
+    same parabola and the zero-gradient outlet must keep it: the steady state
+    of the open channel equals Eq. (exact) at every node."""
+    ny_f, nx = 10, 24
+    tau = 0.5 + np.sqrt(3) / 4
+    nu = (tau - 0.5) / 3
+    umax = 0.005
+    g0 = 8 * nu * umax / ny_f ** 2
+    g = G.channel(0, nx, ny_f, q_lo=0.5, q_hi=0.5, bc_lo=0, bc_hi=0, open_x=(True, True))
+    cfg = _cfg_for(g, tau=tau, bc=0, g=(g0, 0, 0), inlet_umax=umax, inlet_y0=0.5, inlet_y1=ny_f + 0.5)
+    y = (np.arange(g.N) // nx) % g.ny
+    prof = G.poiseuille_profile(y, 0.5, ny_f + 0.5, g0, nu)
+    u0 = np.zeros((g.N, 3))
+    u0[:, 0] = prof
+    st = O.init(cfg, g.solid, u=u0)
+    O.run(cfg, g.solid, g.links, st, int(40 * ny_f ** 2 / (nu * np.pi ** 2)))
+    fl = (g.solid == 0).reshape(g.ny, nx).copy()
+    fl[:, 0] = fl[:, -1] = False
+    fl = fl.reshape(-1)
+    # The state is a fixed point, but a weakly unstable one: nothing fixes the
+    # mass level (the inlet fixes u, the force-driven bulk velocity scales as
+    # 1/rho), so the start-up transient leaves a slowly drifting residue of a
+    # few 1e-6; a wrong inlet or outlet formula gives errors of order 1e-2.
+    assert np.abs(st.u[fl, 0] - prof[fl]).max() < 2e-5 * umax
+    assert np.abs(st.u[fl, 1]).max() < 2e-5 * umax
