@@ -1,0 +1,214 @@
+/* lbm.h -- C ABI of liblbm.so: the lattice-Boltzmann time step with the
+ * velocity-interpolation bounce-back (VIBB) boundary of Jin et al.,
+ * "Velocity interpolation based Bounce-Back scheme for non-slip boundary
+ * condition in Lattice Boltzmann Method", arXiv:1903.01111, on NVIDIA GB300
+ * (sm_103a).  Half-way and Bouzidi bounce-back are provided as the paper's
+ * comparison rules.
+ *
+ * Conventions (all entry points):
+ *  - Every call returns an lbm_status; no C++ exception or abort crosses the
+ *    ABI.  On failure lbm_last_error() gives a message (thread-local).
+ *  - Node index n = x + nx*(y + ny*z); node x sits at integer coordinates.
+ *  - Velocity sets: D2Q9 in the order of the moment matrix M of Sec. 2:
+ *    e0=(0,0) e1=(1,0) e2=(0,1) e3=(-1,0) e4=(0,-1) e5=(1,1) e6=(-1,1)
+ *    e7=(-1,-1) e8=(1,-1); weights 4/9, 1/9, 1/36.  D3Q19 (not in the
+ *    paper): e0=0, e1..e6 = +x,-x,+y,-y,+z,-z, e7..e18 = (1,1,0),(-1,-1,0),
+ *    (1,-1,0),(-1,1,0),(1,0,1),(-1,0,-1),(1,0,-1),(-1,0,1),(0,1,1),
+ *    (0,-1,-1),(0,1,-1),(0,-1,1); weights 1/3, 1/18, 1/36.
+ *  - Population arrays exchanged with the caller are FP64, laid out [Q][N],
+ *    and hold the post-collision populations f+_i(x, t) (the state between
+ *    two steps).  Inside, the library stores FP64 or FP32 "shifted"
+ *    populations f_i - w_i rho0 (LBM_FP32_SHIFTED).
+ *  - Host pointers are read or written before the call returns unless said
+ *    otherwise; the library never keeps caller pointers.  Device memory for
+ *    the state is owned by the library.
+ *  - Work is ordered on the lattice's CUDA stream (lbm_config.cuda_stream,
+ *    or a stream the library creates).  Calls that return data to the host
+ *    synchronise that stream.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_INVALID_ARG = 1,  /* a bad argument; nothing was changed */
+  LBM_ERR_STATE = 2,        /* call not valid in the handle's state */
+  LBM_ERR_CUDA = 3,         /* a CUDA runtime error (message has the detail) */
+  LBM_ERR_OOM = 4,          /* device or host allocation failed */
+  LBM_ERR_DIVERGED = 5,     /* non-finite population or non-positive density */
+  LBM_ERR_TIMEOUT = 6,      /* reserved for bounded device waits */
+  LBM_ERR_UNSUPPORTED = 7   /* valid request this build does not implement */
+} lbm_status;
+
+enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 };
+enum { LBM_BGK = 0, LBM_MRT = 1 };
+enum { LBM_BC_DEFAULT = -1, LBM_BC_HALFWAY = 0, LBM_BC_BOUZIDI = 1, LBM_BC_VIBB = 2 };
+enum { LBM_FP64 = 0, LBM_FP32_SHIFTED = 1 };
+
+#define LBM_MAX_BODIES 64
+
+typedef struct lbm_lattice_s* lbm_handle;
+
+/* Run configuration.
+ *  stencil    LBM_D2Q9 (nz must be 1) or LBM_D3Q19.
+ *  collision  LBM_BGK: f+ = f - (f - feq)/tau + F_i, feq of Sec. 2
+ *             Eq. (feq) with C = 1, tau = 3 nu + 1/2 (Sec. 2).  The body
+ *             force g enters by Guo forcing (velocity u = (sum f e + g/2)/rho,
+ *             source (1 - 1/(2 tau)) w_i [3 (e_i - u) + 9 (e_i.u) e_i].g);
+ *             the paper names a constant body force (Sec. 4.1) but no scheme.
+ *             LBM_MRT (Sec. 2, Eq. mrt) is not built yet: LBM_ERR_UNSUPPORTED.
+ *  bc         default link rule for links whose own rule is LBM_BC_DEFAULT.
+ *  nx,ny,nz   lattice size; N = nx*ny*nz nodes.
+ *  periodic   per axis, 1 = periodic.  On a non-periodic axis every node of
+ *             the two end faces must be solid (or an open column, below).
+ *  inlet      D2Q9 only: column x = 0 (its non-solid nodes) is a velocity
+ *             inlet by non-equilibrium extrapolation (Sec. 4.3):
+ *             f+(0,y) = feq(rho(1,y), u_in(y)) + f+(1,y) - feq(rho(1,y), u(1,y)),
+ *             u_in(y) = 4 inlet_umax (y - inlet_y0)(inlet_y1 - y)/(inlet_y1 - inlet_y0)^2.
+ *  outlet     D2Q9 only: column x = nx-1 copies every population of column
+ *             x = nx-2 (zero gradient, Sec. 4.3).
+ *  tau, rho0  relaxation time (> 1/2) and reference density (the rho0 of
+ *             the moving-wall term 6 w rho0 (e_i.u_w), Eqs. q_less/q_larger).
+ *  g          body force per unit volume.
+ *  precision  LBM_FP64 or LBM_FP32_SHIFTED.
+ *  cuda_stream a cudaStream_t to order all work on, or NULL for a stream the
+ *             library creates and destroys. */
+typedef struct {
+  int32_t stencil;
+  int32_t collision;
+  int32_t bc;
+  int32_t nx, ny, nz;
+  int32_t periodic[3];
+  int32_t inlet, outlet;
+  double tau, rho0;
+  double g[3];
+  double inlet_umax, inlet_y0, inlet_y1;
+  int32_t precision;
+  int32_t reserved;
+  void* cuda_stream;
+} lbm_config;
+
+/* One cut link (Sec. 3, Fig. 1): fluid node x_f = node whose neighbour
+ * x_s = x_f + e_dir is solid.  dir is i' (pointing from the fluid into the
+ * wall); the rule rebuilds f_i(x_f, t+1) with i = opp(i').
+ *  q     |x_f - x_w| / |x_f - x_s| in (0, 1] (Sec. 3).
+ *  uw    wall velocity at x_w (only the first D entries are used).
+ *  bc    LBM_BC_* for this link or LBM_BC_DEFAULT.
+ *  body  force accumulator 0..LBM_MAX_BODIES-1 that this link's momentum
+ *        exchange adds to, or -1. */
+typedef struct {
+  int64_t node;
+  int32_t dir;
+  int16_t bc;
+  int16_t body;
+  double q;
+  double uw[3];
+} lbm_link;
+
+/* Counters of a lattice (lbm_query). */
+typedef struct {
+  int64_t n_nodes, n_fluid, n_links, n_cached, step;
+  int64_t device_bytes;  /* device memory the lattice holds */
+  int32_t Q, D, precision, real_bytes;
+} lbm_info;
+
+/* Create a lattice: validates cfg, allocates the device state (two
+ * population buffers, the moment cache, the node mask, two force slots).
+ * *out receives the handle.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
+lbm_status lbm_create_lattice(const lbm_config* cfg, lbm_handle* out);
+
+/* Free a lattice and everything it owns (synchronises its stream). */
+lbm_status lbm_destroy(lbm_handle h);
+
+/* Node classification and cut links (Sec. 3: fluid, solid and boundary
+ * nodes; missing populations are those that would stream from solid
+ * nodes).  solid: N bytes on the host, nonzero = solid.  links: n_links
+ * records on the host.  Everything is copied and checked: node in range and
+ * fluid, dir in 1..Q-1, q in (0,1], x_s solid and inside the lattice on
+ * non-periodic axes, bc and body in range, no duplicate (node, dir), and
+ * every fluid node with a solid neighbour in direction i' has a link.  The
+ * second fluid node x_ff = x_f - e_i' of a link falls back to x_f when it is
+ * not a fluid node (narrow gaps).  Invalidates the state: call
+ * lbm_init_equilibrium or lbm_set_distributions next.
+ * Errors: INVALID_ARG (message names the first bad item), OOM, CUDA. */
+lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* links, int64_t n_links);
+
+/* Initial state: f(x,0) = feq(rho(x), u(x)) (Sec. 2, Eq. feq) at every fluid
+ * node, then the collision at t = 0, so that the state holds f+(x,0).
+ * rho: N doubles or NULL (rho0); u: N x 3 doubles (x,y,z interleaved) or
+ * NULL (rest).  Host pointers.  Resets the step counter to 0.
+ * Errors: STATE (no geometry), OOM, CUDA. */
+lbm_status lbm_init_equilibrium(lbm_handle h, const double* rho, const double* u);
+
+/* Advance n >= 0 time steps, asynchronously on the lattice's stream.  Each
+ * step: link rules at every cut link (half-way; Bouzidi Eqs. q_less and
+ * q_larger; VIBB Sec. 3.1), open columns (Sec. 4.3), pull streaming (Eq. 1)
+ * with moments and collision (Sec. 2).  Errors: STATE, CUDA. */
+lbm_status lbm_step(lbm_handle h, int64_t n);
+
+/* Macroscopic fields of the current state (Sec. 2 density and velocity
+ * sums): rho = sum_i f+_i, u = (sum_i f+_i e_i - g/2)/rho, which equals the
+ * velocity the last collision used.  rho: N doubles, u: D x N doubles
+ * ([component][node]); both host or both device pointers (detected); solid
+ * and open-column nodes get 0.  Host outputs synchronise the stream.
+ * Errors: STATE, INVALID_ARG, OOM, CUDA. */
+lbm_status lbm_moments(lbm_handle h, double* rho, double* u);
+
+/* Force on body `body` during the last step by momentum exchange,
+ * F = sum over its links of (f+_i'(x_f,t) + f_i(x_f,t+1)) e_i', summed in
+ * FP64 (the paper uses the lift force in Sec. 4.3 but does not say how it
+ * is computed; momentum exchange is the method of the moving-wall term it
+ * cites).  F: 3 doubles on the host (z = 0 in 2-D).  Synchronises.
+ * Errors: STATE, INVALID_ARG, CUDA. */
+lbm_status lbm_force(lbm_handle h, int32_t body, double F[3]);
+
+/* Copy the state out as FP64 post-collision populations f+_i(x,t), [Q][N]
+ * on the host (solid and open-column nodes get 0).  Synchronises.
+ * Errors: STATE, OOM, CUDA. */
+lbm_status lbm_get_distributions(lbm_handle h, double* f);
+
+/* Replace the state by caller populations f+_i(x,t), [Q][N] FP64 on the
+ * host; the moment cache is recomputed from them with the lbm_moments
+ * formulas.  Does not change the step counter.  Errors: STATE, OOM, CUDA. */
+lbm_status lbm_set_distributions(lbm_handle h, const double* f);
+
+/* Post-collision populations f+_i(x, t) of n listed nodes, FP64 unshifted,
+ * written to out[k*Q + i] (host).  nodes: n host indices in [0, N).  Solid
+ * and open-column nodes give 0.  Synchronises.  Used for probes and for
+ * sampled checks of large lattices.  Errors: STATE, INVALID_ARG, OOM, CUDA. */
+lbm_status lbm_gather(lbm_handle h, const int64_t* nodes, int64_t n, double* out);
+
+/* Failure detection: scan the state; LBM_ERR_DIVERGED if a fluid node has
+ * a non-finite population or rho <= 0 (BGK loses stability as tau -> 1/2,
+ * Sec. 2).  Synchronises.  Errors: STATE, DIVERGED, CUDA. */
+lbm_status lbm_check(lbm_handle h);
+
+/* Wait for all work queued on the lattice's stream.  Errors: CUDA. */
+lbm_status lbm_synchronize(lbm_handle h);
+
+/* Fill *info with counts and sizes.  Errors: INVALID_ARG. */
+lbm_status lbm_query(lbm_handle h, lbm_info* info);
+
+/* Kernel timing for measurement.  While on, lbm_step launches the kernels
+ * one by one (no CUDA graph) with a CUDA event pair around each launch on
+ * the lattice's stream.  lbm_kernel_times synchronises and returns, per
+ * kernel k (0 = links, 1 = open columns, 2 = bulk), the number of timed
+ * launches and their summed duration in milliseconds since profiling was
+ * switched on.  Errors: STATE, CUDA, OOM. */
+lbm_status lbm_set_profiling(lbm_handle h, int32_t on);
+lbm_status lbm_kernel_times(lbm_handle h, int64_t launches[3], double ms[3]);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

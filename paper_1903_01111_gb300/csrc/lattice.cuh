@@ -1,0 +1,71 @@
+// Lattice constants and the parameter block shared by the kernels and the
+// host side of liblbm.so.  Velocity sets:
+//   D2Q9  in the order of the moment matrix M (Sec. 2 of arXiv:1903.01111):
+//         e1=(1,0) e2=(0,1) e3=(-1,0) e4=(0,-1) e5=(1,1) e6=(-1,1) e7=(-1,-1)
+//         e8=(1,-1), weights 4/9, 1/9, 1/36;
+//   D3Q19 rest, +-x, +-y, +-z, (+-1,+-1,0), (+-1,0,+-1), (0,+-1,+-1) with
+//         opposite directions adjacent, weights 1/3, 1/18, 1/36.
+// Everything is constexpr so that unrolled loops fold the velocities.
+#pragma once
+#include <cstdint>
+
+namespace lbm {
+
+// mask bits of the device node mask
+enum : uint8_t { M_SOLID = 1, M_CACHE = 2, M_OPEN = 4 };
+
+// packed link key: node << 16 | body+1 << 9 | wrap << 8 | fffb << 7 | rule << 5 | dir
+constexpr int KEY_NODE_SHIFT = 16;
+__host__ __device__ inline uint64_t pack_key(int64_t node, int dir, int rule, int ff_fallback, int wrap, int body) {
+  return ((uint64_t)node << KEY_NODE_SHIFT) | ((uint64_t)(body + 1) << 9) | ((uint64_t)wrap << 8) |
+         ((uint64_t)ff_fallback << 7) | ((uint64_t)rule << 5) | (uint64_t)dir;
+}
+constexpr int MAX_BODIES = 64;
+
+struct D2Q9 {
+  static constexpr int Q = 9, D = 2;
+  __host__ __device__ static constexpr int cx(int i) {
+    return (i == 1 || i == 5 || i == 8) ? 1 : (i == 3 || i == 6 || i == 7) ? -1 : 0;
+  }
+  __host__ __device__ static constexpr int cy(int i) {
+    return (i == 2 || i == 5 || i == 6) ? 1 : (i == 4 || i == 7 || i == 8) ? -1 : 0;
+  }
+  __host__ __device__ static constexpr int cz(int) { return 0; }
+  __host__ __device__ static constexpr double w(int i) { return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0); }
+  __host__ __device__ static constexpr int opp(int i) { return i == 0 ? 0 : (i < 5 ? 1 + ((i + 1) & 3) : 5 + ((i - 3) & 3)); }
+};
+
+struct D3Q19 {
+  static constexpr int Q = 19, D = 3;
+  __host__ __device__ static constexpr int cx(int i) {
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+           : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1
+                                                                  : 0;
+  }
+  __host__ __device__ static constexpr int cy(int i) {
+    return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+           : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1
+                                                                 : 0;
+  }
+  __host__ __device__ static constexpr int cz(int i) {
+    return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+           : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1
+                                                                   : 0;
+  }
+  __host__ __device__ static constexpr double w(int i) { return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0); }
+  __host__ __device__ static constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+};
+
+// Run parameters handed to every kernel by value.
+struct Params {
+  int nx, ny, nz;
+  int64_t N;            // nx*ny*nz
+  double tau, rho0;
+  double g[3];
+  int has_force;        // g != 0
+  int collision;        // 0 BGK, 1 MRT
+  double inlet_umax, inlet_y0, inlet_y1;
+  int inlet, outlet;
+};
+
+}  // namespace lbm

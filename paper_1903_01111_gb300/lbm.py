@@ -1,0 +1,309 @@
+"""Python binding of liblbm.so (C ABI in include/lbm.h).
+
+Argument marshalling only: every step of the computation runs in the
+library's CUDA kernels.  The functions keep the C names; ``Lattice`` is a
+small owner object around a handle.  There is no fallback: if liblbm.so is
+missing or fails to load, importing this module raises.
+
+Arrays: host inputs are numpy arrays; ``lbm_moments`` also takes torch CUDA
+tensors (device pointers) or numpy arrays (host pointers).  PyTorch is used
+only for device memory and for the CUDA stream handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbm.so")
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built; run `python -m paper_1903_01111_gb300.build` (needs nvcc)")
+_lib = ctypes.CDLL(LIB_PATH)
+
+LBM_OK, LBM_ERR_INVALID_ARG, LBM_ERR_STATE, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_DIVERGED, LBM_ERR_TIMEOUT, \
+    LBM_ERR_UNSUPPORTED = range(8)
+LBM_D2Q9, LBM_D3Q19 = 0, 1
+LBM_BGK, LBM_MRT = 0, 1
+LBM_BC_DEFAULT, LBM_BC_HALFWAY, LBM_BC_BOUZIDI, LBM_BC_VIBB = -1, 0, 1, 2
+LBM_FP64, LBM_FP32_SHIFTED = 0, 1
+LBM_MAX_BODIES = 64
+STATUS_NAMES = {0: "LBM_OK", 1: "LBM_ERR_INVALID_ARG", 2: "LBM_ERR_STATE", 3: "LBM_ERR_CUDA", 4: "LBM_ERR_OOM",
+                5: "LBM_ERR_DIVERGED", 6: "LBM_ERR_TIMEOUT", 7: "LBM_ERR_UNSUPPORTED"}
+
+LINK_DTYPE = np.dtype(
+    [("node", "<i8"), ("dir", "<i4"), ("bc", "<i2"), ("body", "<i2"), ("q", "<f8"), ("uw", "<f8", (3,))],
+    align=True,
+)
+assert LINK_DTYPE.itemsize == 48
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class lbm_config(ctypes.Structure):
+    _fields_ = [
+        ("stencil", ctypes.c_int32),
+        ("collision", ctypes.c_int32),
+        ("bc", ctypes.c_int32),
+        ("nx", ctypes.c_int32),
+        ("ny", ctypes.c_int32),
+        ("nz", ctypes.c_int32),
+        ("periodic", ctypes.c_int32 * 3),
+        ("inlet", ctypes.c_int32),
+        ("outlet", ctypes.c_int32),
+        ("tau", ctypes.c_double),
+        ("rho0", ctypes.c_double),
+        ("g", ctypes.c_double * 3),
+        ("inlet_umax", ctypes.c_double),
+        ("inlet_y0", ctypes.c_double),
+        ("inlet_y1", ctypes.c_double),
+        ("precision", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
+class lbm_info(ctypes.Structure):
+    _fields_ = [
+        ("n_nodes", ctypes.c_int64),
+        ("n_fluid", ctypes.c_int64),
+        ("n_links", ctypes.c_int64),
+        ("n_cached", ctypes.c_int64),
+        ("step", ctypes.c_int64),
+        ("device_bytes", ctypes.c_int64),
+        ("Q", ctypes.c_int32),
+        ("D", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("real_bytes", ctypes.c_int32),
+    ]
+
+
+_H = ctypes.c_void_p
+_P = ctypes.POINTER
+_vp = ctypes.c_void_p
+_sig = {
+    "lbm_create_lattice": [_P(lbm_config), _P(_H)],
+    "lbm_destroy": [_H],
+    "lbm_set_geometry": [_H, _vp, _vp, ctypes.c_int64],
+    "lbm_init_equilibrium": [_H, _vp, _vp],
+    "lbm_step": [_H, ctypes.c_int64],
+    "lbm_moments": [_H, _vp, _vp],
+    "lbm_force": [_H, ctypes.c_int32, _P(ctypes.c_double)],
+    "lbm_get_distributions": [_H, _vp],
+    "lbm_set_distributions": [_H, _vp],
+    "lbm_gather": [_H, _vp, ctypes.c_int64, _vp],
+    "lbm_check": [_H],
+    "lbm_synchronize": [_H],
+    "lbm_query": [_H, _P(lbm_info)],
+    "lbm_set_profiling": [_H, ctypes.c_int32],
+    "lbm_kernel_times": [_H, _P(ctypes.c_int64), _P(ctypes.c_double)],
+}
+for _name, _args in _sig.items():
+    _fn = getattr(_lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = ctypes.c_int
+_lib.lbm_last_error.restype = ctypes.c_char_p
+_lib.lbm_last_error.argtypes = []
+
+EXPORTED = tuple(_sig) + ("lbm_last_error",)
+
+
+def lbm_last_error() -> str:
+    return _lib.lbm_last_error().decode(errors="replace")
+
+
+def _check(st):
+    if st != LBM_OK:
+        raise LBMError(st, lbm_last_error())
+
+
+def _ptr(a):
+    """Pointer of a numpy array (host) or a torch tensor (host or device)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def make_config(stencil=LBM_D2Q9, nx=1, ny=1, nz=1, periodic=(1, 1, 1), tau=0.8, rho0=1.0, g=(0.0, 0.0, 0.0),
+                bc=LBM_BC_VIBB, collision=LBM_BGK, inlet=0, outlet=0, inlet_umax=0.0, inlet_y0=0.0, inlet_y1=0.0,
+                precision=LBM_FP64, stream=None) -> lbm_config:
+    c = lbm_config()
+    c.stencil, c.collision, c.bc = stencil, collision, bc
+    c.nx, c.ny, c.nz = nx, ny, nz
+    for a in range(3):
+        c.periodic[a] = int(periodic[a])
+        c.g[a] = float(g[a]) if a < len(g) else 0.0
+    c.inlet, c.outlet = int(inlet), int(outlet)
+    c.tau, c.rho0 = float(tau), float(rho0)
+    c.inlet_umax, c.inlet_y0, c.inlet_y1 = float(inlet_umax), float(inlet_y0), float(inlet_y1)
+    c.precision = precision
+    c.cuda_stream = stream
+    return c
+
+
+def lbm_create_lattice(cfg: lbm_config) -> int:
+    h = _H()
+    _check(_lib.lbm_create_lattice(ctypes.byref(cfg), ctypes.byref(h)))
+    return h.value
+
+
+def lbm_destroy(h) -> None:
+    _check(_lib.lbm_destroy(h))
+
+
+def lbm_set_geometry(h, solid, links) -> None:
+    solid = np.ascontiguousarray(solid, np.uint8).reshape(-1)
+    links = np.ascontiguousarray(links, dtype=LINK_DTYPE)
+    _check(_lib.lbm_set_geometry(h, solid.ctypes.data, links.ctypes.data if links.size else None, links.size))
+
+
+def lbm_init_equilibrium(h, rho=None, u=None) -> None:
+    r = None if rho is None else np.ascontiguousarray(rho, np.float64).reshape(-1)
+    uu = None if u is None else np.ascontiguousarray(u, np.float64).reshape(-1, 3)
+    _check(_lib.lbm_init_equilibrium(h, None if r is None else r.ctypes.data, None if uu is None else uu.ctypes.data))
+
+
+def lbm_step(h, n: int) -> None:
+    _check(_lib.lbm_step(h, int(n)))
+
+
+def lbm_moments(h, rho, u) -> None:
+    """Write rho (N) and u (D x N) float64; numpy (host) or torch CUDA tensors."""
+    _check(_lib.lbm_moments(h, _ptr(rho), _ptr(u)))
+
+
+def lbm_force(h, body: int = 0) -> np.ndarray:
+    F = (ctypes.c_double * 3)()
+    _check(_lib.lbm_force(h, int(body), F))
+    return np.array(F[:])
+
+
+def lbm_query(h) -> lbm_info:
+    info = lbm_info()
+    _check(_lib.lbm_query(h, ctypes.byref(info)))
+    return info
+
+
+def lbm_get_distributions(h, out=None) -> np.ndarray:
+    info = lbm_query(h)
+    if out is None:
+        out = np.empty((info.Q, info.n_nodes), np.float64)
+    assert out.dtype == np.float64 and out.flags.c_contiguous and out.size == info.Q * info.n_nodes
+    _check(_lib.lbm_get_distributions(h, out.ctypes.data))
+    return out
+
+
+def lbm_set_distributions(h, f) -> None:
+    f = np.ascontiguousarray(f, np.float64)
+    info = lbm_query(h)
+    assert f.size == info.Q * info.n_nodes
+    _check(_lib.lbm_set_distributions(h, f.ctypes.data))
+
+
+def lbm_gather(h, nodes) -> np.ndarray:
+    """Post-collision populations (n, Q) of the listed nodes, FP64."""
+    nodes = np.ascontiguousarray(nodes, np.int64).reshape(-1)
+    info = lbm_query(h)
+    out = np.empty((nodes.size, info.Q), np.float64)
+    _check(_lib.lbm_gather(h, nodes.ctypes.data if nodes.size else None, nodes.size, out.ctypes.data))
+    return out
+
+
+def lbm_check(h) -> None:
+    _check(_lib.lbm_check(h))
+
+
+def lbm_synchronize(h) -> None:
+    _check(_lib.lbm_synchronize(h))
+
+
+def lbm_set_profiling(h, on: bool) -> None:
+    _check(_lib.lbm_set_profiling(h, 1 if on else 0))
+
+
+def lbm_kernel_times(h):
+    """(launches[3], ms[3]) for kernels 0 = links, 1 = open columns, 2 = bulk."""
+    n = (ctypes.c_int64 * 3)()
+    ms = (ctypes.c_double * 3)()
+    _check(_lib.lbm_kernel_times(h, n, ms))
+    return list(n), list(ms)
+
+
+KERNEL_NAMES = ("k_links", "k_open", "k_bulk")
+
+
+class Lattice:
+    """Owner of one lattice handle; mirrors the C entry points."""
+
+    def __init__(self, geometry=None, **cfg):
+        if geometry is not None:
+            cfg.setdefault("stencil", geometry.stencil)
+            cfg.setdefault("nx", geometry.nx)
+            cfg.setdefault("ny", geometry.ny)
+            cfg.setdefault("nz", geometry.nz)
+            cfg.setdefault("periodic", geometry.periodic)
+            cfg.setdefault("inlet", int(geometry.open_x[0]))
+            cfg.setdefault("outlet", int(geometry.open_x[1]))
+        self.cfg = make_config(**cfg)
+        self.h = lbm_create_lattice(self.cfg)
+        if geometry is not None:
+            self.set_geometry(geometry.solid, geometry.links)
+
+    def close(self):
+        if self.h:
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_geometry(self, solid, links):
+        lbm_set_geometry(self.h, solid, links)
+
+    def init_equilibrium(self, rho=None, u=None):
+        lbm_init_equilibrium(self.h, rho, u)
+
+    def step(self, n=1):
+        lbm_step(self.h, n)
+
+    def moments(self, rho=None, u=None):
+        info = self.info()
+        if rho is None:
+            rho = np.empty(info.n_nodes)
+            u = np.empty((info.D, info.n_nodes))
+        lbm_moments(self.h, rho, u)
+        return rho, u
+
+    def force(self, body=0):
+        return lbm_force(self.h, body)
+
+    def distributions(self):
+        return lbm_get_distributions(self.h)
+
+    def set_distributions(self, f):
+        lbm_set_distributions(self.h, f)
+
+    def check(self):
+        lbm_check(self.h)
+
+    def synchronize(self):
+        lbm_synchronize(self.h)
+
+    def info(self):
+        return lbm_query(self.h)

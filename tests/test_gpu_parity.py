@@ -1,0 +1,363 @@
+"""GPU path (liblbm.so through its C ABI) against the FP64 CPU oracle.
+
+Tolerances:
+* FP64 storage: max |f_gpu - f_oracle| <= 1e-11 over fluid nodes after 200
+  steps (the two sides differ only in summation order).
+* FP32 shifted storage: every stored value is h = f - w rho0, so a rounding
+  costs at most eps32 |h|; a step applies a few dozen roundings per value and
+  errors add at most linearly over steps, so the bound used is
+  tol = 4 * steps * eps32 * max|h| (max over the oracle's state), i.e. a few
+  ulps of the deviation part per step.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1903_01111_gb300 import geometry as G
+
+pytestmark = pytest.mark.gpu
+
+EPS32 = float(np.finfo(np.float32).eps)
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1903_01111_gb300 import lbm
+
+    return lbm
+
+
+def _cfg(geo, **kw):
+    base = dict(stencil=geo.stencil, nx=geo.nx, ny=geo.ny, nz=geo.nz, periodic=geo.periodic,
+                inlet=int(geo.open_x[0]), outlet=int(geo.open_x[1]))
+    base.update(kw)
+    return base
+
+
+def _run_both(L, geo, steps, precision, nbody=1, init_u=None, **kw):
+    cfg = _cfg(geo, **kw)
+    ocfg = O.make_config(**cfg)
+    st = O.init(ocfg, geo.solid, u=init_u)
+    F_ref = O.run(ocfg, geo.solid, geo.links, st, steps, nbody=nbody)
+    lat = L.Lattice(geo, precision=precision, **{k: v for k, v in kw.items()})
+    lat.init_equilibrium(u=init_u)
+    lat.step(steps)
+    f = lat.distributions()
+    F = np.array([lat.force(b) for b in range(nbody)]) if steps > 0 else None
+    rho, u = lat.moments()
+    lat.close()
+    return f, F, rho, u, st, F_ref
+
+
+def _fluid(geo):
+    m = (geo.solid == 0).reshape(geo.nz, geo.ny, geo.nx).copy()
+    if geo.open_x[0]:
+        m[:, :, 0] = False
+    if geo.open_x[1]:
+        m[:, :, -1] = False
+    return m.reshape(-1)
+
+
+def _tol(L, precision, steps, st, geo):
+    if precision == L.LBM_FP64:
+        return 1e-11
+    _, w = O.velocity_set(geo.stencil)
+    fl = _fluid(geo)
+    hmax = np.abs(st.fp[:, fl] - w[:, None]).max()
+    return 4 * steps * EPS32 * max(hmax, 1e-6)
+
+
+def _compare(L, geo, steps, precision, nbody=1, init_u=None, **kw):
+    f, F, rho, u, st, F_ref = _run_both(L, geo, steps, precision, nbody=nbody, init_u=init_u, **kw)
+    fl = _fluid(geo)
+    tol = _tol(L, precision, steps, st, geo)
+    err = np.abs(f[:, fl] - st.fp[:, fl]).max()
+    assert err <= tol, f"max |f - oracle| = {err:.3e} > {tol:.3e}"
+    assert np.all(f[:, ~fl] == 0.0)
+    # moments of the state: rho, u (D x N) against the oracle's
+    D = 2 + geo.stencil
+    urel = 1e-12 if precision == L.LBM_FP64 else 50 * tol
+    assert np.abs(rho[fl] - st.rho[fl]).max() <= urel
+    assert np.abs(u[:, fl] - st.u[fl, :D].T).max() <= urel
+    if F is not None and nbody:
+        scale = max(np.abs(F_ref).max(), 1e-12)
+        ftol = 1e-10 * scale + 1e-15 if precision == L.LBM_FP64 else 1e-4 * scale + len(geo.links) * tol
+        assert np.abs(F - F_ref).max() <= ftol, (F, F_ref)
+    return err, tol
+
+
+PRECISIONS = ["fp64", "fp32s"]
+
+
+def _p(L, name):
+    return L.LBM_FP64 if name == "fp64" else L.LBM_FP32_SHIFTED
+
+
+# ------------------------------------------------------------------ cases --
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+@pytest.mark.parametrize("bc", [0, 1, 2])
+def test_poiseuille_32x24(L, bc, prec):
+    """Plane Poiseuille flow, 32 x 24 fluid nodes, walls at q = 0.3 from the
+    first and last fluid rows, g = 1e-6, tau = 0.8, 200 steps."""
+    geo = G.channel(0, 32, 24, q_lo=0.3, q_hi=0.3)
+    _compare(L, geo, 200, _p(L, prec), tau=0.8, g=(1e-6, 0, 0), bc=bc)
+
+
+def test_poiseuille_32x24_5000_steps(L):
+    geo = G.channel(0, 32, 24, q_lo=0.3, q_hi=0.3)
+    f, F, rho, u, st, F_ref = _run_both(L, geo, 5000, L.LBM_FP64, tau=0.8, g=(1e-6, 0, 0), bc=2)
+    fl = _fluid(geo)
+    assert np.abs(f[:, fl] - st.fp[:, fl]).max() <= 1e-11
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+@pytest.mark.parametrize("bc", [0, 1, 2])
+def test_rotating_cylinder_ragged_lattice(L, bc, prec):
+    """Off-grid rotating cylinder (moving wall velocity per link) in a
+    periodic 45 x 33 lattice; the body force has two components."""
+    geo = G.build(0, (45, 33, 1), (1, 1, 1), [G.ball((20.37, 15.61, 0), 6.3, omega=(0, 0, 0.004), force_id=0)])
+    _compare(L, geo, 200, _p(L, prec), tau=0.7, g=(2e-5, 1e-5, 0), bc=bc)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+@pytest.mark.parametrize("bc", [0, 1, 2])
+def test_sphere_pack_32(L, bc, prec):
+    """D3Q19 body-force flow through a periodic overlapping sphere pack
+    (the 384^3 workload's recipe at 32^3 with smaller radii)."""
+    geo = G.sphere_pack(32, porosity=0.40, rmin=3.0, rmax=6.0, seed=7)
+    _compare(L, geo, 200, _p(L, prec), tau=0.7, g=(1e-5, 0, 0), bc=bc)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_d3q19_channel_moving_walls(L, prec):
+    U = (0.02, 0.0, -0.01)
+    geo = G.channel(1, 12, 10, nz=7, q_lo=0.27, q_hi=0.81, u_lo=(0, 0, 0), u_hi=U)
+    _compare(L, geo, 200, _p(L, prec), tau=0.9, g=(1e-5, 0, 2e-6), bc=2)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_open_channel_cylinder(L, prec):
+    """The channel-with-cylinder workload scaled down: half-way channel walls,
+    parabolic velocity inlet, zero-gradient outlet, VIBB cylinder."""
+    geo = G.cylinder_channel(nx=120, ny_fluid=30, center=(30.37, 15.61), radius=4.3)
+    y = (np.arange(geo.N) // geo.nx) % geo.ny
+    u0 = np.zeros((geo.N, 3))
+    u0[:, 0] = np.where(geo.solid == 0, 4 * 0.05 * (y - 0.5) * (30.5 - y) / 30 ** 2, 0.0)
+    _compare(L, geo, 200, _p(L, prec), nbody=1, init_u=u0, tau=0.6, bc=2, inlet_umax=0.05, inlet_y0=0.5,
+             inlet_y1=30.5)
+
+
+def test_narrow_gap_second_node_fallback(L):
+    """Two circles 0.6 apart: links whose x_ff is solid fall back to x_f."""
+    geo = G.build(0, (40, 30, 1), (1, 1, 1), [G.ball((12.2, 15.3, 0), 6.1), G.ball((25.0, 15.3, 0), 6.1)])
+    for bc in (1, 2):
+        _compare(L, geo, 100, L.LBM_FP64, tau=0.75, g=(1e-5, 2e-6, 0), bc=bc)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_no_links_periodic_box_spanning_tiles(L, prec):
+    """No solid at all; 300 x 7 lattice (two 256-thread row tiles with a
+    ragged tail) and random smooth initial velocity."""
+    geo = G.build(0, (300, 7, 1), (1, 1, 1), [])
+    rng = np.random.default_rng(3)
+    u0 = np.zeros((geo.N, 3))
+    u0[:, :2] = rng.uniform(-0.02, 0.02, (geo.N, 2))
+    _compare(L, geo, 50, _p(L, prec), nbody=0, init_u=u0, tau=0.55, g=(1e-5, 0, 0), bc=0)
+
+
+def test_step_chunks_and_profiling_are_bitwise_equal(L):
+    """lbm_step(n) (graph replay), n x lbm_step(1) and profiled launches
+    compute the same bits."""
+    geo = G.build(0, (45, 33, 1), (1, 1, 1), [G.ball((20.37, 15.61, 0), 6.3, omega=(0, 0, 0.004))])
+    outs = []
+    for mode in ("graph", "single", "profiled"):
+        lat = L.Lattice(geo, tau=0.7, g=(2e-5, 1e-5, 0), bc=2)
+        lat.init_equilibrium()
+        if mode == "graph":
+            lat.step(37)
+        elif mode == "single":
+            for _ in range(37):
+                lat.step(1)
+        else:
+            L.lbm_set_profiling(lat.h, True)
+            lat.step(37)
+            n, ms = L.lbm_kernel_times(lat.h)
+            assert n[0] == 37 and n[2] == 37 and n[1] == 0 and ms[2] > 0
+        outs.append((lat.distributions(), lat.force(0)))
+        lat.close()
+    for f, F in outs[1:]:
+        assert np.array_equal(f, outs[0][0])
+        # block partial sums meet in FP64 atomics, whose order may vary
+        np.testing.assert_allclose(F, outs[0][1], rtol=1e-13, atol=1e-18)
+
+
+def test_moments_device_pointers(L):
+    import torch
+
+    geo = G.channel(0, 32, 24, q_lo=0.3, q_hi=0.3)
+    lat = L.Lattice(geo, tau=0.8, g=(1e-6, 0, 0), bc=2, stream=torch.cuda.current_stream().cuda_stream)
+    lat.init_equilibrium()
+    lat.step(30)
+    rho_h, u_h = lat.moments()
+    rho_d = torch.empty(geo.N, dtype=torch.float64, device="cuda")
+    u_d = torch.empty((2, geo.N), dtype=torch.float64, device="cuda")
+    L.lbm_moments(lat.h, rho_d, u_d)
+    torch.cuda.synchronize()
+    assert np.array_equal(rho_d.cpu().numpy(), rho_h) and np.array_equal(u_d.cpu().numpy(), u_h)
+    lat.close()
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_set_distributions_then_step(L, prec):
+    """A random post-collision state set through the ABI evolves like the
+    oracle started from the same state (moments rebuilt from f+ on both
+    sides)."""
+    geo = G.build(0, (30, 22, 1), (1, 1, 1), [G.ball((14.2, 10.9, 0), 4.4)])
+    _, w = O.velocity_set(0)
+    rng = np.random.default_rng(5)
+    f0 = w[:, None] * (1 + 0.01 * rng.standard_normal((9, geo.N)))
+    f0[:, geo.solid == 1] = 0
+    cfg = _cfg(geo, tau=0.7, g=(1e-5, 0, 0), bc=2)
+    ocfg = O.make_config(**cfg)
+    rho, u = O.moments(ocfg, geo.solid, f0.copy())
+    st = O.State(f0.copy(), rho, u)
+    O.run(ocfg, geo.solid, geo.links, st, 60)
+    lat = L.Lattice(geo, precision=_p(L, prec), tau=0.7, g=(1e-5, 0, 0), bc=2)
+    lat.set_distributions(f0)
+    back = lat.distributions()
+    fl = geo.solid == 0
+    assert np.abs(back[:, fl] - f0[:, fl]).max() <= (0 if prec == "fp64" else 2 * EPS32)
+    lat.step(60)
+    f = lat.distributions()
+    tol = 1e-11 if prec == "fp64" else 4 * 60 * EPS32 * np.abs(f0[:, fl] - w[:, None]).max() * 4
+    assert np.abs(f[:, fl] - st.fp[:, fl]).max() <= tol
+    lat.close()
+
+
+def test_invalid_geometry_is_rejected(L):
+    geo = G.channel(0, 16, 8, q_lo=0.3, q_hi=0.3)
+    lat = L.Lattice(None, stencil=0, nx=geo.nx, ny=geo.ny, nz=1, periodic=geo.periodic, tau=0.8)
+    bad = []
+    missing = geo.links[1:]
+    bad.append(missing)
+    dup = np.concatenate([geo.links, geo.links[:1]])
+    bad.append(dup)
+    q0 = geo.links.copy()
+    q0["q"][3] = 0.0
+    bad.append(q0)
+    to_fluid = geo.links.copy()
+    to_fluid["dir"][0] = 1  # +x neighbour of a fluid node is fluid
+    bad.append(to_fluid)
+    for links in bad:
+        with pytest.raises(L.LBMError) as ex:
+            lat.set_geometry(geo.solid, links)
+        assert ex.value.status == L.LBM_ERR_INVALID_ARG
+    # fluid on a face of a non-periodic axis
+    solid = geo.solid.copy()
+    solid[:geo.nx] = 0
+    with pytest.raises(L.LBMError):
+        lat.set_geometry(solid, geo.links)
+    with pytest.raises(L.LBMError) as ex:
+        lat.step(1)
+    assert ex.value.status == L.LBM_ERR_STATE
+    lat.set_geometry(geo.solid, geo.links)  # the valid one still works
+    lat.close()
+
+
+def test_bad_configs_are_rejected(L):
+    for kw in (dict(tau=0.5), dict(stencil=0, nz=2), dict(collision=1), dict(stencil=1, inlet=1, periodic=(0, 1, 1)),
+               dict(precision=7)):
+        base = dict(stencil=0, nx=8, ny=8, nz=1, tau=0.8)
+        base.update(kw)
+        with pytest.raises(L.LBMError):
+            L.Lattice(None, **base)
+
+
+def test_divergence_is_reported(L):
+    """Failure detection without a GPU fault: an unstable run (tau close to
+    1/2, large velocity) produces non-finite values that lbm_check reports."""
+    geo = G.build(0, (32, 32, 1), (1, 1, 1), [])
+    u0 = np.zeros((geo.N, 3))
+    x = np.arange(geo.N) % 32
+    u0[:, 0] = 0.45 * np.sin(2 * np.pi * x / 32)
+    lat = L.Lattice(geo, tau=0.5000001, bc=0)
+    lat.init_equilibrium(u=u0)
+    lat.check()
+    lat.step(3000)
+    with pytest.raises(L.LBMError) as ex:
+        lat.check()
+    assert ex.value.status == L.LBM_ERR_DIVERGED
+    lat.close()
+
+
+def _oracle_one_node_step(geo, e, w, opp, links_at, fp_of, x, tau, g):
+    """f+(x, t+1) from gathered f+(., t): pull, link rules, collision."""
+    cfg = O.make_config(stencil=geo.stencil, tau=tau, g=g, bc=2)
+    Q = len(w)
+    f = np.empty(Q)
+    nx, ny, nz = geo.shape
+
+    def nb(n, d, s):
+        c = np.array([n % nx, (n // nx) % ny, n // (nx * ny)]) + s * e[d]
+        c %= np.array(geo.shape)
+        return int(c[0] + nx * (c[1] + ny * c[2]))
+
+    for i in range(Q):
+        f[i] = fp_of(nb(x, i, -1))
+    for lk in links_at.get(x, []):
+        ip = int(lk["dir"])
+        i = opp[ip]
+        ff = nb(x, i, 1)
+        if geo.solid[ff]:
+            ff = x
+        vf, vff = fp_of(x), fp_of(ff)
+        rf, rff = vf.sum(), vff.sum()
+        uf = (vf @ e - 0.5 * np.asarray(g)) / rf
+        uff = (vff @ e - 0.5 * np.asarray(g)) / rff
+        f[i] = O.link_value(cfg, 2, ip, lk["q"], lk["uw"], vf, vff, rf, uf, rff, uff)
+    fp, _, _ = O.collide(cfg, f)
+    return fp
+
+
+def test_full_size_sphere_pack_sampled_nodes(L):
+    """The 384^3 workload in the bench's launch configuration: after one step
+    from a non-uniform state, f+(t+1) at sampled fluid nodes equals the
+    oracle's pull + link rules + collision computed node by node from the
+    gathered f+(t)."""
+    geo = G.sphere_pack(384, seed=0)
+    e, w = O.velocity_set(1)
+    opp = [int(np.flatnonzero((e == -e[i]).all(1))[0]) for i in range(19)]
+    tau, g = 0.7, (1e-6, 0.0, 0.0)
+    lat = L.Lattice(geo, tau=tau, g=g, bc=2)
+    lat.init_equilibrium()
+    lat.step(3)  # non-uniform state near the walls
+    rng = np.random.default_rng(0)
+    fluid = np.flatnonzero(geo.solid == 0)
+    boundary = np.unique(geo.links["node"])
+    sample = np.concatenate([rng.choice(boundary, 150, replace=False), rng.choice(fluid, 50, replace=False)])
+    nx, ny, _ = geo.shape
+    need = set()
+    for x in sample:
+        c = np.array([x % nx, (x // nx) % ny, x // (nx * ny)])
+        for d1 in range(19):
+            for d2 in range(19):
+                cc = (c - e[d1] + e[d2]) % np.array(geo.shape)
+                need.add(int(cc[0] + nx * (cc[1] + ny * cc[2])))
+    need = np.array(sorted(need))
+    vals = L.lbm_gather(lat.h, need)
+    table = dict(zip(need.tolist(), vals))
+    sel = np.isin(geo.links["node"], sample)
+    links_at = {}
+    for lk in geo.links[sel]:
+        links_at.setdefault(int(lk["node"]), []).append(lk)
+    lat.step(1)
+    got = L.lbm_gather(lat.h, sample)
+    for k, x in enumerate(sample):
+        want = _oracle_one_node_step(geo, e, w, opp, links_at, lambda n: table[n], int(x), tau, g)
+        assert np.abs(got[k] - want).max() < 1e-13, (x, got[k] - want)
+    lat.close()
