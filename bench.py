@@ -1,0 +1,346 @@
+"""Throughput of the VIBB lattice-Boltzmann step on one GB300 (or N replicas).
+
+Workload (default): D3Q19 BGK body-force-driven flow through a periodic
+random packing of overlapping spheres, 384^3 lattice, radii U[6, 14], centres
+U[0, 384)^3 from seed 0, added until the node porosity is <= 0.40; tau = 0.7,
+g = 1e-6 along x, VIBB on every cut link (~3.1e7 links).  A step is one full
+time step: link rules + momentum-exchange force, pull streaming, moments,
+collision.  The state (8.6 GB FP32 / 17.2 GB FP64) is far larger than L2, so
+no L2 flush is needed between steps.
+
+Metric: MLUPS counted over fluid nodes, FP32 shifted storage (``value``) and
+FP64 (``fp64``), each with the HBM roofline fraction of its dominant kernel
+(the bulk pull/collide kernel): algorithmic bytes 2*Q*s + 1 per fluid node
+divided by the kernel's average CUDA-event duration inside the timed region.
+
+--impl reference times the FP64 CPU oracle (the reference implementation of
+this build) on a bounded sub-case of the same recipe.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % HBM roofline (FP32 vs FP64)"
+WORKLOAD = ("D3Q19 BGK body-force flow through a periodic random overlapping sphere pack: 384^3 lattice, "
+            "radii U[6,14], seed 0, porosity 0.40, tau 0.7, g 1e-6, VIBB links (rho_d = rho_f for q > 1/2)")
+Q3 = 19
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)"
+    except Exception:
+        return 6800.0, "fallback (6.8 TB/s, one earlier GB300 copy measurement)"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        rows = []
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), max=float(parts[2]), power=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], swp=parts[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        smx = max(r["max"] for r in rows)
+        load = [r for r in rows if r["power"] > 200.0] or rows
+        reasons = set()
+        for r in load:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("swp", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in load), "sm_max_mhz": smx,
+                "reasons": sorted(reasons), "samples": len(rows), "samples_under_load": len(load),
+                "power_w_max": max(r["power"] for r in rows)}
+
+
+def _dist():
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        import torch.distributed as dist
+
+        if not dist.is_initialized():
+            dist.init_process_group("nccl")
+        return dist
+    return None
+
+
+def _barrier(dist, torch):
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+def _max_over_ranks(dist, torch, v):
+    """Max of a per-rank timing over all ranks (each rank runs a replica)."""
+    if dist is None:
+        return v
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_mlups(world, units_per_rank, steps, max_ms):
+    """Whole-job throughput of `world` replicas: all units they processed
+    divided by the slowest rank's time."""
+    return world * units_per_rank * steps / (max_ms * 1e-3) / 1e6
+
+
+def geometry(n, seed=0):
+    from paper_1903_01111_gb300 import geometry as G
+
+    return G.sphere_pack(n, porosity=0.40, rmin=6.0, rmax=14.0, seed=seed)
+
+
+def run_precision(lbm, torch, geo, precision, steps, warmup, dist, peak):
+    s = 8 if precision == lbm.LBM_FP64 else 4
+    # a dedicated stream: torch's default stream has handle 0, which the
+    # library would replace by its own stream
+    stream = torch.cuda.Stream()
+    lat = lbm.Lattice(geo, precision=precision, tau=0.7, g=(1e-6, 0.0, 0.0), bc=lbm.LBM_BC_VIBB,
+                      stream=stream.cuda_stream, vibb_density=lbm.LBM_VIBB_RHO_LOCAL)
+    info = lat.info()
+    lat.init_equilibrium()
+    lat.step(warmup)
+    _barrier(dist, torch)
+    lbm.lbm_set_profiling(lat.h, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    _barrier(dist, torch)
+    e0.record(stream)
+    lat.step(steps)
+    e1.record(stream)
+    _barrier(dist, torch)
+    ms = e0.elapsed_time(e1)
+    n_launch, kms = lbm.lbm_kernel_times(lat.h)
+    lbm.lbm_set_profiling(lat.h, False)
+    lat.check()
+    F = lat.force(0)
+    lat.close()
+    ms = _max_over_ranks(dist, torch, ms)
+    nf, nl, N = info.n_fluid, info.n_links, info.n_nodes
+    world = dist.get_world_size() if dist is not None else 1
+    mlups = replica_mlups(world, nf, steps, ms)
+    bulk_ms = kms[2] / max(n_launch[2], 1)
+    link_ms = kms[0] / max(n_launch[0], 1)
+    bulk_bytes = nf * (2 * Q3 * s + 1)  # algorithmic bytes per bulk launch
+    # per link: packed key 8 B, q, f+_i'(x_f), f+_i'(x_ff), moments (1 + D) at x_f and x_ff, one write
+    link_bytes = nl * (8 + s + 2 * s + 2 * (1 + 3) * s + s)
+    bulk_gbs = bulk_bytes / (bulk_ms * 1e-3) / 1e9
+    link_gbs = link_bytes / (link_ms * 1e-3) / 1e9
+    return {
+        "mlups": mlups, "ms_per_step": ms / steps, "n_fluid": nf, "n_links": nl, "n_nodes": N,
+        "launches": int(sum(n_launch)), "force": F.tolist(),
+        "roofline": {"bound": "hbm", "achieved": bulk_gbs, "peak": peak, "unit": "GB/s", "frac": bulk_gbs / peak,
+                     "traffic": None, "kernel": "k_bulk", "bytes_per_launch": bulk_bytes,
+                     "avg_launch_ms": bulk_ms},
+        "kernels": {
+            "k_bulk": {"launches": n_launch[2], "avg_ms": bulk_ms, "share": kms[2] / max(sum(kms), 1e-30),
+                       "gbs": bulk_gbs, "bytes_per_launch": bulk_bytes},
+            "k_links": {"launches": n_launch[0], "avg_ms": link_ms, "share": kms[0] / max(sum(kms), 1e-30),
+                        "gbs": link_gbs, "bytes_per_launch": link_bytes},
+        },
+        "step_gbs": (bulk_bytes + link_bytes) / (ms / steps * 1e-3) / 1e9,
+    }
+
+
+def run_e2e(lbm, torch, geo, steps):
+    """Same workload through the C ABI with host buffers: geometry upload,
+    initialisation, per step lbm_step(1) + lbm_force to a host array, and the
+    final macroscopic fields copied to host memory."""
+    import ctypes
+
+    solid = np.ascontiguousarray(geo.solid, np.uint8)
+    links = np.ascontiguousarray(geo.links, dtype=lbm.LINK_DTYPE)
+    rho = np.empty(geo.N)
+    u = np.empty((3, geo.N))
+    F = (ctypes.c_double * 3)()
+    cfg = lbm.make_config(stencil=1, nx=geo.nx, ny=geo.ny, nz=geo.nz, periodic=geo.periodic, tau=0.7,
+                          g=(1e-6, 0, 0), bc=lbm.LBM_BC_VIBB, precision=lbm.LBM_FP32_SHIFTED,
+                          stream=None, vibb_density=lbm.LBM_VIBB_RHO_LOCAL)
+    h = lbm.lbm_create_lattice(cfg)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lbm.lbm_set_geometry(h, solid, links)
+    lbm.lbm_init_equilibrium(h)
+    for _ in range(steps):
+        lbm.lbm_step(h, 1)
+        lbm._check(lbm._lib.lbm_force(h, 0, F))
+    lbm.lbm_moments(h, rho, u)
+    t1 = time.perf_counter()
+    info = lbm.lbm_query(h)
+    lbm.lbm_destroy(h)
+    h2d = solid.nbytes + links.nbytes
+    d2h = 24 * steps + rho.nbytes + u.nbytes
+    return {"value": info.n_fluid * steps / (t1 - t0) / 1e6, "unit": "MLUPS",
+            "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps, "seconds": t1 - t0,
+            "gpu_launches": steps * 2 + 2}
+
+
+def run_oracle(n, steps):
+    """The FP64 CPU oracle on an n^3 sub-case of the same recipe."""
+    import oracle as O
+
+    geo = geometry(n)
+    cfg = O.make_config(stencil=1, nx=n, ny=n, nz=n, periodic=(1, 1, 1), tau=0.7, g=(1e-6, 0, 0), bc=2,
+                        vibb_density=1)
+    st = O.init(cfg, geo.solid)
+    O.run(cfg, geo.solid, geo.links, st, 1)
+    t0 = time.perf_counter()
+    O.run(cfg, geo.solid, geo.links, st, steps)
+    dt = time.perf_counter() - t0
+    nf = geo.fluid_count()
+    return {"value": nf * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{n}^3 sub-case of the same sphere-pack recipe ({nf} fluid nodes, {len(geo.links)} links), "
+                      f"{steps} steps, FP64 oracle, single thread, {dt:.1f} s"}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    # sample sized so that the whole --steps run stays within about a minute
+    n = int(round((20e6 / (0.4 * max(args.steps, 1))) ** (1 / 3)))
+    n = max(32, min(96, n))
+    import oracle as O
+
+    geo = geometry(n)
+    cfg = O.make_config(stencil=1, nx=n, ny=n, nz=n, periodic=(1, 1, 1), tau=0.7, g=(1e-6, 0, 0), bc=2,
+                        vibb_density=1)
+    st = O.init(cfg, geo.solid)
+    O.run(cfg, geo.solid, geo.links, st, args.warmup)
+    t0 = time.perf_counter()
+    O.run(cfg, geo.solid, geo.links, st, args.steps)
+    dt = time.perf_counter() - t0
+    nf = geo.fluid_count()
+    v = nf * args.steps / dt / 1e6
+    line = {"metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": f"{n}^3 sub-case of the same recipe",
+                       "fluid_nodes": nf, "links": int(len(geo.links)), "parallelism": "replicas"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": f"{n}^3 sub-case, {args.steps} steps, FP64 oracle, single thread"},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=384, help="lattice side (default: the 384^3 workload)")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+
+    dist = _dist()
+    rank = dist.get_rank() if dist is not None else 0
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    from paper_1903_01111_gb300 import lbm
+
+    peak, peak_src = _peaks()
+    t0 = time.perf_counter()
+    geo = geometry(args.n)
+    t_geo = time.perf_counter() - t0
+    clocks = Clocks(local)
+    clocks.start()
+    r32 = run_precision(lbm, torch, geo, lbm.LBM_FP32_SHIFTED, args.steps, args.warmup, dist, peak)
+    ck = clocks.stop()
+    r64 = None
+    if not args.no_fp64:
+        clocks64 = Clocks(local)
+        clocks64.start()
+        r64 = run_precision(lbm, torch, geo, lbm.LBM_FP64, args.steps, args.warmup, dist, peak)
+        r64["clocks"] = clocks64.stop()
+    e2e = None if args.no_e2e else run_e2e(lbm, torch, geo, args.steps)
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = run_oracle(96, 16)
+    if rank != 0:
+        return 0
+    world = dist.get_world_size() if dist is not None else 1
+    line = {
+        "metric": METRIC, "value": r32["mlups"], "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r32["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.n == 384 else WORKLOAD.replace("384^3", f"{args.n}^3"),
+                   "precision": "fp32_shifted", "nodes": r32["n_nodes"], "fluid_nodes": r32["n_fluid"],
+                   "links": r32["n_links"], "porosity": geo.info["porosity"], "spheres": geo.info["spheres"],
+                   "l2": "inputs larger than L2 (state > 8 GB), no flush", "parallelism": "replicas",
+                   "geometry_build_s": t_geo},
+        "roofline": dict(r32["roofline"], peak_source=peak_src),
+        "kernels": r32["kernels"], "step_gbs": r32["step_gbs"],
+        "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": r32["launches"],
+        "clocks": ck,
+    }
+    if r64 is not None:
+        line["fp64"] = {"value": r64["mlups"], "unit": "MLUPS", "ms_per_step": r64["ms_per_step"],
+                        "roofline": dict(r64["roofline"], peak_source=peak_src), "kernels": r64["kernels"],
+                        "step_gbs": r64["step_gbs"], "gpu_launches": r64["launches"], "clocks": r64["clocks"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -50,6 +50,7 @@ enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 };
 enum { LBM_BGK = 0, LBM_MRT = 1 };
 enum { LBM_BC_DEFAULT = -1, LBM_BC_HALFWAY = 0, LBM_BC_BOUZIDI = 1, LBM_BC_VIBB = 2 };
 enum { LBM_FP64 = 0, LBM_FP32_SHIFTED = 1 };
+enum { LBM_VIBB_RHO_PRINTED = 0, LBM_VIBB_RHO_LOCAL = 1 };
 
 #define LBM_MAX_BODIES 64
 
@@ -77,6 +78,13 @@ typedef struct lbm_lattice_s* lbm_handle;
  *             the moving-wall term 6 w rho0 (e_i.u_w), Eqs. q_less/q_larger).
  *  g          body force per unit volume.
  *  precision  LBM_FP64 or LBM_FP32_SHIFTED.
+ *  vibb_density  LBM_VIBB_RHO_PRINTED: rho_d = 2q rho_f + (1 - 2q) rho_ff for
+ *             every q (Sec. 3.1, Eq. rhod; an extrapolation when q > 1/2).
+ *             LBM_VIBB_RHO_LOCAL: rho_d = rho_f when q > 1/2 (the O(Ma^2)
+ *             density approximation rho_s = rho_f that Sec. 3.1 quotes from
+ *             the non-equilibrium extrapolation scheme).  The printed form
+ *             drains mass at dead-end pore nodes of 3-D porous media and
+ *             diverges there; the local form does not.
  *  cuda_stream a cudaStream_t to order all work on, or NULL for a stream the
  *             library creates and destroys. */
 typedef struct {
@@ -90,7 +98,7 @@ typedef struct {
   double g[3];
   double inlet_umax, inlet_y0, inlet_y1;
   int32_t precision;
-  int32_t reserved;
+  int32_t vibb_density;
   void* cuda_stream;
 } lbm_config;
 

@@ -52,6 +52,8 @@ class OracleConfig(ctypes.Structure):
         ("inlet_umax", ctypes.c_double),
         ("inlet_y0", ctypes.c_double),
         ("inlet_y1", ctypes.c_double),
+        ("precision", ctypes.c_int32),
+        ("vibb_density", ctypes.c_int32),
     ]
 
 
@@ -97,7 +99,8 @@ def _check(rc):
 
 
 def make_config(stencil=0, nx=1, ny=1, nz=1, periodic=(1, 1, 1), tau=0.8, rho0=1.0, g=(0.0, 0.0, 0.0), bc=2,
-                collision=0, inlet=0, outlet=0, inlet_umax=0.0, inlet_y0=0.0, inlet_y1=0.0) -> OracleConfig:
+                collision=0, inlet=0, outlet=0, inlet_umax=0.0, inlet_y0=0.0, inlet_y1=0.0, vibb_density=0,
+                precision=0) -> OracleConfig:
     c = OracleConfig()
     c.stencil, c.collision, c.bc = stencil, collision, bc
     c.nx, c.ny, c.nz = nx, ny, nz
@@ -107,6 +110,8 @@ def make_config(stencil=0, nx=1, ny=1, nz=1, periodic=(1, 1, 1), tau=0.8, rho0=1
     c.inlet, c.outlet = int(inlet), int(outlet)
     c.tau, c.rho0 = float(tau), float(rho0)
     c.inlet_umax, c.inlet_y0, c.inlet_y1 = float(inlet_umax), float(inlet_y0), float(inlet_y1)
+    c.vibb_density = int(vibb_density)
+    c.precision = int(precision)
     return c
 
 

@@ -79,6 +79,8 @@ struct oracle_config {
   double g[3];                // body force per unit volume
   double inlet_umax;          // peak of the parabolic inflow
   double inlet_y0, inlet_y1;  // wall positions bounding the inflow parabola
+  int32_t precision;          // unused by the oracle (always FP64)
+  int32_t vibb_density;       // 0: rho_d as printed for every q; 1: rho_d = rho_f when q > 1/2
 };
 
 // Own definition of one cut link (same layout as the library's lbm_link).
@@ -247,7 +249,10 @@ struct Oracle {
       return (fp_f[ip] + wall) / (2.0 * q) + (2.0 * q - 1.0) / (2.0 * q) * fp_f[i];
     }
     // VIBB (Sec. 3.1): f_i(x_f,t+1) = feq_i'(rho_d, u_d) + fneq_i'(x_d) + wall
-    const T rd = 2.0 * q * rf + (1.0 - 2.0 * q) * rff;  // Eq. (rhod)
+    // Eq. (rhod) as printed extrapolates for q > 1/2; the optional reading
+    // takes the density of x_f there (the O(Ma^2) approximation rho_s = rho_f
+    // that Sec. 3.1 quotes from the non-equilibrium extrapolation scheme).
+    const T rd = (c.vibb_density == 1 && q > 0.5) ? rf : 2.0 * q * rf + (1.0 - 2.0 * q) * rff;
     // non-equilibrium part at d, each term rescaled by its density ratio
     const T nd = 2.0 * q * (fp_f[ip] - feq(ip, rf, uf)) * (rd / rf) +
                  (1.0 - 2.0 * q) * (fp_ff[ip] - feq(ip, rff, uff)) * (rd / rff);

@@ -16,6 +16,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <stdint.h>
 
 typedef struct {
   int32_t kind;      /* 0 = ball, 1 = half-space */
@@ -274,69 +275,67 @@ int64_t geom_pack_add(int nx, int ny, int nz, const int32_t* periodic, const dou
   return k;
 }
 
-/* Cut links of all fluid nodes, sorted by (node, dir).  Fluid nodes in the
- * columns x = 0 (if open_lo) and x = nx-1 (if open_hi) are open-boundary nodes
- * and get no links.  out may be NULL to count only.  Returns the link count,
- * or a negative error code:
- *   -1 allocation failure, -2 a fluid node's neighbour leaves the lattice
- *   through a non-periodic face, -3 a solid neighbour has no wall crossing.
- * err_node receives the offending node for -2/-3. */
-int64_t geom_links(int stencil, int nx, int ny, int nz, const int32_t* periodic, const geom_body* bodies, int nb,
-                   const uint8_t* mask, int open_lo, int open_hi, geom_link* out, int64_t* err_node) {
-  ctx_t g;
-  if (setup(&g, stencil, nx, ny, nz, periodic, bodies, nb) != 0) return -1;
-  const int64_t N = (int64_t)nx * ny * nz;
+/* Links of one lattice row (y, z): count only (out == NULL) or fill.
+ * Returns the count, or a negative error code with *err_node set. */
+static int64_t row_links(const ctx_t* g, const uint8_t* mask, int open_lo, int open_hi, int64_t y, int64_t z,
+                         geom_link* out, int64_t* err_node) {
+  const int nx = g->nx, ny = g->ny, nz = g->nz;
   const int L[3] = {nx, ny, nz};
   int64_t count = 0;
-  for (int64_t n = 0; n < N; ++n) {
+  for (int x = 0; x < nx; ++x) {
+    const int64_t n = x + (int64_t)nx * (y + (int64_t)ny * z);
     if (mask[n]) continue;
-    const int xi[3] = {(int)(n % nx), (int)((n / nx) % ny), (int)(n / ((int64_t)nx * ny))};
-    if ((open_lo && xi[0] == 0) || (open_hi && xi[0] == nx - 1)) continue;
-    const double xf[3] = {(double)xi[0], (double)xi[1], (double)xi[2]};
-    for (int d = 1; d < g.Q; ++d) {
+    if ((open_lo && x == 0) || (open_hi && x == nx - 1)) continue;
+    const int xi[3] = {x, (int)y, (int)z};
+    const double xf[3] = {(double)x, (double)y, (double)z};
+    for (int d = 1; d < g->Q; ++d) {
       int s[3];
       int outside = 0;
       for (int a = 0; a < 3; ++a) {
-        s[a] = xi[a] + g.e[d][a];
+        s[a] = xi[a] + g->e[d][a];
         if (s[a] < 0 || s[a] >= L[a]) {
-          if (!periodic[a]) outside = 1;
+          if (!g->periodic[a]) outside = 1;
           s[a] = wrap_idx(s[a], L[a]);
         }
       }
       if (outside) {
         /* allowed only when the neighbour face is an open boundary column */
-        const int through_x_open = (xi[0] + g.e[d][0] < 0 && open_lo) || (xi[0] + g.e[d][0] >= nx && open_hi);
+        const int through_x_open = (xi[0] + g->e[d][0] < 0 && open_lo) || (xi[0] + g->e[d][0] >= nx && open_hi);
         if (through_x_open) continue;
-        free_grid(&g);
-        if (err_node) *err_node = n;
+        *err_node = n;
         return -2;
       }
       const int64_t sn = s[0] + (int64_t)nx * (s[1] + (int64_t)ny * s[2]);
       if (!mask[sn]) continue;
-      /* first wall crossing along x_f + t e_d */
-      double best = 2.0;
-      int bbest = -1;
-      const int cx = s[0] / g.cs, cy = s[1] / g.cs, cz = s[2] / g.cs;
-      const int64_t cell = cx + (int64_t)g.gx * (cy + (int64_t)g.gy * cz);
-      for (int32_t k = g.cell_start[cell]; k < g.cell_start[cell + 1]; ++k) {
-        const int bi = g.cell_items[k];
-        const double t = entry(&g, &bodies[bi], xf, g.e[d]);
-        if (t > 0.0 && t < best) { best = t; bbest = bi; }
-      }
-      for (int k = 0; k < g.nplanes; ++k) {
-        const int bi = g.planes[k];
-        const double t = entry(&g, &bodies[bi], xf, g.e[d]);
-        if (t > 0.0 && t < best) { best = t; bbest = bi; }
-      }
-      if (bbest < 0 || best > 1.0 + 1e-9) {
-        free_grid(&g);
-        if (err_node) *err_node = n;
-        return -3;
-      }
-      if (best > 1.0) best = 1.0;
       if (out) {
+        /* first wall crossing along x_f + t e_d */
+        double best = 2.0;
+        int bbest = -1;
+        const int cx = s[0] / g->cs, cy = s[1] / g->cs, cz = s[2] / g->cs;
+        const int64_t cell = cx + (int64_t)g->gx * (cy + (int64_t)g->gy * cz);
+        for (int32_t k = g->cell_start[cell]; k < g->cell_start[cell + 1]; ++k) {
+          const int bi = g->cell_items[k];
+          const double t = entry(g, &g->bodies[bi], xf, g->e[d]);
+          if (t > 0.0 && t < best) {
+            best = t;
+            bbest = bi;
+          }
+        }
+        for (int k = 0; k < g->nplanes; ++k) {
+          const int bi = g->planes[k];
+          const double t = entry(g, &g->bodies[bi], xf, g->e[d]);
+          if (t > 0.0 && t < best) {
+            best = t;
+            bbest = bi;
+          }
+        }
+        if (bbest < 0 || best > 1.0 + 1e-9) {
+          *err_node = n;
+          return -3;
+        }
+        if (best > 1.0) best = 1.0;
         geom_link* lk = &out[count];
-        const geom_body* b = &bodies[bbest];
+        const geom_body* b = &g->bodies[bbest];
         lk->node = n;
         lk->dir = d;
         lk->bc = (int16_t)b->bc;
@@ -345,9 +344,9 @@ int64_t geom_links(int stencil, int nx, int ny, int nz, const int32_t* periodic,
         /* wall velocity at x_w = x_f + q e: U + omega x (x_w - c) */
         double uw[3] = {b->vel[0], b->vel[1], b->vel[2]};
         if (b->kind == 0) {
-          const double xw[3] = {xf[0] + best * g.e[d][0], xf[1] + best * g.e[d][1], xf[2] + best * g.e[d][2]};
+          const double xw[3] = {xf[0] + best * g->e[d][0], xf[1] + best * g->e[d][1], xf[2] + best * g->e[d][2]};
           double r[3];
-          ball_disp(&g, b, xw, r);
+          ball_disp(g, b, xw, r);
           uw[0] += b->omega[1] * r[2] - b->omega[2] * r[1];
           uw[1] += b->omega[2] * r[0] - b->omega[0] * r[2];
           uw[2] += b->omega[0] * r[1] - b->omega[1] * r[0];
@@ -359,6 +358,71 @@ int64_t geom_links(int stencil, int nx, int ny, int nz, const int32_t* periodic,
       ++count;
     }
   }
-  free_grid(&g);
   return count;
+}
+
+/* Cut links of all fluid nodes, sorted by (node, dir).  Fluid nodes in the
+ * columns x = 0 (if open_lo) and x = nx-1 (if open_hi) are open-boundary nodes
+ * and get no links.  out may be NULL to count only.  Returns the link count,
+ * or a negative error code:
+ *   -1 allocation failure, -2 a fluid node's neighbour leaves the lattice
+ *   through a non-periodic face, -3 a solid neighbour has no wall crossing.
+ * err_node receives the offending node (the smallest one) for -2/-3.
+ * Rows are processed in parallel (OpenMP). */
+int64_t geom_links(int stencil, int nx, int ny, int nz, const int32_t* periodic, const geom_body* bodies, int nb,
+                   const uint8_t* mask, int open_lo, int open_hi, geom_link* out, int64_t* err_node) {
+  ctx_t g;
+  if (setup(&g, stencil, nx, ny, nz, periodic, bodies, nb) != 0) return -1;
+  const int64_t rows = (int64_t)ny * nz;
+  int64_t* start = (int64_t*)calloc(rows + 1, sizeof(int64_t));
+  if (!start) {
+    free_grid(&g);
+    return -1;
+  }
+  int64_t err = 0, bad = INT64_MAX;
+  /* pass 1: counts per row (no intersection work) */
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t r = 0; r < rows; ++r) {
+    int64_t en = 0;
+    const int64_t c = row_links(&g, mask, open_lo, open_hi, r % ny, r / ny, NULL, &en);
+    if (c < 0) {
+#pragma omp critical
+      {
+        if (en < bad) {
+          bad = en;
+          err = c;
+        }
+      }
+    } else {
+      start[r + 1] = c;
+    }
+  }
+  if (err == 0) {
+    for (int64_t r = 0; r < rows; ++r) start[r + 1] += start[r];
+    if (out) {
+      /* pass 2: fill each row's slice */
+#pragma omp parallel for schedule(dynamic, 16)
+      for (int64_t r = 0; r < rows; ++r) {
+        int64_t en = 0;
+        const int64_t c = row_links(&g, mask, open_lo, open_hi, r % ny, r / ny, out + start[r], &en);
+        if (c < 0) {
+#pragma omp critical
+          {
+            if (en < bad) {
+              bad = en;
+              err = c;
+            }
+          }
+        }
+      }
+    }
+  }
+  const int64_t total = start[rows];
+  free(start);
+  free_grid(&g);
+  if (err != 0) {
+    if (err_node) *err_node = bad;
+    return err;
+  }
+  return total;
 }

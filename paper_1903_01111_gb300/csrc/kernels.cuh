@@ -142,7 +142,8 @@ template <class L, class P>
 __device__ __forceinline__ typename P::T link_rule(int rule, int ip, typename P::T q, typename P::T fpf,
                                                    typename P::T fpff, typename P::T fpi, typename P::T wall,
                                                    const typename P::T* uw, typename P::T rf, const typename P::T* uf,
-                                                   typename P::T rff, const typename P::T* uff, double rho0) {
+                                                   typename P::T rff, const typename P::T* uff, double rho0,
+                                                   int local_rho) {
   using T = typename P::T;
   if (rule == 0) return fpf + wall;  // half-way bounce-back
   const T two_q = (T)2 * q;
@@ -153,7 +154,8 @@ __device__ __forceinline__ typename P::T link_rule(int rule, int ip, typename P:
   // VIBB, Sec. 3.1
   const T rhof = P::shifted ? (T)rho0 + rf : rf;
   const T rhoff = P::shifted ? (T)rho0 + rff : rff;
-  const T rd = two_q * rf + ((T)1 - two_q) * rff;  // Eq. (rhod), storage form
+  // Eq. (rhod), storage form; optionally rho_d = rho_f when q > 1/2
+  const T rd = (local_rho && q > (T)0.5) ? rf : two_q * rf + ((T)1 - two_q) * rff;
   const T rhod = P::shifted ? (T)rho0 + rd : rd;
   const T neq_f = fpf - equilibrium<L, P>(ip, rf, rhof, uf[0], uf[1], uf[2]);
   const T neq_ff = fpff - equilibrium<L, P>(ip, rff, rhoff, uff[0], uff[1], uff[2]);
@@ -236,7 +238,7 @@ __global__ void __launch_bounds__(256) k_links(typename P::T* __restrict__ f, co
         uff[2] = mom[3 * N + ff];
       }
     }
-    const T val = link_rule<L, P>(rule, ip, q, fpf, fpff, fpi, wall, uw, rf, uf, rff, uff, p.rho0);
+    const T val = link_rule<L, P>(rule, ip, q, fpf, fpff, fpi, wall, uw, rf, uf, rff, uff, p.rho0, p.vibb_local_rho);
     f[(int64_t)i * N + s] = val;
     if (body >= 0) {
       // momentum exchange (f+_i'(x_f,t) + f_i(x_f,t+1)) e_i', FP64; shifted

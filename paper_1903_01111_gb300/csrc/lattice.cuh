@@ -66,6 +66,7 @@ struct Params {
   int collision;        // 0 BGK, 1 MRT
   double inlet_umax, inlet_y0, inlet_y1;
   int inlet, outlet;
+  int vibb_local_rho;   // rho_d = rho_f when q > 1/2
 };
 
 }  // namespace lbm

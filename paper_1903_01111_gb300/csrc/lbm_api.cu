@@ -209,6 +209,8 @@ lbm_status lbm_create_lattice(const lbm_config* cfg, lbm_handle* out) {
   if (c.collision == LBM_MRT) return fail(LBM_ERR_UNSUPPORTED, "MRT collision is not built");
   if (c.collision != LBM_BGK) return fail(LBM_ERR_INVALID_ARG, "unknown collision %d", c.collision);
   if (c.bc < LBM_BC_HALFWAY || c.bc > LBM_BC_VIBB) return fail(LBM_ERR_INVALID_ARG, "unknown default rule %d", c.bc);
+  if (c.vibb_density != LBM_VIBB_RHO_PRINTED && c.vibb_density != LBM_VIBB_RHO_LOCAL)
+    return fail(LBM_ERR_INVALID_ARG, "unknown vibb_density %d", c.vibb_density);
   if (c.nx < 1 || c.ny < 1 || c.nz < 1) return fail(LBM_ERR_INVALID_ARG, "lattice size must be positive");
   if (c.stencil == LBM_D2Q9 && c.nz != 1) return fail(LBM_ERR_INVALID_ARG, "D2Q9 needs nz == 1");
   if (c.ny > 65535 || c.nz > 65535) return fail(LBM_ERR_UNSUPPORTED, "ny and nz are limited to 65535");
@@ -249,6 +251,7 @@ lbm_status lbm_create_lattice(const lbm_config* cfg, lbm_handle* out) {
   p.inlet_umax = c.inlet_umax;
   p.inlet_y0 = c.inlet_y0;
   p.inlet_y1 = c.inlet_y1;
+  p.vibb_local_rho = c.vibb_density == LBM_VIBB_RHO_LOCAL ? 1 : 0;
 
   lbm_status st = LBM_OK;
   if (c.cuda_stream) {
@@ -527,7 +530,7 @@ lbm_status lbm_step(lbm_handle h, int64_t n) {
       if (st != LBM_OK) return st;
       h->cur ^= 1;
       ++h->step;
-      if (h->ev_used > 4096) {
+      if (h->ev_used > (1u << 16)) {
         st = harvest_events(h);
         if (st != LBM_OK) return st;
       }

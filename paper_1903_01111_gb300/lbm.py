@@ -28,6 +28,7 @@ LBM_D2Q9, LBM_D3Q19 = 0, 1
 LBM_BGK, LBM_MRT = 0, 1
 LBM_BC_DEFAULT, LBM_BC_HALFWAY, LBM_BC_BOUZIDI, LBM_BC_VIBB = -1, 0, 1, 2
 LBM_FP64, LBM_FP32_SHIFTED = 0, 1
+LBM_VIBB_RHO_PRINTED, LBM_VIBB_RHO_LOCAL = 0, 1
 LBM_MAX_BODIES = 64
 STATUS_NAMES = {0: "LBM_OK", 1: "LBM_ERR_INVALID_ARG", 2: "LBM_ERR_STATE", 3: "LBM_ERR_CUDA", 4: "LBM_ERR_OOM",
                 5: "LBM_ERR_DIVERGED", 6: "LBM_ERR_TIMEOUT", 7: "LBM_ERR_UNSUPPORTED"}
@@ -63,7 +64,7 @@ class lbm_config(ctypes.Structure):
         ("inlet_y0", ctypes.c_double),
         ("inlet_y1", ctypes.c_double),
         ("precision", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("vibb_density", ctypes.c_int32),
         ("cuda_stream", ctypes.c_void_p),
     ]
 
@@ -133,7 +134,7 @@ def _ptr(a):
 
 def make_config(stencil=LBM_D2Q9, nx=1, ny=1, nz=1, periodic=(1, 1, 1), tau=0.8, rho0=1.0, g=(0.0, 0.0, 0.0),
                 bc=LBM_BC_VIBB, collision=LBM_BGK, inlet=0, outlet=0, inlet_umax=0.0, inlet_y0=0.0, inlet_y1=0.0,
-                precision=LBM_FP64, stream=None) -> lbm_config:
+                precision=LBM_FP64, stream=None, vibb_density=LBM_VIBB_RHO_PRINTED) -> lbm_config:
     c = lbm_config()
     c.stencil, c.collision, c.bc = stencil, collision, bc
     c.nx, c.ny, c.nz = nx, ny, nz
@@ -144,6 +145,7 @@ def make_config(stencil=LBM_D2Q9, nx=1, ny=1, nz=1, periodic=(1, 1, 1), tau=0.8,
     c.tau, c.rho0 = float(tau), float(rho0)
     c.inlet_umax, c.inlet_y0, c.inlet_y1 = float(inlet_umax), float(inlet_y0), float(inlet_y1)
     c.precision = precision
+    c.vibb_density = vibb_density
     c.cuda_stream = stream
     return c
 

@@ -308,7 +308,7 @@ def _oracle_one_node_step(geo, e, w, opp, links_at, fp_of, x, tau, g):
         return int(c[0] + nx * (c[1] + ny * c[2]))
 
     for i in range(Q):
-        f[i] = fp_of(nb(x, i, -1))
+        f[i] = fp_of(nb(x, i, -1))[i]
     for lk in links_at.get(x, []):
         ip = int(lk["dir"])
         i = opp[ip]
@@ -361,3 +361,11 @@ def test_full_size_sphere_pack_sampled_nodes(L):
         want = _oracle_one_node_step(geo, e, w, opp, links_at, lambda n: table[n], int(x), tau, g)
         assert np.abs(got[k] - want).max() < 1e-13, (x, got[k] - want)
     lat.close()
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_sphere_pack_32_local_density(L, prec):
+    """The LBM_VIBB_RHO_LOCAL reading (rho_d = rho_f when q > 1/2), used by
+    the 384^3 porous workload."""
+    geo = G.sphere_pack(32, porosity=0.40, rmin=3.0, rmax=6.0, seed=7)
+    _compare(L, geo, 200, _p(L, prec), tau=0.7, g=(1e-5, 0, 0), bc=2, vibb_density=1)

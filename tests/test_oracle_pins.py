@@ -539,3 +539,39 @@ def test_open_boundaries_keep_developed_poiseuille():
     # few 1e-6; a wrong inlet or outlet formula gives errors of order 1e-2.
     assert np.abs(st.u[fl, 0] - prof[fl]).max() < 2e-5 * umax
     assert np.abs(st.u[fl, 1]).max() < 2e-5 * umax
+
+
+@pytest.mark.parametrize("stencil", [0, 1])
+def test_vibb_local_density_reading(stencil):
+    """The optional reading LBM_VIBB_RHO_LOCAL keeps the density of x_f when
+    q > 1/2 and is otherwise the printed rule: identical for q <= 1/2 (bit for
+    bit), and for q > 1/2 exact with rho held at rho_f while u and fneq/rho
+    are taken at the departure point."""
+    e, w = _dirs(stencil)
+    printed = O.make_config(stencil=stencil, rho0=1.0)
+    local = O.make_config(stencil=stencil, rho0=1.0, vibb_density=1)
+    rng = np.random.default_rng(21 + stencil)
+    Q = len(w)
+    opp = [int(np.flatnonzero((e == -e[i]).all(1))[0]) for i in range(Q)]
+    for q in (0.1, 0.37, 0.5, 0.62, 0.93, 1.0):
+        for ip in range(1, Q):
+            u0, du = rng.uniform(-0.05, 0.05, 3), rng.uniform(-0.02, 0.02, 3)
+            if stencil == 0:
+                u0[2] = du[2] = 0.0
+            uf = lambda s: u0 + du * s
+            r0, dr = 1.0 + rng.uniform(-0.01, 0.01), rng.uniform(-0.01, 0.01)
+            rf = lambda s: r0 + dr * s
+            af, aff = rng.normal() * 1e-3, rng.normal() * 1e-3
+            fpf = O.feq(stencil, rf(0), uf(0))
+            fpff = O.feq(stencil, rf(-1), uf(-1))
+            fpf[ip] += af * rf(0)
+            fpff[ip] += aff * rf(-1)
+            uw = uf(q)
+            args = (2, ip, q, uw, fpf, fpff, rf(0), uf(0), rf(-1), uf(-1))
+            a, b = O.link_value(printed, *args), O.link_value(local, *args)
+            if q <= 0.5:
+                assert a == b
+            else:
+                wall = 6 * w[ip] * float(e[opp[ip]] @ uw)
+                expect = (O.feq(stencil, rf(0), uf(2 * q - 1))[ip] + rf(0) * (af + (af - aff) * (2 * q - 1)) + wall)
+                assert abs(b - expect) < 5e-15
