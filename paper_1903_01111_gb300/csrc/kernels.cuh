@@ -37,6 +37,13 @@ struct F32S {
   static constexpr bool shifted = true;
 };
 
+// One moment-cache record per node: (r, ux, uy, uz) with r = rho (F64) or
+// rho - rho0 (F32S); 16 B (FP32) or 32 B (FP64), loaded in one piece.
+template <class T>
+struct __align__(4 * sizeof(T)) Mom4 {
+  T r, ux, uy, uz;
+};
+
 // --------------------------------------------------------------- helpers --
 
 // Equilibrium of Eq. (feq), C = 1, in storage form: r is rho (F64) or
@@ -57,10 +64,10 @@ __device__ __forceinline__ typename P::T equilibrium(int i, typename P::T r, typ
 __device__ __forceinline__ int src_coord(int c, int x, int xm, int xp) { return c == 0 ? x : (c > 0 ? xm : xp); }
 
 // Moments, collision and store of one fluid node.  f holds the pre-collision
-// populations f(x, t+1) in storage form.
+// populations f(x, t+1) in storage form; n < 2^31.
 template <class L, class P>
 __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Params& p, typename P::T* __restrict__ fout,
-                                              int64_t n, typename P::T* __restrict__ mom, bool cache) {
+                                              uint32_t n, Mom4<typename P::T>* __restrict__ mom, bool cache) {
   using T = typename P::T;
   T r = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
@@ -78,27 +85,25 @@ __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Pa
   const T inv = (T)1 / rho;
   // Guo forcing: velocity shifted by half the body force
   const T ux = (jx + (T)0.5 * gx) * inv, uy = (jy + (T)0.5 * gy) * inv, uz = (jz + (T)0.5 * gz) * inv;
-  if (cache) {
-    const int64_t N = p.N;
-    mom[n] = r;
-    mom[N + n] = ux;
-    mom[2 * N + n] = uy;
-    if (L::D == 3) mom[3 * N + n] = uz;
-  }
+  if (cache) mom[n] = Mom4<T>{r, ux, uy, L::D == 3 ? uz : (T)0};
   const T omega = (T)(1.0 / p.tau);
-  const T fpre = (T)(1.0 - 0.5 / p.tau);
+  const T uu15 = (T)1.5 * (ux * ux + uy * uy + uz * uz);
+  // Guo source (1 - 1/(2 tau)) w_i [3 (e_i - u).g + 9 (e_i.u)(e_i.g)]
+  //   = 3 (1 - 1/(2 tau)) w_i [(e_i.g)(1 + 3 e_i.u) - u.g]
+  const T fpre3 = (T)(3.0 * (1.0 - 0.5 / p.tau));
+  const T ug = ux * gx + uy * gy + uz * gz;
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
-    const T feq = equilibrium<L, P>(i, r, rho, ux, uy, uz);
+    const T eu = (T)L::cx(i) * ux + (T)L::cy(i) * uy + (T)L::cz(i) * uz;
+    const T w = (T)L::w(i);
+    const T poly = (T)3 * eu + (T)4.5 * eu * eu - uu15;
+    const T feq = P::shifted ? w * (r + rho * poly) : w * rho * ((T)1 + poly);
     T out = f[i] + omega * (feq - f[i]);
     if (p.has_force) {
-      const T ex = (T)L::cx(i), ey = (T)L::cy(i), ez = (T)L::cz(i);
-      const T eu = ex * ux + ey * uy + ez * uz;
-      const T s = ((T)3 * (ex - ux) + (T)9 * eu * ex) * gx + ((T)3 * (ey - uy) + (T)9 * eu * ey) * gy +
-                  ((T)3 * (ez - uz) + (T)9 * eu * ez) * gz;
-      out += fpre * (T)L::w(i) * s;
+      const T eg = (T)L::cx(i) * gx + (T)L::cy(i) * gy + (T)L::cz(i) * gz;
+      out += fpre3 * w * (eg * ((T)1 + (T)3 * eu) - ug);
     }
-    fout[(int64_t)i * p.N + n] = out;
+    fout[(size_t)i * p.N + n] = out;
   }
 }
 
@@ -108,78 +113,85 @@ __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Pa
 // Block (0,0,0) also clears the force slot of the next step.
 template <class L, class P>
 __global__ void __launch_bounds__(256) k_bulk(const typename P::T* __restrict__ fin, typename P::T* __restrict__ fout,
-                                              const uint8_t* __restrict__ mask, typename P::T* __restrict__ mom,
+                                              const uint8_t* __restrict__ mask, Mom4<typename P::T>* __restrict__ mom,
                                               double* __restrict__ force_next, Params p) {
   using T = typename P::T;
   if (force_next && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0)
     for (int t = threadIdx.x; t < 3 * MAX_BODIES; t += blockDim.x) force_next[t] = 0.0;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y, z = blockIdx.z;
-  if (x >= p.nx) return;
-  const int64_t n = x + (int64_t)p.nx * (y + (int64_t)p.ny * z);
+  const uint32_t x = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t y = blockIdx.y, z = blockIdx.z;
+  const uint32_t nx = p.nx, nxy = (uint32_t)p.nx * (uint32_t)p.ny;
+  if (x >= nx) return;
+  const uint32_t row = nx * y + nxy * z;
+  const uint32_t n = x + row;
   const uint8_t m = mask[n];
   if (m & (M_SOLID | M_OPEN)) return;
-  const int xm = x == 0 ? p.nx - 1 : x - 1, xp = x == p.nx - 1 ? 0 : x + 1;
-  const int ym = y == 0 ? p.ny - 1 : y - 1, yp = y == p.ny - 1 ? 0 : y + 1;
-  const int zm = z == 0 ? p.nz - 1 : z - 1, zp = z == p.nz - 1 ? 0 : z + 1;
+  // wrapped neighbour coordinates as row/plane offsets (32-bit)
+  const uint32_t xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+  const uint32_t ym = (y == 0 ? p.ny - 1 : y - 1) * nx, y0 = y * nx, yp = (y == (uint32_t)p.ny - 1 ? 0 : y + 1) * nx;
+  const uint32_t zm = (z == 0 ? p.nz - 1 : z - 1) * nxy, z0 = z * nxy, zp = (z == (uint32_t)p.nz - 1 ? 0 : z + 1) * nxy;
   T f[L::Q];
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
-    const int sx = src_coord(L::cx(i), x, xm, xp);
-    const int sy = src_coord(L::cy(i), y, ym, yp);
-    const int sz = src_coord(L::cz(i), z, zm, zp);
-    f[i] = __ldg(fin + (int64_t)i * p.N + sx + (int64_t)p.nx * (sy + (int64_t)p.ny * sz));
+    const uint32_t sx = L::cx(i) == 0 ? x : (L::cx(i) > 0 ? xm : xp);
+    const uint32_t sy = L::cy(i) == 0 ? y0 : (L::cy(i) > 0 ? ym : yp);
+    const uint32_t sz = L::cz(i) == 0 ? z0 : (L::cz(i) > 0 ? zm : zp);
+    f[i] = __ldg(fin + (size_t)i * p.N + (sx + sy + sz));
   }
   collide_store<L, P>(f, p, fout, n, mom, (m & M_CACHE) != 0);
 }
 
 // ----------------------------------------------------------------- links --
 
-// Missing population of one link in storage form.  fpf = f+_i'(x_f),
-// fpff = f+_i'(x_ff), fpi = f+_i(x_f); (rf, uf), (rff, uff): cached moments
-// (r = rho or rho - rho0) at time t; wall = 6 w rho0 (e_i . u_w).
-template <class L, class P>
-__device__ __forceinline__ typename P::T link_rule(int rule, int ip, typename P::T q, typename P::T fpf,
-                                                   typename P::T fpff, typename P::T fpi, typename P::T wall,
-                                                   const typename P::T* uw, typename P::T rf, const typename P::T* uf,
-                                                   typename P::T rff, const typename P::T* uff, double rho0,
-                                                   int local_rho) {
+// Per-direction data of the link kernel, staged in shared memory so that
+// lanes holding different directions read it without serialisation.
+template <class T, int Q>
+struct DirTable {
+  int off[Q];   // cx + nx (cy + ny cz): node offset of e_d (32-bit)
+  int opp[Q];
+  T w[Q];
+  T e[Q][3];
+};
+
+// Equilibrium of direction d from table values (storage form, see above).
+template <class P>
+__device__ __forceinline__ typename P::T eq_dir(typename P::T w, typename P::T ex, typename P::T ey, typename P::T ez,
+                                                typename P::T r, typename P::T rho, typename P::T ux, typename P::T uy,
+                                                typename P::T uz) {
   using T = typename P::T;
-  if (rule == 0) return fpf + wall;  // half-way bounce-back
-  const T two_q = (T)2 * q;
-  if (rule == 1) {  // Bouzidi, Eqs. (q_less) and (q_larger)
-    if (q <= (T)0.5) return two_q * fpf + ((T)1 - two_q) * fpff + wall;
-    return (fpf + wall) / two_q + (two_q - (T)1) / two_q * fpi;
-  }
-  // VIBB, Sec. 3.1
-  const T rhof = P::shifted ? (T)rho0 + rf : rf;
-  const T rhoff = P::shifted ? (T)rho0 + rff : rff;
-  // Eq. (rhod), storage form; optionally rho_d = rho_f when q > 1/2
-  const T rd = (local_rho && q > (T)0.5) ? rf : two_q * rf + ((T)1 - two_q) * rff;
-  const T rhod = P::shifted ? (T)rho0 + rd : rd;
-  const T neq_f = fpf - equilibrium<L, P>(ip, rf, rhof, uf[0], uf[1], uf[2]);
-  const T neq_ff = fpff - equilibrium<L, P>(ip, rff, rhoff, uff[0], uff[1], uff[2]);
-  const T nd = two_q * neq_f * (rhod / rhof) + ((T)1 - two_q) * neq_ff * (rhod / rhoff);
-  T ud[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const T us = q <= (T)0.5 ? two_q * uf[a] + ((T)1 - two_q) * uff[a]
-                             : ((T)1 - q) / q * uf[a] + (two_q - (T)1) / q * uw[a];
-    const T uss = ((T)1 - q) / ((T)1 + q) * uff[a] + two_q / ((T)1 + q) * uw[a];
-    ud[a] = us / (T)3 + (T)2 * uss / (T)3;
-  }
-  return equilibrium<L, P>(ip, rd, rhod, ud[0], ud[1], ud[2]) + nd + wall;
+  const T eu = ex * ux + ey * uy + ez * uz;
+  const T poly = (T)3 * eu + (T)4.5 * eu * eu - (T)1.5 * (ux * ux + uy * uy + uz * uz);
+  return P::shifted ? w * (r + rho * poly) : w * rho * ((T)1 + poly);
 }
 
 // One thread per link.  keys: packed (node, dir, rule, ff fallback, wrap,
 // body); qv: q in storage precision; uw: [D][nl] wall velocities or null.
 // force: the step's accumulator slot [MAX_BODIES][3] (FP64).
+//
+// Rules (storage form; the rest part w rho0 cancels because every rule's
+// weights sum to one):
+//   half-way  f_i = f+_i'(x_f) + wall
+//   Bouzidi   q <= 1/2: 2q f+_i'(x_f) + (1-2q) f+_i'(x_ff) + wall   (Eq. q_less)
+//             q >  1/2: (f+_i'(x_f) + wall)/(2q) + (2q-1)/(2q) f+_i(x_f)  (Eq. q_larger)
+//   VIBB      feq_i'(rho_d, u_d) + fneq_i'(x_d) + wall                 (Sec. 3.1)
+// with wall = 6 w rho0 (e_i . u_w).
 template <class L, class P>
-__global__ void __launch_bounds__(256) k_links(typename P::T* __restrict__ f, const typename P::T* __restrict__ mom,
+__global__ void __launch_bounds__(256) k_links(typename P::T* __restrict__ f, const Mom4<typename P::T>* __restrict__ mom,
                                                const uint64_t* __restrict__ keys, const typename P::T* __restrict__ qv,
                                                const typename P::T* __restrict__ uwv, int64_t nl,
                                                double* __restrict__ force, Params p) {
   using T = typename P::T;
+  __shared__ DirTable<T, L::Q> tab;
+  if (threadIdx.x < L::Q) {
+    const int d = threadIdx.x;
+    tab.off[d] = L::cx(d) + p.nx * (L::cy(d) + p.ny * L::cz(d));
+    tab.opp[d] = L::opp(d);
+    tab.w[d] = (T)L::w(d);
+    tab.e[d][0] = (T)L::cx(d);
+    tab.e[d][1] = (T)L::cy(d);
+    tab.e[d][2] = (T)L::cz(d);
+  }
+  __syncthreads();
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double F0 = 0.0, F1 = 0.0, F2 = 0.0;
   int body = -1;
@@ -190,63 +202,89 @@ __global__ void __launch_bounds__(256) k_links(typename P::T* __restrict__ f, co
     const int fb = (int)((key >> 7) & 1);
     const int wrap = (int)((key >> 8) & 1);
     body = (int)((key >> 9) & 127) - 1;
-    const int64_t node = (int64_t)(key >> KEY_NODE_SHIFT);
-    const int i = L::opp(ip);
-    const int cx = L::cx(ip), cy = L::cy(ip), cz = L::cz(ip);
-    const int64_t N = p.N;
-    int64_t s, ff;
+    const uint32_t node = (uint32_t)(key >> KEY_NODE_SHIFT);
+    const int i = tab.opp[ip];
+    const T ex = tab.e[ip][0], ey = tab.e[ip][1], ez = tab.e[ip][2];
+    const T w = tab.w[ip];
+    const size_t N = (size_t)p.N;
+    uint32_t s, ff;
     if (!wrap) {
-      const int64_t o = cx + (int64_t)p.nx * (cy + (int64_t)p.ny * cz);
+      const uint32_t o = (uint32_t)tab.off[ip];
       s = node + o;
       ff = node - o;
     } else {
-      const int64_t nxy = (int64_t)p.nx * p.ny;
-      const int x = (int)(node % p.nx), y = (int)((node / p.nx) % p.ny), z = (int)(node / nxy);
-      const int xs = (x + cx + p.nx) % p.nx, ys = (y + cy + p.ny) % p.ny, zs = (z + cz + p.nz) % p.nz;
-      const int xf = (x - cx + p.nx) % p.nx, yf = (y - cy + p.ny) % p.ny, zf = (z - cz + p.nz) % p.nz;
-      s = xs + p.nx * (ys + (int64_t)p.ny * zs);
-      ff = xf + p.nx * (yf + (int64_t)p.ny * zf);
+      const uint32_t nx = p.nx, ny = p.ny, nz = p.nz;
+      const uint32_t x = node % nx, y = (node / nx) % ny, z = node / (nx * ny);
+      const int cx = (int)ex, cy = (int)ey, cz = (int)ez;
+      const uint32_t xs = (x + cx + nx) % nx, ys = (y + cy + ny) % ny, zs = (z + cz + nz) % nz;
+      const uint32_t xf = (x - cx + nx) % nx, yf = (y - cy + ny) % ny, zf = (z - cz + nz) % nz;
+      s = xs + nx * (ys + ny * zs);
+      ff = xf + nx * (yf + ny * zf);
     }
     if (fb) ff = node;
     const T q = qv[k];
-    T uw[3] = {0, 0, 0};
+    T uw0 = 0, uw1 = 0, uw2 = 0;
     if (uwv) {
-      uw[0] = uwv[k];
-      uw[1] = uwv[nl + k];
-      if (L::D == 3) uw[2] = uwv[2 * nl + k];
+      uw0 = uwv[k];
+      uw1 = uwv[nl + k];
+      if (L::D == 3) uw2 = uwv[2 * nl + k];
     }
     // 6 w_i' rho0 (e_i . u_w) with e_i = -e_i'
-    const T wall = -(T)(6.0 * L::w(ip) * p.rho0) * ((T)cx * uw[0] + (T)cy * uw[1] + (T)cz * uw[2]);
-    const T fpf = f[(int64_t)ip * N + node];
-    T fpff = 0, fpi = 0, rf = 0, rff = 0;
-    T uf[3] = {0, 0, 0}, uff[3] = {0, 0, 0};
-    if (rule == 1) {
-      if (q <= (T)0.5)
-        fpff = f[(int64_t)ip * N + ff];
-      else
-        fpi = f[(int64_t)i * N + node];
-    } else if (rule == 2) {
-      fpff = f[(int64_t)ip * N + ff];
-      rf = mom[node];
-      rff = mom[ff];
-      uf[0] = mom[N + node];
-      uf[1] = mom[2 * N + node];
-      uff[0] = mom[N + ff];
-      uff[1] = mom[2 * N + ff];
-      if (L::D == 3) {
-        uf[2] = mom[3 * N + node];
-        uff[2] = mom[3 * N + ff];
+    const T wall = -(T)6 * w * (T)p.rho0 * (ex * uw0 + ey * uw1 + ez * uw2);
+    const T fpf = f[(size_t)ip * N + node];
+    const T two_q = (T)2 * q;
+    T val;
+    if (rule == 0) {
+      val = fpf + wall;
+    } else if (rule == 1) {
+      if (q <= (T)0.5) {
+        val = two_q * fpf + ((T)1 - two_q) * f[(size_t)ip * N + ff] + wall;
+      } else {
+        const T fpi = f[(size_t)i * N + node];
+        const T inv2q = (T)1 / two_q;
+        val = (fpf + wall) * inv2q + (two_q - (T)1) * inv2q * fpi;
       }
+    } else {
+      const T fpff = f[(size_t)ip * N + ff];
+      const Mom4<T> mf = mom[node], mff = mom[ff];
+      const T rhof = P::shifted ? (T)p.rho0 + mf.r : mf.r;
+      const T rhoff = P::shifted ? (T)p.rho0 + mff.r : mff.r;
+      // Eq. (rhod) in storage form; optionally rho_d = rho_f when q > 1/2
+      const T rd = (p.vibb_local_rho && q > (T)0.5) ? mf.r : two_q * mf.r + ((T)1 - two_q) * mff.r;
+      const T rhod = P::shifted ? (T)p.rho0 + rd : rd;
+      const T neq_f = fpf - eq_dir<P>(w, ex, ey, ez, mf.r, rhof, mf.ux, mf.uy, mf.uz);
+      const T neq_ff = fpff - eq_dir<P>(w, ex, ey, ez, mff.r, rhoff, mff.ux, mff.uy, mff.uz);
+      // fneq at d, each term rescaled by its density ratio
+      const T nd = rhod * (two_q * neq_f / rhof + ((T)1 - two_q) * neq_ff / rhoff);
+      // u*_d (piecewise linear), u**_d (between x_ff and the wall), weighted 1/3 : 2/3
+      T af, aff, aw;
+      if (q <= (T)0.5) {
+        af = two_q;
+        aff = (T)1 - two_q;
+        aw = 0;
+      } else {
+        const T iq = (T)1 / q;
+        af = ((T)1 - q) * iq;
+        aff = 0;
+        aw = (two_q - (T)1) * iq;
+      }
+      const T i1q = (T)1 / ((T)1 + q);
+      const T bff = ((T)1 - q) * i1q, bw = two_q * i1q;
+      const T third = (T)(1.0 / 3.0), two_thirds = (T)(2.0 / 3.0);
+      const T cf = third * af, cff = third * aff + two_thirds * bff, cw = third * aw + two_thirds * bw;
+      const T udx = cf * mf.ux + cff * mff.ux + cw * uw0;
+      const T udy = cf * mf.uy + cff * mff.uy + cw * uw1;
+      const T udz = cf * mf.uz + cff * mff.uz + cw * uw2;
+      val = eq_dir<P>(w, ex, ey, ez, rd, rhod, udx, udy, udz) + nd + wall;
     }
-    const T val = link_rule<L, P>(rule, ip, q, fpf, fpff, fpi, wall, uw, rf, uf, rff, uff, p.rho0, p.vibb_local_rho);
-    f[(int64_t)i * N + s] = val;
+    f[(size_t)i * N + s] = val;
     if (body >= 0) {
       // momentum exchange (f+_i'(x_f,t) + f_i(x_f,t+1)) e_i', FP64; shifted
       // storage adds back the two rest parts w rho0
-      const double t = (double)fpf + (double)val + (P::shifted ? 2.0 * L::w(ip) * p.rho0 : 0.0);
-      F0 = t * cx;
-      F1 = t * cy;
-      F2 = t * cz;
+      const double t = (double)fpf + (double)val + (P::shifted ? 2.0 * (double)w * p.rho0 : 0.0);
+      F0 = t * (double)ex;
+      F1 = t * (double)ey;
+      F2 = t * (double)ez;
     }
   }
   // block reduction: one atomic per component when the block has one body
@@ -303,27 +341,27 @@ __global__ void __launch_bounds__(256) k_links(typename P::T* __restrict__ f, co
 // with the parabolic velocity u_in(y); outlet column x = nx-1 copies x = nx-2.
 // One thread per row (D2Q9).
 template <class L, class P>
-__global__ void k_open(typename P::T* __restrict__ f, const typename P::T* __restrict__ mom,
+__global__ void k_open(typename P::T* __restrict__ f, const Mom4<typename P::T>* __restrict__ mom,
                        const uint8_t* __restrict__ mask, Params p) {
   using T = typename P::T;
   const int y = blockIdx.x * blockDim.x + threadIdx.x;
   if (y >= p.ny) return;
-  const int64_t N = p.N;
+  const size_t N = (size_t)p.N;
   if (p.inlet) {
-    const int64_t n0 = (int64_t)p.nx * y, n1 = n0 + 1;
+    const uint32_t n0 = (uint32_t)p.nx * y, n1 = n0 + 1;
     if (mask[n0] & M_OPEN) {
       const double h = p.inlet_y1 - p.inlet_y0;
       const T uin = (T)(4.0 * p.inlet_umax * ((double)y - p.inlet_y0) * (p.inlet_y1 - (double)y) / (h * h));
-      const T r1 = mom[n1];
-      const T rho1 = P::shifted ? (T)p.rho0 + r1 : r1;
-      const T ux = mom[N + n1], uy = mom[2 * N + n1];
+      const Mom4<T> m1 = mom[n1];
+      const T rho1 = P::shifted ? (T)p.rho0 + m1.r : m1.r;
 #pragma unroll
       for (int i = 0; i < L::Q; ++i)
-        f[i * N + n0] = equilibrium<L, P>(i, r1, rho1, uin, (T)0, (T)0) + (f[i * N + n1] - equilibrium<L, P>(i, r1, rho1, ux, uy, (T)0));
+        f[i * N + n0] = equilibrium<L, P>(i, m1.r, rho1, uin, (T)0, (T)0) +
+                        (f[i * N + n1] - equilibrium<L, P>(i, m1.r, rho1, m1.ux, m1.uy, (T)0));
     }
   }
   if (p.outlet) {
-    const int64_t n = (int64_t)p.nx * y + p.nx - 1;
+    const uint32_t n = (uint32_t)p.nx * y + p.nx - 1;
     if (mask[n] & M_OPEN) {
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) f[i * N + n] = f[i * N + n - 1];
@@ -337,7 +375,7 @@ __global__ void k_open(typename P::T* __restrict__ f, const typename P::T* __res
 // nodes); zero elsewhere.  rho_in (N) and u_in (N x 3, interleaved) may be
 // null for rho0 and rest.
 template <class L, class P>
-__global__ void k_init(typename P::T* __restrict__ f, typename P::T* __restrict__ mom, const uint8_t* __restrict__ mask,
+__global__ void k_init(typename P::T* __restrict__ f, Mom4<typename P::T>* __restrict__ mom, const uint8_t* __restrict__ mask,
                        const double* __restrict__ rho_in, const double* __restrict__ u_in, Params p) {
   using T = typename P::T;
   const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -358,7 +396,7 @@ __global__ void k_init(typename P::T* __restrict__ f, typename P::T* __restrict_
     const double poly = 3.0 * eu + 4.5 * eu * eu - 1.5 * (ux * ux + uy * uy + uz * uz);
     fl[i] = P::shifted ? (T)(L::w(i) * ((rho - p.rho0) + rho * poly)) : (T)(L::w(i) * rho * (1.0 + poly));
   }
-  collide_store<L, P>(fl, p, f, n, mom, (m & M_CACHE) != 0);
+  collide_store<L, P>(fl, p, f, (uint32_t)n, mom, (m & M_CACHE) != 0);
 }
 
 // rho = sum f+, u = (sum f+ e - g/2)/rho of the post-collision state (the
@@ -396,7 +434,7 @@ __global__ void k_moments(const typename P::T* __restrict__ f, const uint8_t* __
 // the populations): same formula as k_moments, storage precision.
 template <class L, class P>
 __global__ void k_refresh(const typename P::T* __restrict__ f, const uint8_t* __restrict__ mask,
-                          typename P::T* __restrict__ mom, Params p) {
+                          Mom4<typename P::T>* __restrict__ mom, Params p) {
   using T = typename P::T;
   const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (n >= p.N || !(mask[n] & M_CACHE)) return;
@@ -411,10 +449,8 @@ __global__ void k_refresh(const typename P::T* __restrict__ f, const uint8_t* __
     jz += (T)L::cz(i) * v;
   }
   const T rho = P::shifted ? (T)p.rho0 + r : r;
-  mom[n] = r;
-  mom[N + n] = (jx - (T)(0.5 * p.g[0])) / rho;
-  mom[2 * N + n] = (jy - (T)(0.5 * p.g[1])) / rho;
-  if (L::D == 3) mom[3 * N + n] = (jz - (T)(0.5 * p.g[2])) / rho;
+  mom[n] = Mom4<T>{r, (jx - (T)(0.5 * p.g[0])) / rho, (jy - (T)(0.5 * p.g[1])) / rho,
+                   L::D == 3 ? (jz - (T)(0.5 * p.g[2])) / rho : (T)0};
 }
 
 // One direction of the state to/from FP64 unshifted populations.
@@ -509,26 +545,26 @@ struct Launch {
                    cudaStream_t s) {
     const int bx = p.nx >= 256 ? 256 : ((p.nx + 31) / 32) * 32;
     dim3 grid(blocks_for(p.nx, bx), p.ny, p.nz);
-    k_bulk<L, P><<<grid, bx, 0, s>>>((const T*)fin, (T*)fout, mask, (T*)mom, force_next, p);
+    k_bulk<L, P><<<grid, bx, 0, s>>>((const T*)fin, (T*)fout, mask, (Mom4<T>*)mom, force_next, p);
   }
   static void links(void* f, const void* mom, const uint64_t* keys, const void* q, const void* uw, int64_t nl,
                     double* force, const Params& p, cudaStream_t s) {
     if (nl == 0) return;
-    k_links<L, P><<<blocks_for(nl, 256), 256, 0, s>>>((T*)f, (const T*)mom, keys, (const T*)q, (const T*)uw, nl, force,
-                                                     p);
+    k_links<L, P><<<blocks_for(nl, 256), 256, 0, s>>>((T*)f, (const Mom4<T>*)mom, keys, (const T*)q, (const T*)uw, nl,
+                                                     force, p);
   }
   static void open(void* f, const void* mom, const uint8_t* mask, const Params& p, cudaStream_t s) {
-    k_open<L, P><<<blocks_for(p.ny, 128), 128, 0, s>>>((T*)f, (const T*)mom, mask, p);
+    k_open<L, P><<<blocks_for(p.ny, 128), 128, 0, s>>>((T*)f, (const Mom4<T>*)mom, mask, p);
   }
   static void init(void* f, void* mom, const uint8_t* mask, const double* rho, const double* u, const Params& p,
                    cudaStream_t s) {
-    k_init<L, P><<<blocks_for(p.N, 256), 256, 0, s>>>((T*)f, (T*)mom, mask, rho, u, p);
+    k_init<L, P><<<blocks_for(p.N, 256), 256, 0, s>>>((T*)f, (Mom4<T>*)mom, mask, rho, u, p);
   }
   static void moments(const void* f, const uint8_t* mask, double* rho, double* u, const Params& p, cudaStream_t s) {
     k_moments<L, P><<<blocks_for(p.N, 256), 256, 0, s>>>((const T*)f, mask, rho, u, p);
   }
   static void refresh(const void* f, const uint8_t* mask, void* mom, const Params& p, cudaStream_t s) {
-    k_refresh<L, P><<<blocks_for(p.N, 256), 256, 0, s>>>((const T*)f, mask, (T*)mom, p);
+    k_refresh<L, P><<<blocks_for(p.N, 256), 256, 0, s>>>((const T*)f, mask, (Mom4<T>*)mom, p);
   }
   static void get_dir(const void* f, const uint8_t* mask, int i, double* out, const Params& p, cudaStream_t s) {
     k_get_dir<L, P><<<blocks_for(p.N, 256), 256, 0, s>>>((const T*)f, mask, i, out, p);

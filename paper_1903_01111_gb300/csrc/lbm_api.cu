@@ -223,7 +223,7 @@ lbm_status lbm_create_lattice(const lbm_config* cfg, lbm_handle* out) {
   if ((c.inlet || c.outlet) && c.periodic[0]) return fail(LBM_ERR_INVALID_ARG, "open columns need a non-periodic x axis");
   if (c.inlet && !(c.inlet_y1 > c.inlet_y0)) return fail(LBM_ERR_INVALID_ARG, "inlet needs inlet_y1 > inlet_y0");
   const int64_t N = (int64_t)c.nx * c.ny * c.nz;
-  if (N >= ((int64_t)1 << 47)) return fail(LBM_ERR_UNSUPPORTED, "lattice too large");
+  if (N >= ((int64_t)1 << 31)) return fail(LBM_ERR_UNSUPPORTED, "lattices are limited to 2^31 nodes");
 
   lbm_handle h = new (std::nothrow) lbm_lattice_s;
   if (!h) return fail(LBM_ERR_OOM, "host allocation failed");
@@ -266,12 +266,12 @@ lbm_status lbm_create_lattice(const lbm_config* cfg, lbm_handle* out) {
   }
   const size_t fb = (size_t)h->Q * N * h->rb;
   for (int k = 0; k < 2 && st == LBM_OK; ++k) st = dev_alloc(h, &h->f[k], fb);
-  if (st == LBM_OK) st = dev_alloc(h, &h->mom, (size_t)(1 + h->D) * N * h->rb);
+  if (st == LBM_OK) st = dev_alloc(h, &h->mom, (size_t)4 * N * h->rb);
   if (st == LBM_OK) st = dev_alloc(h, (void**)&h->mask, (size_t)N);
   if (st == LBM_OK) st = dev_alloc(h, (void**)&h->force, sizeof(double) * 2 * 3 * MAX_BODIES);
   if (st == LBM_OK) {
     cudaError_t e = cudaMemsetAsync(h->force, 0, sizeof(double) * 2 * 3 * MAX_BODIES, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->mom, 0, (size_t)(1 + h->D) * N * h->rb, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->mom, 0, (size_t)4 * N * h->rb, h->stream);
     if (e != cudaSuccess) st = fail(LBM_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
   }
   if (st != LBM_OK) {
@@ -504,7 +504,7 @@ lbm_status lbm_init_equilibrium(lbm_handle h, const double* rho, const double* u
   if (rho) e = cudaMemcpyAsync(drho, rho, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream);
   if (u && e == cudaSuccess) e = cudaMemcpyAsync(du, u, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) {
-    CUDA_TRY(cudaMemsetAsync(h->mom, 0, (size_t)(1 + h->D) * N * h->rb, h->stream));
+    CUDA_TRY(cudaMemsetAsync(h->mom, 0, (size_t)4 * N * h->rb, h->stream));
     h->ops.init(h->f[0], h->mom, h->mask, drho, du, h->p, h->stream);
     e = cudaGetLastError();
   }
