@@ -179,9 +179,8 @@ def run_precision(lbm, torch, geo, precision, steps, warmup, dist, peak):
     return {
         "mlups": mlups, "ms_per_step": ms / steps, "n_fluid": nf, "n_links": nl, "n_nodes": N,
         "launches": int(sum(n_launch)), "force": F.tolist(),
-        "roofline": {"bound": "hbm", "achieved": bulk_gbs, "peak": peak, "unit": "GB/s", "frac": bulk_gbs / peak,
-                     "traffic": None, "kernel": "k_bulk", "bytes_per_launch": bulk_bytes,
-                     "avg_launch_ms": bulk_ms},
+        "roofline": dict(roofline_entry(bulk_bytes, nf * FLOPS_PER_NODE[Q3], bulk_ms, s, peak), kernel="k_bulk",
+                         bytes_per_launch=bulk_bytes, avg_launch_ms=bulk_ms),
         "kernels": {
             "k_bulk": {"launches": n_launch[2], "avg_ms": bulk_ms, "share": kms[2] / max(sum(kms), 1e-30),
                        "gbs": bulk_gbs, "bytes_per_launch": bulk_bytes},
@@ -190,6 +189,62 @@ def run_precision(lbm, torch, geo, precision, steps, warmup, dist, peak):
         },
         "step_gbs": (bulk_bytes + link_bytes) / (ms / steps * 1e-3) / 1e9,
     }
+
+
+# FP64 arithmetic peak of GB300, from unit counts and clock: 152 SMs x 2 FP64
+# FMA per clock per SM x 2 flops x 2.07 GHz = 1.26 TFLOP/s (nominal 1.25).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# Algorithmic FP64 flops of one BGK + Guo node update (FMA = 2): moments
+# (Q-1 adds for rho, 3 x (Q_nonzero - 1) for j, 7 for u), 11 for |u|^2 and
+# u.g, and per direction 16 (e.u, polynomial, equilibrium, relaxation, Guo).
+FLOPS_PER_NODE = {9: 8 + 3 * 5 + 7 + 11 + 9 * 16, 19: 18 + 3 * 9 + 7 + 11 + 19 * 16}
+
+
+def roofline_entry(bytes_per_launch, flops_per_launch, avg_ms, s, peak_gbs):
+    gbs = bytes_per_launch / (avg_ms * 1e-3) / 1e9
+    if s == 8:
+        tf = flops_per_launch / (avg_ms * 1e-3) / 1e12
+        return {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tf / FP64_PEAK_TFLOPS, "traffic": None, "hbm_gbs": gbs, "hbm_frac": gbs / peak_gbs,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz"}
+    return {"bound": "hbm", "achieved": gbs, "peak": peak_gbs, "unit": "GB/s", "frac": gbs / peak_gbs,
+            "traffic": None}
+
+
+def run_sweep(lbm, torch, steps, peak):
+    """No-solid periodic lattices: D2Q9 16384 x 8192 and D3Q19 384^3, FP32
+    shifted and FP64; the bulk kernel's roofline on each."""
+    from paper_1903_01111_gb300 import geometry as G
+
+    out = {}
+    for name, stencil, shape in (("d2q9_16384x8192", 0, (16384, 8192, 1)), ("d3q19_384^3", 1, (384, 384, 384))):
+        geo = G.build(stencil, shape, (1, 1, 1), [])
+        Q = 9 if stencil == 0 else 19
+        for prec, s in ((lbm.LBM_FP32_SHIFTED, 4), (lbm.LBM_FP64, 8)):
+            stream = torch.cuda.Stream()
+            lat = lbm.Lattice(geo, precision=prec, tau=0.7, g=(1e-6, 0.0, 0.0), bc=0, stream=stream.cuda_stream)
+            lat.init_equilibrium()
+            n = steps if s == 4 else max(10, steps // 5)
+            lat.step(3)
+            torch.cuda.synchronize()
+            lbm.lbm_set_profiling(lat.h, True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lat.step(n)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            nl, kms = lbm.lbm_kernel_times(lat.h)
+            lbm.lbm_set_profiling(lat.h, False)
+            lat.check()
+            nf = lat.info().n_fluid
+            lat.close()
+            bulk_ms = kms[2] / max(nl[2], 1)
+            r = roofline_entry(nf * (2 * Q * s + 1), nf * FLOPS_PER_NODE[Q], bulk_ms, s, peak)
+            out[f"{name}_{'fp32s' if s == 4 else 'fp64'}"] = {
+                "mlups": nf * n / (ms * 1e-3) / 1e6, "ms_per_step": ms / n, "steps": n,
+                "bytes_per_node": 2 * Q * s + 1, "bulk_avg_ms": bulk_ms, "roofline": r}
+    return out
 
 
 def run_e2e(lbm, torch, geo, steps):
@@ -284,6 +339,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--sweep-steps", type=int, default=100)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -313,6 +370,7 @@ def main():
         r64 = run_precision(lbm, torch, geo, lbm.LBM_FP64, args.steps, args.warmup, dist, peak)
         r64["clocks"] = clocks64.stop()
     e2e = None if args.no_e2e else run_e2e(lbm, torch, geo, args.steps)
+    sweep = None if args.no_sweep else run_sweep(lbm, torch, args.sweep_steps, peak)
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = run_oracle(96, 16)
@@ -329,14 +387,17 @@ def main():
                    "l2": "inputs larger than L2 (state > 8 GB), no flush", "parallelism": "replicas",
                    "geometry_build_s": t_geo},
         "roofline": dict(r32["roofline"], peak_source=peak_src),
+        "hbm_peak_source": peak_src,
         "kernels": r32["kernels"], "step_gbs": r32["step_gbs"],
         "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": r32["launches"],
         "clocks": ck,
     }
+    if sweep is not None:
+        line["roofline_sweep"] = sweep
     if r64 is not None:
         line["fp64"] = {"value": r64["mlups"], "unit": "MLUPS", "ms_per_step": r64["ms_per_step"],
-                        "roofline": dict(r64["roofline"], peak_source=peak_src), "kernels": r64["kernels"],
+                        "roofline": r64["roofline"], "kernels": r64["kernels"],
                         "step_gbs": r64["step_gbs"], "gpu_launches": r64["launches"], "clocks": r64["clocks"]}
     print(json.dumps(line), flush=True)
     return 0

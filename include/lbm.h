@@ -124,6 +124,8 @@ typedef struct {
   int64_t n_nodes, n_fluid, n_links, n_cached, step;
   int64_t device_bytes;  /* device memory the lattice holds */
   int32_t Q, D, precision, real_bytes;
+  int64_t n_stored;      /* nodes with storage: fluid, open-column and ghost nodes */
+  int64_t n_runs;        /* runs of consecutive fluid nodes along x */
 } lbm_info;
 
 /* Create a lattice: validates cfg, allocates the device state (two

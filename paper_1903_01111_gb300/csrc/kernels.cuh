@@ -5,20 +5,28 @@
 //   F32S -- populations stored in float as h_i = f_i - w_i rho0 ("shifted"),
 //           so the O(1) rest part w_i rho0 never enters a float rounding.
 //
-// Storage: SoA  f[i*N + n], n = x + nx*(y + ny*z).  The buffer read by a
-// step holds the post-collision populations f+(t) of every fluid node; the
-// solid nodes' slots serve as ghost cells that the link kernel fills with
-// the missing populations before the bulk kernel pulls them.
+// Storage (compacted): only fluid nodes, open-column nodes and ghost nodes
+// (solid nodes that receive a link's missing population) are stored, in
+// x-row order; k is the storage index, S their number.  SoA f[i*S + k].
+// A fluid run (maximal x-run of fluid nodes in one row) has every node of
+// its neighbour rows over [x0 - 1, x_end + 1] stored and contiguous, so one
+// run record (the storage index of (x0, row') for each neighbour row)
+// addresses every pull; pulls across the periodic x seam use the row's first
+// and last storage index.  The buffer read by a step holds f+(t) of every
+// fluid node; ghost slots are filled by the link kernel before the bulk
+// kernel pulls them.
 //
 // Step t -> t+1 (three launches on one stream):
 //   k_links: per cut link (x_f, i'), the missing f_i(x_f, t+1), i = opp(i'),
 //            from f+ and the moment cache at x_f and x_ff (Sec. 3 and 3.1),
-//            written to f[i][x_f + e_i'] (the solid neighbour's slot, read
-//            only by x_f); momentum exchange force in FP64.
+//            written to the ghost slot f[i][k_s] (read only by x_f);
+//            momentum exchange force in FP64.
 //   k_open:  inlet/outlet columns (Sec. 4.3), D2Q9 only.
 //   k_bulk:  pull streaming f_i(x, t+1) = f+_i(x - e_i, t) (Eq. 1), moments,
 //            Guo-forced BGK (Sec. 2, Eq. feq) -> f+(t+1) into the other
-//            buffer; rho, u(t+1) into the moment cache where flagged.
+//            buffer; rho, u(t+1) into the moment cache where flagged.  Ghost
+//            and open slots of the output get zeros so that every written
+//            sector is complete.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -44,6 +52,41 @@ struct __align__(4 * sizeof(T)) Mom4 {
   T r, ux, uy, uz;
 };
 
+// Per stored node word: run id of a fluid node, or the open / ghost bit.
+constexpr uint32_t W_RUN = (1u << 29) - 1;
+constexpr uint32_t W_CACHE = 1u << 29;
+constexpr uint32_t W_OPEN = 1u << 30;
+constexpr uint32_t W_GHOST = 1u << 31;
+
+// One fluid run: x0, its storage index k0, its row (y, z), and for each
+// neighbour row (slot order below) the storage index of (x0, row').
+struct __align__(16) RunRec {
+  int32_t x0, k0, y, z;
+  int32_t base[8];
+};
+
+// Neighbour-row slots by source-row offset (dy, dz).  D2Q9: (1,0), (-1,0).
+// D3Q19: (1,0), (-1,0), (0,1), (0,-1), (1,1), (-1,-1), (1,-1), (-1,1).
+__host__ __device__ constexpr int row_slot(int dy, int dz) {
+  return dz == 0 ? (dy > 0 ? 0 : 1)
+                 : (dy == 0 ? (dz > 0 ? 2 : 3) : (dy == dz ? (dy > 0 ? 4 : 5) : (dy > 0 ? 6 : 7)));
+}
+
+struct Layout {
+  int64_t S;                   // stored nodes
+  const uint32_t* word;        // [S]
+  const int32_t* node_of;      // [S] dense node index
+  const RunRec* runs;
+  const int32_t* row_first;    // [ny*nz] storage index of the row's first stored node (-1: none)
+  const int32_t* row_last;     // [ny*nz] ... last stored node
+};
+
+// One link: storage indices of x_f, x_ff (x_f if no second fluid node) and
+// the ghost x_s; meta = dir | rule << 5 | (body + 1) << 7.
+struct __align__(16) LinkRec {
+  uint32_t kf, kff, ks, meta;
+};
+
 // --------------------------------------------------------------- helpers --
 
 // Equilibrium of Eq. (feq), C = 1, in storage form: r is rho (F64) or
@@ -67,7 +110,7 @@ __device__ __forceinline__ int src_coord(int c, int x, int xm, int xp) { return 
 // populations f(x, t+1) in storage form; n < 2^31.
 template <class L, class P>
 __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Params& p, typename P::T* __restrict__ fout,
-                                              uint32_t n, Mom4<typename P::T>* __restrict__ mom, bool cache) {
+                                              size_t S, uint32_t n_, Mom4<typename P::T>* __restrict__ mom, bool cache) {
   using T = typename P::T;
   T r = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
@@ -85,60 +128,124 @@ __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Pa
   const T inv = (T)1 / rho;
   // Guo forcing: velocity shifted by half the body force
   const T ux = (jx + (T)0.5 * gx) * inv, uy = (jy + (T)0.5 * gy) * inv, uz = (jz + (T)0.5 * gz) * inv;
-  if (cache) mom[n] = Mom4<T>{r, ux, uy, L::D == 3 ? uz : (T)0};
-  const T omega = (T)(1.0 / p.tau);
+  if (cache) mom[n_] = Mom4<T>{r, ux, uy, L::D == 3 ? uz : (T)0};
+  const T omega = (T)p.omega;
   const T uu15 = (T)1.5 * (ux * ux + uy * uy + uz * uz);
+  if constexpr (L::Q == 9) {
+    if (p.collision == 1) {
+      // MRT (Sec. 2, Eq. mrt) on the non-equilibrium part n = f - feq, whose
+      // moments are m - meq (meq = M feq, the moments of the BGK
+      // equilibrium); Guo source in moment space scaled by (1 - s_k/2).
+      const T gx_ = gx, gy_ = gy;
+      const T ug2 = ux * gx_ + uy * gy_;
+      T n[9], src[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const T eu = (T)L::cx(i) * ux + (T)L::cy(i) * uy;
+        const T w = (T)L::w(i);
+        const T poly = (T)3 * eu + (T)4.5 * eu * eu - uu15;
+        const T feq = P::shifted ? w * (r + rho * poly) : (w * rho) * ((T)1 + poly);
+        n[i] = f[i] - feq;
+        const T eg = (T)L::cx(i) * gx_ + (T)L::cy(i) * gy_;
+        src[i] = p.has_force ? w * ((T)3 * (eg - ug2) + (T)9 * eu * eg) : (T)0;
+      }
+      T dm[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        T mn = 0, ms = 0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          if (mrt_m(k, i) != 0) {
+            mn += (T)mrt_m(k, i) * n[i];
+            ms += (T)mrt_m(k, i) * src[i];
+          }
+        }
+        const T sk = (k == 7 || k == 8) ? omega : (T)((k == 0 || k == 3 || k == 5) ? 0.3 : (k == 1 || k == 2) ? 1.5 : 1.2);
+        dm[k] = (sk * mn - ((T)1 - (T)0.5 * sk) * ms) / (T)mrt_norm2(k);
+      }
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        T d = 0;
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+          if (mrt_m(k, i) != 0) d += (T)mrt_m(k, i) * dm[k];
+        fout[(size_t)i * S + n_] = f[i] - d;
+      }
+      return;
+    }
+  }
   // Guo source (1 - 1/(2 tau)) w_i [3 (e_i - u).g + 9 (e_i.u)(e_i.g)]
   //   = 3 (1 - 1/(2 tau)) w_i [(e_i.g)(1 + 3 e_i.u) - u.g]
-  const T fpre3 = (T)(3.0 * (1.0 - 0.5 / p.tau));
+  const T fpre3 = (T)p.fpre3;
   const T ug = ux * gx + uy * gy + uz * gz;
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
     const T eu = (T)L::cx(i) * ux + (T)L::cy(i) * uy + (T)L::cz(i) * uz;
     const T w = (T)L::w(i);
     const T poly = (T)3 * eu + (T)4.5 * eu * eu - uu15;
-    const T feq = P::shifted ? w * (r + rho * poly) : w * rho * ((T)1 + poly);
+    const T feq = P::shifted ? w * (r + rho * poly) : (w * rho) * ((T)1 + poly);
     T out = f[i] + omega * (feq - f[i]);
     if (p.has_force) {
       const T eg = (T)L::cx(i) * gx + (T)L::cy(i) * gy + (T)L::cz(i) * gz;
       out += fpre3 * w * (eg * ((T)1 + (T)3 * eu) - ug);
     }
-    fout[(size_t)i * p.N + n] = out;
+    fout[(size_t)i * S + n_] = out;
   }
 }
 
 // ------------------------------------------------------------------ bulk --
 
-// One thread per node of an x-row segment; grid (ceil(nx/bx), ny, nz).
-// Block (0,0,0) also clears the force slot of the next step.
+// One thread per stored node; block (0) also clears the force slot of the
+// next step.
 template <class L, class P>
 __global__ void __launch_bounds__(256) k_bulk(const typename P::T* __restrict__ fin, typename P::T* __restrict__ fout,
-                                              const uint8_t* __restrict__ mask, Mom4<typename P::T>* __restrict__ mom,
+                                              Layout lay, Mom4<typename P::T>* __restrict__ mom,
                                               double* __restrict__ force_next, Params p) {
   using T = typename P::T;
-  if (force_next && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0)
+  if (force_next && blockIdx.x == 0)
     for (int t = threadIdx.x; t < 3 * MAX_BODIES; t += blockDim.x) force_next[t] = 0.0;
-  const uint32_t x = blockIdx.x * blockDim.x + threadIdx.x;
-  const uint32_t y = blockIdx.y, z = blockIdx.z;
-  const uint32_t nx = p.nx, nxy = (uint32_t)p.nx * (uint32_t)p.ny;
-  if (x >= nx) return;
-  const uint32_t row = nx * y + nxy * z;
-  const uint32_t n = x + row;
-  const uint8_t m = mask[n];
-  if (m & (M_SOLID | M_OPEN)) return;
-  // wrapped neighbour coordinates as row/plane offsets (32-bit)
-  const uint32_t xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-  const uint32_t ym = (y == 0 ? p.ny - 1 : y - 1) * nx, y0 = y * nx, yp = (y == (uint32_t)p.ny - 1 ? 0 : y + 1) * nx;
-  const uint32_t zm = (z == 0 ? p.nz - 1 : z - 1) * nxy, z0 = z * nxy, zp = (z == (uint32_t)p.nz - 1 ? 0 : z + 1) * nxy;
+  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= (uint64_t)lay.S) return;
+  const size_t S = (size_t)lay.S;
+  const uint32_t w = __ldg(lay.word + k);
+  if (w & (W_GHOST | W_OPEN)) {
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) fout[(size_t)i * S + k] = (T)0;
+    return;
+  }
+  const RunRec run = lay.runs[w & W_RUN];
+  const int nx = p.nx;
+  const int x = run.x0 + (int)(k - (uint32_t)run.k0);
+  const bool left = x == 0, right = x == nx - 1;
   T f[L::Q];
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
-    const uint32_t sx = L::cx(i) == 0 ? x : (L::cx(i) > 0 ? xm : xp);
-    const uint32_t sy = L::cy(i) == 0 ? y0 : (L::cy(i) > 0 ? ym : yp);
-    const uint32_t sz = L::cz(i) == 0 ? z0 : (L::cz(i) > 0 ? zm : zp);
-    f[i] = __ldg(fin + (size_t)i * p.N + (sx + sy + sz));
+    // source x - e_i: offsets (dx, dy, dz) = -(cx, cy, cz)
+    const int dx = -L::cx(i), dy = -L::cy(i), dz = -L::cz(i);
+    uint32_t src;
+    if (dy == 0 && dz == 0) {
+      if (dx == 0) {
+        src = k;
+      } else if ((dx < 0 && left) || (dx > 0 && right)) {
+        const int row = run.y + p.ny * run.z;
+        src = (uint32_t)(dx < 0 ? lay.row_last[row] : lay.row_first[row]);
+      } else {
+        src = k + dx;
+      }
+    } else {
+      if ((dx < 0 && left) || (dx > 0 && right)) {
+        int yy = run.y + dy, zz = run.z + dz;
+        yy = yy < 0 ? yy + p.ny : (yy >= p.ny ? yy - p.ny : yy);
+        zz = zz < 0 ? zz + p.nz : (zz >= p.nz ? zz - p.nz : zz);
+        const int row = yy + p.ny * zz;
+        src = (uint32_t)(dx < 0 ? lay.row_last[row] : lay.row_first[row]);
+      } else {
+        src = (uint32_t)(run.base[row_slot(dy, dz)] + (x + dx - run.x0));
+      }
+    }
+    f[i] = __ldg(fin + (size_t)i * S + src);
   }
-  collide_store<L, P>(f, p, fout, n, mom, (m & M_CACHE) != 0);
+  collide_store<L, P>(f, p, fout, S, k, mom, (w & W_CACHE) != 0);
 }
 
 // ----------------------------------------------------------------- links --
@@ -164,9 +271,60 @@ __device__ __forceinline__ typename P::T eq_dir(typename P::T w, typename P::T e
   return P::shifted ? w * (r + rho * poly) : w * rho * ((T)1 + poly);
 }
 
-// One thread per link.  keys: packed (node, dir, rule, ff fallback, wrap,
-// body); qv: q in storage precision; uw: [D][nl] wall velocities or null.
-// force: the step's accumulator slot [MAX_BODIES][3] (FP64).
+// Missing population f_i(x_f, t+1) of one link in storage form (see the
+// rule list below).  fpf = f+_i'(x_f), fpff = f+_i'(x_ff), fpi = f+_i(x_f)
+// (only read by the rule that needs it, through the callbacks' values);
+// mf, mff: moments at time t at x_f and x_ff; (w, ex, ey, ez) of i'.
+template <class P>
+__device__ __forceinline__ typename P::T link_value(int rule, typename P::T q, typename P::T w, typename P::T ex,
+                                                    typename P::T ey, typename P::T ez, typename P::T fpf,
+                                                    typename P::T fpff, typename P::T fpi, const Mom4<typename P::T>& mf,
+                                                    const Mom4<typename P::T>& mff, typename P::T uw0,
+                                                    typename P::T uw1, typename P::T uw2, double rho0, int local_rho) {
+  using T = typename P::T;
+  // 6 w_i' rho0 (e_i . u_w) with e_i = -e_i'
+  const T wall = -(T)6 * w * (T)rho0 * (ex * uw0 + ey * uw1 + ez * uw2);
+  const T two_q = (T)2 * q;
+  if (rule == 0) return fpf + wall;
+  if (rule == 1) {
+    if (q <= (T)0.5) return two_q * fpf + ((T)1 - two_q) * fpff + wall;
+    const T inv2q = (T)1 / two_q;
+    return (fpf + wall) * inv2q + (two_q - (T)1) * inv2q * fpi;
+  }
+  const T rhof = P::shifted ? (T)rho0 + mf.r : mf.r;
+  const T rhoff = P::shifted ? (T)rho0 + mff.r : mff.r;
+  // Eq. (rhod) in storage form; optionally rho_d = rho_f when q > 1/2
+  const T rd = (local_rho && q > (T)0.5) ? mf.r : two_q * mf.r + ((T)1 - two_q) * mff.r;
+  const T rhod = P::shifted ? (T)rho0 + rd : rd;
+  const T neq_f = fpf - eq_dir<P>(w, ex, ey, ez, mf.r, rhof, mf.ux, mf.uy, mf.uz);
+  const T neq_ff = fpff - eq_dir<P>(w, ex, ey, ez, mff.r, rhoff, mff.ux, mff.uy, mff.uz);
+  // fneq at d, each term rescaled by its density ratio
+  const T nd = rhod * (two_q * neq_f / rhof + ((T)1 - two_q) * neq_ff / rhoff);
+  // u*_d (piecewise linear), u**_d (between x_ff and the wall), weighted 1/3 : 2/3
+  T af, aff, aw;
+  if (q <= (T)0.5) {
+    af = two_q;
+    aff = (T)1 - two_q;
+    aw = 0;
+  } else {
+    const T iq = (T)1 / q;
+    af = ((T)1 - q) * iq;
+    aff = 0;
+    aw = (two_q - (T)1) * iq;
+  }
+  const T i1q = (T)1 / ((T)1 + q);
+  const T bff = ((T)1 - q) * i1q, bw = two_q * i1q;
+  const T third = (T)(1.0 / 3.0), two_thirds = (T)(2.0 / 3.0);
+  const T cf = third * af, cff = third * aff + two_thirds * bff, cw = third * aw + two_thirds * bw;
+  const T udx = cf * mf.ux + cff * mff.ux + cw * uw0;
+  const T udy = cf * mf.uy + cff * mff.uy + cw * uw1;
+  const T udz = cf * mf.uz + cff * mff.uz + cw * uw2;
+  return eq_dir<P>(w, ex, ey, ez, rd, rhod, udx, udy, udz) + nd + wall;
+}
+
+// One thread per link.  recs: storage indices and metadata; qv: q in
+// storage precision; uw: [D][nl] wall velocities or null.  force: the step's
+// accumulator slot [MAX_BODIES][3] (FP64).
 //
 // Rules (storage form; the rest part w rho0 cancels because every rule's
 // weights sum to one):
@@ -177,14 +335,14 @@ __device__ __forceinline__ typename P::T eq_dir(typename P::T w, typename P::T e
 // with wall = 6 w rho0 (e_i . u_w).
 template <class L, class P>
 __global__ void __launch_bounds__(256) k_links(typename P::T* __restrict__ f, const Mom4<typename P::T>* __restrict__ mom,
-                                               const uint64_t* __restrict__ keys, const typename P::T* __restrict__ qv,
+                                               const LinkRec* __restrict__ recs, const typename P::T* __restrict__ qv,
                                                const typename P::T* __restrict__ uwv, int64_t nl,
-                                               double* __restrict__ force, Params p) {
+                                               double* __restrict__ force, Params p, int64_t S_) {
   using T = typename P::T;
   __shared__ DirTable<T, L::Q> tab;
   if (threadIdx.x < L::Q) {
     const int d = threadIdx.x;
-    tab.off[d] = L::cx(d) + p.nx * (L::cy(d) + p.ny * L::cz(d));
+    tab.off[d] = 0;
     tab.opp[d] = L::opp(d);
     tab.w[d] = (T)L::w(d);
     tab.e[d][0] = (T)L::cx(d);
@@ -196,32 +354,15 @@ __global__ void __launch_bounds__(256) k_links(typename P::T* __restrict__ f, co
   double F0 = 0.0, F1 = 0.0, F2 = 0.0;
   int body = -1;
   if (k < nl) {
-    const uint64_t key = keys[k];
-    const int ip = (int)(key & 31);
-    const int rule = (int)((key >> 5) & 3);
-    const int fb = (int)((key >> 7) & 1);
-    const int wrap = (int)((key >> 8) & 1);
-    body = (int)((key >> 9) & 127) - 1;
-    const uint32_t node = (uint32_t)(key >> KEY_NODE_SHIFT);
+    const LinkRec rec = recs[k];
+    const int ip = (int)(rec.meta & 31);
+    const int rule = (int)((rec.meta >> 5) & 3);
+    body = (int)((rec.meta >> 7) & 127) - 1;
+    const uint32_t node = rec.kf, ff = rec.kff, s = rec.ks;
     const int i = tab.opp[ip];
     const T ex = tab.e[ip][0], ey = tab.e[ip][1], ez = tab.e[ip][2];
     const T w = tab.w[ip];
-    const size_t N = (size_t)p.N;
-    uint32_t s, ff;
-    if (!wrap) {
-      const uint32_t o = (uint32_t)tab.off[ip];
-      s = node + o;
-      ff = node - o;
-    } else {
-      const uint32_t nx = p.nx, ny = p.ny, nz = p.nz;
-      const uint32_t x = node % nx, y = (node / nx) % ny, z = node / (nx * ny);
-      const int cx = (int)ex, cy = (int)ey, cz = (int)ez;
-      const uint32_t xs = (x + cx + nx) % nx, ys = (y + cy + ny) % ny, zs = (z + cz + nz) % nz;
-      const uint32_t xf = (x - cx + nx) % nx, yf = (y - cy + ny) % ny, zf = (z - cz + nz) % nz;
-      s = xs + nx * (ys + ny * zs);
-      ff = xf + nx * (yf + ny * zf);
-    }
-    if (fb) ff = node;
+    const size_t N = (size_t)S_;
     const T q = qv[k];
     T uw0 = 0, uw1 = 0, uw2 = 0;
     if (uwv) {
@@ -229,54 +370,21 @@ __global__ void __launch_bounds__(256) k_links(typename P::T* __restrict__ f, co
       uw1 = uwv[nl + k];
       if (L::D == 3) uw2 = uwv[2 * nl + k];
     }
-    // 6 w_i' rho0 (e_i . u_w) with e_i = -e_i'
-    const T wall = -(T)6 * w * (T)p.rho0 * (ex * uw0 + ey * uw1 + ez * uw2);
     const T fpf = f[(size_t)ip * N + node];
-    const T two_q = (T)2 * q;
-    T val;
-    if (rule == 0) {
-      val = fpf + wall;
-    } else if (rule == 1) {
-      if (q <= (T)0.5) {
-        val = two_q * fpf + ((T)1 - two_q) * f[(size_t)ip * N + ff] + wall;
-      } else {
-        const T fpi = f[(size_t)i * N + node];
-        const T inv2q = (T)1 / two_q;
-        val = (fpf + wall) * inv2q + (two_q - (T)1) * inv2q * fpi;
-      }
-    } else {
-      const T fpff = f[(size_t)ip * N + ff];
-      const Mom4<T> mf = mom[node], mff = mom[ff];
-      const T rhof = P::shifted ? (T)p.rho0 + mf.r : mf.r;
-      const T rhoff = P::shifted ? (T)p.rho0 + mff.r : mff.r;
-      // Eq. (rhod) in storage form; optionally rho_d = rho_f when q > 1/2
-      const T rd = (p.vibb_local_rho && q > (T)0.5) ? mf.r : two_q * mf.r + ((T)1 - two_q) * mff.r;
-      const T rhod = P::shifted ? (T)p.rho0 + rd : rd;
-      const T neq_f = fpf - eq_dir<P>(w, ex, ey, ez, mf.r, rhof, mf.ux, mf.uy, mf.uz);
-      const T neq_ff = fpff - eq_dir<P>(w, ex, ey, ez, mff.r, rhoff, mff.ux, mff.uy, mff.uz);
-      // fneq at d, each term rescaled by its density ratio
-      const T nd = rhod * (two_q * neq_f / rhof + ((T)1 - two_q) * neq_ff / rhoff);
-      // u*_d (piecewise linear), u**_d (between x_ff and the wall), weighted 1/3 : 2/3
-      T af, aff, aw;
-      if (q <= (T)0.5) {
-        af = two_q;
-        aff = (T)1 - two_q;
-        aw = 0;
-      } else {
-        const T iq = (T)1 / q;
-        af = ((T)1 - q) * iq;
-        aff = 0;
-        aw = (two_q - (T)1) * iq;
-      }
-      const T i1q = (T)1 / ((T)1 + q);
-      const T bff = ((T)1 - q) * i1q, bw = two_q * i1q;
-      const T third = (T)(1.0 / 3.0), two_thirds = (T)(2.0 / 3.0);
-      const T cf = third * af, cff = third * aff + two_thirds * bff, cw = third * aw + two_thirds * bw;
-      const T udx = cf * mf.ux + cff * mff.ux + cw * uw0;
-      const T udy = cf * mf.uy + cff * mff.uy + cw * uw1;
-      const T udz = cf * mf.uz + cff * mff.uz + cw * uw2;
-      val = eq_dir<P>(w, ex, ey, ez, rd, rhod, udx, udy, udz) + nd + wall;
+    T fpff = 0, fpi = 0;
+    Mom4<T> mf{0, 0, 0, 0}, mff{0, 0, 0, 0};
+    if (rule == 1) {
+      if (q <= (T)0.5)
+        fpff = f[(size_t)ip * N + ff];
+      else
+        fpi = f[(size_t)i * N + node];
+    } else if (rule == 2) {
+      fpff = f[(size_t)ip * N + ff];
+      mf = mom[node];
+      mff = mom[ff];
     }
+    const T val = link_value<P>(rule, q, w, ex, ey, ez, fpf, fpff, fpi, mf, mff, uw0, uw1, uw2, p.rho0,
+                                p.vibb_local_rho);
     f[(size_t)i * N + s] = val;
     if (body >= 0) {
       // momentum exchange (f+_i'(x_f,t) + f_i(x_f,t+1)) e_i', FP64; shifted
@@ -339,53 +447,59 @@ __global__ void __launch_bounds__(256) k_links(typename P::T* __restrict__ f, co
 
 // Sec. 4.3: inlet column x = 0 by non-equilibrium extrapolation from x = 1
 // with the parabolic velocity u_in(y); outlet column x = nx-1 copies x = nx-2.
-// One thread per row (D2Q9).
+// One thread per row (D2Q9); the open node is the first (inlet) or last
+// (outlet) stored node of its row and its fluid neighbour is adjacent.
 template <class L, class P>
-__global__ void k_open(typename P::T* __restrict__ f, const Mom4<typename P::T>* __restrict__ mom,
-                       const uint8_t* __restrict__ mask, Params p) {
+__global__ void k_open(typename P::T* __restrict__ f, const Mom4<typename P::T>* __restrict__ mom, Layout lay,
+                       Params p) {
   using T = typename P::T;
   const int y = blockIdx.x * blockDim.x + threadIdx.x;
   if (y >= p.ny) return;
-  const size_t N = (size_t)p.N;
+  const size_t S = (size_t)lay.S;
   if (p.inlet) {
-    const uint32_t n0 = (uint32_t)p.nx * y, n1 = n0 + 1;
-    if (mask[n0] & M_OPEN) {
+    const int32_t k0 = lay.row_first[y];
+    if (k0 >= 0 && (lay.word[k0] & W_OPEN)) {
+      const uint32_t k1 = (uint32_t)k0 + 1;
       const double h = p.inlet_y1 - p.inlet_y0;
       const T uin = (T)(4.0 * p.inlet_umax * ((double)y - p.inlet_y0) * (p.inlet_y1 - (double)y) / (h * h));
-      const Mom4<T> m1 = mom[n1];
+      const Mom4<T> m1 = mom[k1];
       const T rho1 = P::shifted ? (T)p.rho0 + m1.r : m1.r;
 #pragma unroll
       for (int i = 0; i < L::Q; ++i)
-        f[i * N + n0] = equilibrium<L, P>(i, m1.r, rho1, uin, (T)0, (T)0) +
-                        (f[i * N + n1] - equilibrium<L, P>(i, m1.r, rho1, m1.ux, m1.uy, (T)0));
+        f[i * S + k0] = equilibrium<L, P>(i, m1.r, rho1, uin, (T)0, (T)0) +
+                        (f[i * S + k1] - equilibrium<L, P>(i, m1.r, rho1, m1.ux, m1.uy, (T)0));
     }
   }
   if (p.outlet) {
-    const uint32_t n = (uint32_t)p.nx * y + p.nx - 1;
-    if (mask[n] & M_OPEN) {
+    const int32_t kl = lay.row_last[y];
+    if (kl >= 0 && (lay.word[kl] & W_OPEN)) {
 #pragma unroll
-      for (int i = 0; i < L::Q; ++i) f[i * N + n] = f[i * N + n - 1];
+      for (int i = 0; i < L::Q; ++i) f[i * S + kl] = f[i * S + kl - 1];
     }
   }
 }
 
 // ------------------------------------------------------- init and fields --
 
+__device__ __forceinline__ bool is_fluid(uint32_t w) { return (w & (W_GHOST | W_OPEN)) == 0; }
+
 // f(x,0) = feq(rho_in, u_in) followed by the collision at t = 0 (fluid
-// nodes); zero elsewhere.  rho_in (N) and u_in (N x 3, interleaved) may be
-// null for rho0 and rest.
+// nodes); zero elsewhere.  rho_in (N) and u_in (N x 3, interleaved), dense
+// indices, may be null for rho0 and rest.
 template <class L, class P>
-__global__ void k_init(typename P::T* __restrict__ f, Mom4<typename P::T>* __restrict__ mom, const uint8_t* __restrict__ mask,
+__global__ void k_init(typename P::T* __restrict__ f, Mom4<typename P::T>* __restrict__ mom, Layout lay,
                        const double* __restrict__ rho_in, const double* __restrict__ u_in, Params p) {
   using T = typename P::T;
-  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (n >= p.N) return;
-  const uint8_t m = mask[n];
-  if (m & (M_SOLID | M_OPEN)) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= lay.S) return;
+  const size_t S = (size_t)lay.S;
+  const uint32_t w = lay.word[k];
+  if (!is_fluid(w)) {
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) f[(int64_t)i * p.N + n] = (T)0;
+    for (int i = 0; i < L::Q; ++i) f[(size_t)i * S + k] = (T)0;
     return;
   }
+  const int64_t n = lay.node_of[k];
   const double rho = rho_in ? rho_in[n] : p.rho0;
   const double ux = u_in ? u_in[3 * n] : 0.0, uy = u_in ? u_in[3 * n + 1] : 0.0;
   const double uz = (u_in && L::D == 3) ? u_in[3 * n + 2] : 0.0;
@@ -396,28 +510,24 @@ __global__ void k_init(typename P::T* __restrict__ f, Mom4<typename P::T>* __res
     const double poly = 3.0 * eu + 4.5 * eu * eu - 1.5 * (ux * ux + uy * uy + uz * uz);
     fl[i] = P::shifted ? (T)(L::w(i) * ((rho - p.rho0) + rho * poly)) : (T)(L::w(i) * rho * (1.0 + poly));
   }
-  collide_store<L, P>(fl, p, f, (uint32_t)n, mom, (m & M_CACHE) != 0);
+  collide_store<L, P>(fl, p, f, S, (uint32_t)k, mom, (w & W_CACHE) != 0);
 }
 
 // rho = sum f+, u = (sum f+ e - g/2)/rho of the post-collision state (the
-// collision conserves mass and adds g to the momentum); FP64 output, zero
-// at solid and open nodes.  u: [D][N].
+// collision conserves mass and adds g to the momentum); FP64 output at dense
+// indices (the caller zeroes the outputs first).  u: [D][N].
 template <class L, class P>
-__global__ void k_moments(const typename P::T* __restrict__ f, const uint8_t* __restrict__ mask,
-                          double* __restrict__ rho_out, double* __restrict__ u_out, Params p) {
+__global__ void k_moments(const typename P::T* __restrict__ f, Layout lay, double* __restrict__ rho_out,
+                          double* __restrict__ u_out, Params p) {
   using T = typename P::T;
-  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (n >= p.N) return;
-  const int64_t N = p.N;
-  if (mask[n] & (M_SOLID | M_OPEN)) {
-    rho_out[n] = 0.0;
-    for (int a = 0; a < L::D; ++a) u_out[a * N + n] = 0.0;
-    return;
-  }
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= lay.S || !is_fluid(lay.word[k])) return;
+  const size_t S = (size_t)lay.S;
+  const int64_t N = p.N, n = lay.node_of[k];
   T r = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
-    const T v = f[(int64_t)i * N + n];
+    const T v = f[(size_t)i * S + k];
     r += v;
     jx += (T)L::cx(i) * v;
     jy += (T)L::cy(i) * v;
@@ -433,81 +543,78 @@ __global__ void k_moments(const typename P::T* __restrict__ f, const uint8_t* __
 // Moment cache refresh from a post-collision state (after the caller sets
 // the populations): same formula as k_moments, storage precision.
 template <class L, class P>
-__global__ void k_refresh(const typename P::T* __restrict__ f, const uint8_t* __restrict__ mask,
-                          Mom4<typename P::T>* __restrict__ mom, Params p) {
+__global__ void k_refresh(const typename P::T* __restrict__ f, Layout lay, Mom4<typename P::T>* __restrict__ mom,
+                          Params p) {
   using T = typename P::T;
-  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (n >= p.N || !(mask[n] & M_CACHE)) return;
-  const int64_t N = p.N;
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= lay.S || !(lay.word[k] & W_CACHE) || !is_fluid(lay.word[k])) return;
+  const size_t S = (size_t)lay.S;
   T r = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
-    const T v = f[(int64_t)i * N + n];
+    const T v = f[(size_t)i * S + k];
     r += v;
     jx += (T)L::cx(i) * v;
     jy += (T)L::cy(i) * v;
     jz += (T)L::cz(i) * v;
   }
   const T rho = P::shifted ? (T)p.rho0 + r : r;
-  mom[n] = Mom4<T>{r, (jx - (T)(0.5 * p.g[0])) / rho, (jy - (T)(0.5 * p.g[1])) / rho,
+  mom[k] = Mom4<T>{r, (jx - (T)(0.5 * p.g[0])) / rho, (jy - (T)(0.5 * p.g[1])) / rho,
                    L::D == 3 ? (jz - (T)(0.5 * p.g[2])) / rho : (T)0};
 }
 
-// One direction of the state to/from FP64 unshifted populations.
-template <class L, class P>
-__global__ void k_get_dir(const typename P::T* __restrict__ f, const uint8_t* __restrict__ mask, int i,
-                          double* __restrict__ out, Params p) {
-  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (n >= p.N) return;
-  if (mask[n] & (M_SOLID | M_OPEN)) {
-    out[n] = 0.0;
-    return;
-  }
+template <class L>
+__device__ __forceinline__ double weight_of(int i) {
   double w = 0.0;
 #pragma unroll
   for (int k = 0; k < L::Q; ++k)
     if (k == i) w = L::w(k);
-  out[n] = (double)f[(int64_t)i * p.N + n] + (P::shifted ? w * p.rho0 : 0.0);
+  return w;
+}
+
+// One direction of the state to (k_get_dir, dense FP64 unshifted output,
+// zeroed by the caller) or from (k_set_dir) the caller's layout.
+template <class L, class P>
+__global__ void k_get_dir(const typename P::T* __restrict__ f, Layout lay, int i, double* __restrict__ out, Params p) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= lay.S || !is_fluid(lay.word[k])) return;
+  out[lay.node_of[k]] = (double)f[(size_t)i * lay.S + k] + (P::shifted ? weight_of<L>(i) * p.rho0 : 0.0);
 }
 
 template <class L, class P>
-__global__ void k_set_dir(typename P::T* __restrict__ f, const uint8_t* __restrict__ mask, int i,
-                          const double* __restrict__ in, Params p) {
+__global__ void k_set_dir(typename P::T* __restrict__ f, Layout lay, int i, const double* __restrict__ in, Params p) {
   using T = typename P::T;
-  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (n >= p.N) return;
-  double w = 0.0;
-#pragma unroll
-  for (int k = 0; k < L::Q; ++k)
-    if (k == i) w = L::w(k);
-  f[(int64_t)i * p.N + n] = (mask[n] & (M_SOLID | M_OPEN)) ? (T)0 : (T)(in[n] - (P::shifted ? w * p.rho0 : 0.0));
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= lay.S) return;
+  f[(size_t)i * lay.S + k] =
+      is_fluid(lay.word[k]) ? (T)(in[lay.node_of[k]] - (P::shifted ? weight_of<L>(i) * p.rho0 : 0.0)) : (T)0;
 }
 
-// Populations of listed nodes (FP64 unshifted), out[k*Q + i].
+// Populations of listed storage indices (-1: not a fluid node -> 0), FP64
+// unshifted, out[k*Q + i].
 template <class L, class P>
-__global__ void k_gather(const typename P::T* __restrict__ f, const uint8_t* __restrict__ mask,
-                         const int64_t* __restrict__ nodes, int64_t n, double* __restrict__ out, Params p) {
+__global__ void k_gather(const typename P::T* __restrict__ f, Layout lay, const int64_t* __restrict__ sk, int64_t n,
+                         double* __restrict__ out, Params p) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= n) return;
-  const int64_t node = nodes[k];
-  const bool off = (mask[node] & (M_SOLID | M_OPEN)) != 0;
+  const int64_t s = sk[k];
+  const bool off = s < 0 || !is_fluid(lay.word[s]);
 #pragma unroll
   for (int i = 0; i < L::Q; ++i)
-    out[k * L::Q + i] = off ? 0.0 : (double)f[(int64_t)i * p.N + node] + (P::shifted ? L::w(i) * p.rho0 : 0.0);
+    out[k * L::Q + i] = off ? 0.0 : (double)f[(size_t)i * lay.S + s] + (P::shifted ? L::w(i) * p.rho0 : 0.0);
 }
 
 // Failure detection: flag any non-finite population or non-positive density.
 template <class L, class P>
-__global__ void k_check(const typename P::T* __restrict__ f, const uint8_t* __restrict__ mask, int* __restrict__ flag,
-                        Params p) {
+__global__ void k_check(const typename P::T* __restrict__ f, Layout lay, int* __restrict__ flag, Params p) {
   using T = typename P::T;
-  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (n >= p.N || (mask[n] & (M_SOLID | M_OPEN))) return;
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= lay.S || !is_fluid(lay.word[k])) return;
   T r = 0;
   bool bad = false;
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
-    const T v = f[(int64_t)i * p.N + n];
+    const T v = f[(size_t)i * lay.S + k];
     bad |= !isfinite(v);
     r += v;
   }
@@ -520,19 +627,19 @@ __global__ void k_check(const typename P::T* __restrict__ f, const uint8_t* __re
 struct KernelOps {
   int Q, D;
   size_t real_bytes;
-  void (*bulk)(const void* fin, void* fout, const uint8_t* mask, void* mom, double* force_next, const Params& p,
+  void (*bulk)(const void* fin, void* fout, const Layout& lay, void* mom, double* force_next, const Params& p,
                cudaStream_t s);
-  void (*links)(void* f, const void* mom, const uint64_t* keys, const void* q, const void* uw, int64_t nl, double* force,
-                const Params& p, cudaStream_t s);
-  void (*open)(void* f, const void* mom, const uint8_t* mask, const Params& p, cudaStream_t s);
-  void (*init)(void* f, void* mom, const uint8_t* mask, const double* rho, const double* u, const Params& p,
+  void (*links)(void* f, const void* mom, const LinkRec* recs, const void* q, const void* uw, int64_t nl,
+                double* force, const Params& p, int64_t S, cudaStream_t s);
+  void (*open)(void* f, const void* mom, const Layout& lay, const Params& p, cudaStream_t s);
+  void (*init)(void* f, void* mom, const Layout& lay, const double* rho, const double* u, const Params& p,
                cudaStream_t s);
-  void (*moments)(const void* f, const uint8_t* mask, double* rho, double* u, const Params& p, cudaStream_t s);
-  void (*refresh)(const void* f, const uint8_t* mask, void* mom, const Params& p, cudaStream_t s);
-  void (*get_dir)(const void* f, const uint8_t* mask, int i, double* out, const Params& p, cudaStream_t s);
-  void (*set_dir)(void* f, const uint8_t* mask, int i, const double* in, const Params& p, cudaStream_t s);
-  void (*check)(const void* f, const uint8_t* mask, int* flag, const Params& p, cudaStream_t s);
-  void (*gather)(const void* f, const uint8_t* mask, const int64_t* nodes, int64_t n, double* out, const Params& p,
+  void (*moments)(const void* f, const Layout& lay, double* rho, double* u, const Params& p, cudaStream_t s);
+  void (*refresh)(const void* f, const Layout& lay, void* mom, const Params& p, cudaStream_t s);
+  void (*get_dir)(const void* f, const Layout& lay, int i, double* out, const Params& p, cudaStream_t s);
+  void (*set_dir)(void* f, const Layout& lay, int i, const double* in, const Params& p, cudaStream_t s);
+  void (*check)(const void* f, const Layout& lay, int* flag, const Params& p, cudaStream_t s);
+  void (*gather)(const void* f, const Layout& lay, const int64_t* sk, int64_t n, double* out, const Params& p,
                  cudaStream_t s);
 };
 
@@ -541,44 +648,49 @@ inline unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b
 template <class L, class P>
 struct Launch {
   using T = typename P::T;
-  static void bulk(const void* fin, void* fout, const uint8_t* mask, void* mom, double* force_next, const Params& p,
+  static void bulk(const void* fin, void* fout, const Layout& lay, void* mom, double* force_next, const Params& p,
                    cudaStream_t s) {
-    const int bx = p.nx >= 256 ? 256 : ((p.nx + 31) / 32) * 32;
-    dim3 grid(blocks_for(p.nx, bx), p.ny, p.nz);
-    k_bulk<L, P><<<grid, bx, 0, s>>>((const T*)fin, (T*)fout, mask, (Mom4<T>*)mom, force_next, p);
+    if (lay.S == 0) return;
+    k_bulk<L, P><<<blocks_for(lay.S, 256), 256, 0, s>>>((const T*)fin, (T*)fout, lay, (Mom4<T>*)mom, force_next, p);
   }
-  static void links(void* f, const void* mom, const uint64_t* keys, const void* q, const void* uw, int64_t nl,
-                    double* force, const Params& p, cudaStream_t s) {
+  static void links(void* f, const void* mom, const LinkRec* recs, const void* q, const void* uw, int64_t nl,
+                    double* force, const Params& p, int64_t S, cudaStream_t s) {
     if (nl == 0) return;
-    k_links<L, P><<<blocks_for(nl, 256), 256, 0, s>>>((T*)f, (const Mom4<T>*)mom, keys, (const T*)q, (const T*)uw, nl,
-                                                     force, p);
+    k_links<L, P><<<blocks_for(nl, 256), 256, 0, s>>>((T*)f, (const Mom4<T>*)mom, recs, (const T*)q, (const T*)uw, nl,
+                                                     force, p, S);
   }
-  static void open(void* f, const void* mom, const uint8_t* mask, const Params& p, cudaStream_t s) {
-    k_open<L, P><<<blocks_for(p.ny, 128), 128, 0, s>>>((T*)f, (const Mom4<T>*)mom, mask, p);
+  static void open(void* f, const void* mom, const Layout& lay, const Params& p, cudaStream_t s) {
+    k_open<L, P><<<blocks_for(p.ny, 128), 128, 0, s>>>((T*)f, (const Mom4<T>*)mom, lay, p);
   }
-  static void init(void* f, void* mom, const uint8_t* mask, const double* rho, const double* u, const Params& p,
+  static void init(void* f, void* mom, const Layout& lay, const double* rho, const double* u, const Params& p,
                    cudaStream_t s) {
-    k_init<L, P><<<blocks_for(p.N, 256), 256, 0, s>>>((T*)f, (Mom4<T>*)mom, mask, rho, u, p);
+    if (lay.S == 0) return;
+    k_init<L, P><<<blocks_for(lay.S, 256), 256, 0, s>>>((T*)f, (Mom4<T>*)mom, lay, rho, u, p);
   }
-  static void moments(const void* f, const uint8_t* mask, double* rho, double* u, const Params& p, cudaStream_t s) {
-    k_moments<L, P><<<blocks_for(p.N, 256), 256, 0, s>>>((const T*)f, mask, rho, u, p);
+  static void moments(const void* f, const Layout& lay, double* rho, double* u, const Params& p, cudaStream_t s) {
+    if (lay.S == 0) return;
+    k_moments<L, P><<<blocks_for(lay.S, 256), 256, 0, s>>>((const T*)f, lay, rho, u, p);
   }
-  static void refresh(const void* f, const uint8_t* mask, void* mom, const Params& p, cudaStream_t s) {
-    k_refresh<L, P><<<blocks_for(p.N, 256), 256, 0, s>>>((const T*)f, mask, (Mom4<T>*)mom, p);
+  static void refresh(const void* f, const Layout& lay, void* mom, const Params& p, cudaStream_t s) {
+    if (lay.S == 0) return;
+    k_refresh<L, P><<<blocks_for(lay.S, 256), 256, 0, s>>>((const T*)f, lay, (Mom4<T>*)mom, p);
   }
-  static void get_dir(const void* f, const uint8_t* mask, int i, double* out, const Params& p, cudaStream_t s) {
-    k_get_dir<L, P><<<blocks_for(p.N, 256), 256, 0, s>>>((const T*)f, mask, i, out, p);
+  static void get_dir(const void* f, const Layout& lay, int i, double* out, const Params& p, cudaStream_t s) {
+    if (lay.S == 0) return;
+    k_get_dir<L, P><<<blocks_for(lay.S, 256), 256, 0, s>>>((const T*)f, lay, i, out, p);
   }
-  static void set_dir(void* f, const uint8_t* mask, int i, const double* in, const Params& p, cudaStream_t s) {
-    k_set_dir<L, P><<<blocks_for(p.N, 256), 256, 0, s>>>((T*)f, mask, i, in, p);
+  static void set_dir(void* f, const Layout& lay, int i, const double* in, const Params& p, cudaStream_t s) {
+    if (lay.S == 0) return;
+    k_set_dir<L, P><<<blocks_for(lay.S, 256), 256, 0, s>>>((T*)f, lay, i, in, p);
   }
-  static void check(const void* f, const uint8_t* mask, int* flag, const Params& p, cudaStream_t s) {
-    k_check<L, P><<<blocks_for(p.N, 256), 256, 0, s>>>((const T*)f, mask, flag, p);
+  static void check(const void* f, const Layout& lay, int* flag, const Params& p, cudaStream_t s) {
+    if (lay.S == 0) return;
+    k_check<L, P><<<blocks_for(lay.S, 256), 256, 0, s>>>((const T*)f, lay, flag, p);
   }
-  static void gather(const void* f, const uint8_t* mask, const int64_t* nodes, int64_t n, double* out, const Params& p,
+  static void gather(const void* f, const Layout& lay, const int64_t* sk, int64_t n, double* out, const Params& p,
                      cudaStream_t s) {
     if (n == 0) return;
-    k_gather<L, P><<<blocks_for(n, 256), 256, 0, s>>>((const T*)f, mask, nodes, n, out, p);
+    k_gather<L, P><<<blocks_for(n, 256), 256, 0, s>>>((const T*)f, lay, sk, n, out, p);
   }
   static KernelOps ops() {
     return KernelOps{L::Q, L::D, sizeof(T), bulk, links, open, init, moments, refresh, get_dir, set_dir, check, gather};

@@ -35,6 +35,21 @@ struct D2Q9 {
   __host__ __device__ static constexpr int opp(int i) { return i == 0 ? 0 : (i < 5 ? 1 + ((i + 1) & 3) : 5 + ((i - 3) & 3)); }
 };
 
+// D2Q9 moment matrix of Sec. 2, Eq. (M): rows m0..m8 = (rho, e, epsilon, j_x,
+// q_x, j_y, q_y, p_xx, p_xy), columns = directions in the order above; rows
+// are orthogonal, so M^-1 = M^T diag(1 / |row_k|^2).
+__host__ __device__ constexpr int mrt_m(int k, int i) {
+  constexpr int M[9][9] = {{1, 1, 1, 1, 1, 1, 1, 1, 1},     {-4, -1, -1, -1, -1, 2, 2, 2, 2},
+                           {4, -2, -2, -2, -2, 1, 1, 1, 1}, {0, 1, 0, -1, 0, 1, -1, -1, 1},
+                           {0, -2, 0, 2, 0, 1, -1, -1, 1},  {0, 0, 1, 0, -1, 1, 1, -1, -1},
+                           {0, 0, -2, 0, 2, 1, 1, -1, -1},  {0, 1, -1, 1, -1, 0, 0, 0, 0},
+                           {0, 0, 0, 0, 0, 1, -1, 1, -1}};
+  return M[k][i];
+}
+__host__ __device__ constexpr int mrt_norm2(int k) {
+  return k == 0 ? 9 : (k == 1 || k == 2) ? 36 : (k == 3 || k == 5) ? 6 : (k == 4 || k == 6) ? 12 : 4;
+}
+
 struct D3Q19 {
   static constexpr int Q = 19, D = 3;
   __host__ __device__ static constexpr int cx(int i) {
@@ -61,12 +76,19 @@ struct Params {
   int nx, ny, nz;
   int64_t N;            // nx*ny*nz
   double tau, rho0;
+  double omega;         // 1/tau
+  double fpre3;         // 3 (1 - 1/(2 tau)), Guo source prefactor
   double g[3];
   int has_force;        // g != 0
   int collision;        // 0 BGK, 1 MRT
   double inlet_umax, inlet_y0, inlet_y1;
   int inlet, outlet;
   int vibb_local_rho;   // rho_d = rho_f when q > 1/2
+  int periodic[3];
 };
+
+// Error message shared by every translation unit of the library (set by a
+// failing entry point, read through lbm_last_error).
+void set_last_error(const char* msg);
 
 }  // namespace lbm

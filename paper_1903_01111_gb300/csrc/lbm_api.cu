@@ -1,10 +1,11 @@
 // Host side of liblbm.so: the C ABI declared in include/lbm.h.
 //
-// A lattice owns two population buffers (ping-pong), the moment cache, the
-// node mask, the compacted link arrays and two FP64 force slots.  lbm_step
-// replays a captured CUDA graph of two steps (one per buffer parity) and
-// launches single steps directly for an odd remainder; with profiling on it
-// launches kernel by kernel between CUDA events.
+// A lattice owns two population buffers (ping-pong) over the stored nodes of
+// the compacted layout (fluid, open-column and ghost nodes, see
+// kernels.cuh), the moment cache, the layout tables, the link records and
+// two FP64 force slots.  lbm_step replays a captured CUDA graph of two steps
+// and launches single steps directly for an odd remainder; with profiling on
+// it launches kernel by kernel between CUDA events.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -32,17 +33,28 @@ lbm_status fail(lbm_status st, const char* fmt, ...) {
   return st;
 }
 
-#define CUDA_TRY(call)                                                                               \
-  do {                                                                                               \
-    cudaError_t e_ = (call);                                                                         \
-    if (e_ != cudaSuccess)                                                                           \
+#define CUDA_TRY(call)                                                                                    \
+  do {                                                                                                    \
+    cudaError_t e_ = (call);                                                                              \
+    if (e_ != cudaSuccess)                                                                                \
       return fail(e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, "%s: %s (%s:%d)", #call, \
-                  cudaGetErrorString(e_), __FILE__, __LINE__);                                       \
+                  cudaGetErrorString(e_), __FILE__, __LINE__);                                            \
   } while (0)
 
 constexpr int kMaxTimedKernels = 3;
 
+// host mask bits used while building the layout
+enum : uint8_t { H_SOLID = 1, H_CACHE = 2, H_OPEN = 4, H_GHOST = 8 };
+
 }  // namespace
+
+void lbm::set_last_error(const char* msg) { snprintf(g_msg, sizeof g_msg, "%s", msg); }
+
+// One owned device buffer.
+struct DeviceBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
 
 struct lbm_lattice_s {
   lbm_config cfg{};
@@ -51,44 +63,64 @@ struct lbm_lattice_s {
   int Q = 0, D = 0;
   int64_t N = 0;
   size_t rb = 0;  // bytes per stored real
-  void* f[2] = {nullptr, nullptr};
-  void* mom = nullptr;
-  uint8_t* mask = nullptr;
-  double* force = nullptr;  // [2][MAX_BODIES][3]
-  uint64_t* keys = nullptr;
-  void* q = nullptr;
-  void* uw = nullptr;
-  int64_t n_links = 0, n_fluid = 0, n_cached = 0;
-  int cur = 0;        // buffer holding f+(t)
+  // state over stored nodes
+  DeviceBuf f[2], mom;
+  // layout
+  DeviceBuf word, node_of, runs, row_first, row_last;
+  Layout lay{};
+  std::vector<int32_t> sidx;  // dense -> storage index (-1: not stored), host
+  // links
+  DeviceBuf recs, q, uw;
+  int64_t n_links = 0, n_fluid = 0, n_cached = 0, n_runs = 0;
+  DeviceBuf force;  // [2][MAX_BODIES][3]
+  int cur = 0;      // buffer holding f+(t)
   int64_t step = 0;
   bool has_geometry = false, has_state = false;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // two steps starting at parity 0 / 1
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
   // profiling
   bool profiling = false;
-  std::vector<cudaEvent_t> ev;  // pairs, kernel id in ev_kernel
+  std::vector<cudaEvent_t> ev;
   std::vector<int> ev_kernel;
   size_t ev_used = 0;
   int64_t prof_launches[kMaxTimedKernels] = {0, 0, 0};
   double prof_ms[kMaxTimedKernels] = {0, 0, 0};
-  int64_t device_bytes = 0;
 };
 
 namespace {
 
-lbm_status dev_alloc(lbm_handle h, void** p, size_t bytes) {
-  if (bytes == 0) {
-    *p = nullptr;
-    return LBM_OK;
-  }
-  cudaError_t e = cudaMalloc(p, bytes);
+int64_t device_bytes(const lbm_handle h) {
+  const DeviceBuf* all[] = {&h->f[0], &h->f[1], &h->mom, &h->word, &h->node_of, &h->runs, &h->row_first,
+                            &h->row_last, &h->recs, &h->q, &h->uw, &h->force};
+  int64_t s = 0;
+  for (auto* b : all) s += (int64_t)b->bytes;
+  return s;
+}
+
+void release(DeviceBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+lbm_status acquire(DeviceBuf& b, size_t bytes) {
+  release(b);
+  if (bytes == 0) return LBM_OK;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
   if (e != cudaSuccess) {
-    *p = nullptr;
+    b.p = nullptr;
     cudaGetLastError();
     return fail(LBM_ERR_OOM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
   }
-  h->device_bytes += (int64_t)bytes;
+  b.bytes = bytes;
+  return LBM_OK;
+}
+
+lbm_status upload(DeviceBuf& b, const void* src, size_t bytes) {
+  lbm_status st = acquire(b, bytes);
+  if (st != LBM_OK || bytes == 0) return st;
+  CUDA_TRY(cudaMemcpy(b.p, src, bytes, cudaMemcpyHostToDevice));
   return LBM_OK;
 }
 
@@ -100,12 +132,11 @@ void drop_graphs(lbm_handle h) {
     }
 }
 
-void free_links(lbm_handle h) {
-  if (h->keys) cudaFree(h->keys);
-  if (h->q) cudaFree(h->q);
-  if (h->uw) cudaFree(h->uw);
-  h->keys = nullptr;
-  h->q = h->uw = nullptr;
+void release_geometry(lbm_handle h) {
+  DeviceBuf* all[] = {&h->f[0], &h->f[1], &h->mom, &h->word, &h->node_of, &h->runs,
+                      &h->row_first, &h->row_last, &h->recs, &h->q, &h->uw};
+  for (auto* b : all) release(*b);
+  h->lay = Layout{};
 }
 
 int cx_of(const lbm_handle h, int i) { return h->Q == 9 ? D2Q9::cx(i) : D3Q19::cx(i); }
@@ -114,10 +145,11 @@ int cz_of(const lbm_handle h, int i) { return h->Q == 9 ? D2Q9::cz(i) : D3Q19::c
 
 // Enqueue one time step on the stream (parity = buffer holding f+(t)).
 lbm_status enqueue_step(lbm_handle h, int parity, int64_t step_index, bool timed) {
-  void* fc = h->f[parity];
-  void* fn = h->f[parity ^ 1];
-  double* slot = h->force + 3 * MAX_BODIES * (step_index & 1);
-  double* next = h->force + 3 * MAX_BODIES * ((step_index + 1) & 1);
+  void* fc = h->f[parity].p;
+  void* fn = h->f[parity ^ 1].p;
+  double* force = (double*)h->force.p;
+  double* slot = force + 3 * MAX_BODIES * (step_index & 1);
+  double* next = force + 3 * MAX_BODIES * ((step_index + 1) & 1);
   auto timed_launch = [&](int kid, auto&& fn_launch) -> lbm_status {
     if (!timed) {
       fn_launch();
@@ -140,13 +172,16 @@ lbm_status enqueue_step(lbm_handle h, int parity, int64_t step_index, bool timed
     return LBM_OK;
   };
   lbm_status st;
-  st = timed_launch(0, [&] { h->ops.links(fc, h->mom, h->keys, h->q, h->uw, h->n_links, slot, h->p, h->stream); });
+  st = timed_launch(0, [&] {
+    h->ops.links(fc, h->mom.p, (const LinkRec*)h->recs.p, h->q.p, h->uw.p, h->n_links, slot, h->p, h->lay.S,
+                 h->stream);
+  });
   if (st != LBM_OK) return st;
   if (h->p.inlet || h->p.outlet) {
-    st = timed_launch(1, [&] { h->ops.open(fc, h->mom, h->mask, h->p, h->stream); });
+    st = timed_launch(1, [&] { h->ops.open(fc, h->mom.p, h->lay, h->p, h->stream); });
     if (st != LBM_OK) return st;
   }
-  st = timed_launch(2, [&] { h->ops.bulk(fc, fn, h->mask, h->mom, next, h->p, h->stream); });
+  st = timed_launch(2, [&] { h->ops.bulk(fc, fn, h->lay, h->mom.p, next, h->p, h->stream); });
   if (st != LBM_OK) return st;
   CUDA_TRY(cudaGetLastError());
   return LBM_OK;
@@ -206,14 +241,14 @@ lbm_status lbm_create_lattice(const lbm_config* cfg, lbm_handle* out) {
   if (c.stencil != LBM_D2Q9 && c.stencil != LBM_D3Q19) return fail(LBM_ERR_INVALID_ARG, "unknown stencil %d", c.stencil);
   if (c.precision != LBM_FP64 && c.precision != LBM_FP32_SHIFTED)
     return fail(LBM_ERR_INVALID_ARG, "unknown precision %d", c.precision);
-  if (c.collision == LBM_MRT) return fail(LBM_ERR_UNSUPPORTED, "MRT collision is not built");
-  if (c.collision != LBM_BGK) return fail(LBM_ERR_INVALID_ARG, "unknown collision %d", c.collision);
+  if (c.collision != LBM_BGK && c.collision != LBM_MRT) return fail(LBM_ERR_INVALID_ARG, "unknown collision %d", c.collision);
+  if (c.collision == LBM_MRT && c.stencil != LBM_D2Q9)
+    return fail(LBM_ERR_UNSUPPORTED, "MRT is defined for D2Q9 (the moment matrix of the paper)");
   if (c.bc < LBM_BC_HALFWAY || c.bc > LBM_BC_VIBB) return fail(LBM_ERR_INVALID_ARG, "unknown default rule %d", c.bc);
   if (c.vibb_density != LBM_VIBB_RHO_PRINTED && c.vibb_density != LBM_VIBB_RHO_LOCAL)
     return fail(LBM_ERR_INVALID_ARG, "unknown vibb_density %d", c.vibb_density);
   if (c.nx < 1 || c.ny < 1 || c.nz < 1) return fail(LBM_ERR_INVALID_ARG, "lattice size must be positive");
   if (c.stencil == LBM_D2Q9 && c.nz != 1) return fail(LBM_ERR_INVALID_ARG, "D2Q9 needs nz == 1");
-  if (c.ny > 65535 || c.nz > 65535) return fail(LBM_ERR_UNSUPPORTED, "ny and nz are limited to 65535");
   if (!(c.tau > 0.5) || !std::isfinite(c.tau)) return fail(LBM_ERR_INVALID_ARG, "tau must be finite and > 1/2");
   if (!(c.rho0 > 0.0) || !std::isfinite(c.rho0)) return fail(LBM_ERR_INVALID_ARG, "rho0 must be positive");
   for (int a = 0; a < 3; ++a)
@@ -243,6 +278,8 @@ lbm_status lbm_create_lattice(const lbm_config* cfg, lbm_handle* out) {
   p.N = N;
   p.tau = c.tau;
   p.rho0 = c.rho0;
+  p.omega = 1.0 / c.tau;
+  p.fpre3 = 3.0 * (1.0 - 0.5 / c.tau);
   for (int a = 0; a < 3; ++a) p.g[a] = (a < h->D) ? c.g[a] : 0.0;
   p.has_force = (p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0);
   p.collision = c.collision;
@@ -252,8 +289,8 @@ lbm_status lbm_create_lattice(const lbm_config* cfg, lbm_handle* out) {
   p.inlet_y0 = c.inlet_y0;
   p.inlet_y1 = c.inlet_y1;
   p.vibb_local_rho = c.vibb_density == LBM_VIBB_RHO_LOCAL ? 1 : 0;
+  for (int a = 0; a < 3; ++a) p.periodic[a] = c.periodic[a] ? 1 : 0;
 
-  lbm_status st = LBM_OK;
   if (c.cuda_stream) {
     h->stream = (cudaStream_t)c.cuda_stream;
   } else {
@@ -264,14 +301,9 @@ lbm_status lbm_create_lattice(const lbm_config* cfg, lbm_handle* out) {
     }
     h->own_stream = true;
   }
-  const size_t fb = (size_t)h->Q * N * h->rb;
-  for (int k = 0; k < 2 && st == LBM_OK; ++k) st = dev_alloc(h, &h->f[k], fb);
-  if (st == LBM_OK) st = dev_alloc(h, &h->mom, (size_t)4 * N * h->rb);
-  if (st == LBM_OK) st = dev_alloc(h, (void**)&h->mask, (size_t)N);
-  if (st == LBM_OK) st = dev_alloc(h, (void**)&h->force, sizeof(double) * 2 * 3 * MAX_BODIES);
+  lbm_status st = acquire(h->force, sizeof(double) * 2 * 3 * MAX_BODIES);
   if (st == LBM_OK) {
-    cudaError_t e = cudaMemsetAsync(h->force, 0, sizeof(double) * 2 * 3 * MAX_BODIES, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->mom, 0, (size_t)4 * N * h->rb, h->stream);
+    cudaError_t e = cudaMemsetAsync(h->force.p, 0, h->force.bytes, h->stream);
     if (e != cudaSuccess) st = fail(LBM_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
   }
   if (st != LBM_OK) {
@@ -290,12 +322,8 @@ lbm_status lbm_destroy(lbm_handle h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   drop_graphs(h);
   for (auto e : h->ev) cudaEventDestroy(e);
-  for (int k = 0; k < 2; ++k)
-    if (h->f[k]) cudaFree(h->f[k]);
-  if (h->mom) cudaFree(h->mom);
-  if (h->mask) cudaFree(h->mask);
-  if (h->force) cudaFree(h->force);
-  free_links(h);
+  release_geometry(h);
+  release(h->force);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
   return LBM_OK;
@@ -307,15 +335,16 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
   const lbm_config& c = h->cfg;
   const int64_t N = h->N, nx = c.nx, ny = c.ny, nz = c.nz;
   const int Q = h->Q, D = h->D;
-  // node classes: mask bits
+  if (n_links >= ((int64_t)1 << 31)) return fail(LBM_ERR_UNSUPPORTED, "at most 2^31 - 1 links");
+  // node classes
   std::vector<uint8_t> m(N);
-  for (int64_t n = 0; n < N; ++n) m[n] = solid[n] ? M_SOLID : 0;
+  for (int64_t n = 0; n < N; ++n) m[n] = solid[n] ? H_SOLID : 0;
   if (c.inlet || c.outlet)
     for (int64_t z = 0; z < nz; ++z)
       for (int64_t y = 0; y < ny; ++y) {
         const int64_t row = nx * (y + ny * z);
-        if (c.inlet && !(m[row] & M_SOLID)) m[row] |= M_OPEN;
-        if (c.outlet && !(m[row + nx - 1] & M_SOLID)) m[row + nx - 1] |= M_OPEN;
+        if (c.inlet && !(m[row] & H_SOLID)) m[row] |= H_OPEN;
+        if (c.outlet && !(m[row + nx - 1] & H_SOLID)) m[row + nx - 1] |= H_OPEN;
       }
   // faces of non-periodic axes must be solid (or open columns)
   const int64_t len[3] = {nx, ny, nz};
@@ -323,7 +352,7 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
     if (c.periodic[a] || (a == 2 && D == 2)) continue;
     for (int64_t n = 0; n < N; ++n) {
       const int64_t x[3] = {n % nx, (n / nx) % ny, n / (nx * ny)};
-      if ((x[a] == 0 || x[a] == len[a] - 1) && !(m[n] & (M_SOLID | M_OPEN)))
+      if ((x[a] == 0 || x[a] == len[a] - 1) && !(m[n] & (H_SOLID | H_OPEN)))
         return fail(LBM_ERR_INVALID_ARG,
                     "node (%lld,%lld,%lld) on a face of non-periodic axis %d is fluid: add a solid layer",
                     (long long)x[0], (long long)x[1], (long long)x[2], a);
@@ -335,7 +364,7 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
     x[2] = n / (nx * ny);
   };
   // neighbour n + s e_d with wrap; -1 if it leaves through a non-periodic face
-  auto neighbour = [&](int64_t n, int d, int s, bool* wrapped) -> int64_t {
+  auto neighbour = [&](int64_t n, int d, int s) -> int64_t {
     int64_t x[3];
     coords(n, x);
     const int e[3] = {cx_of(h, d), cy_of(h, d), cz_of(h, d)};
@@ -344,19 +373,18 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
       if (x[a] < 0 || x[a] >= len[a]) {
         if (!c.periodic[a]) return -1;
         x[a] = (x[a] + len[a]) % len[a];
-        if (wrapped) *wrapped = true;
       }
     }
     return x[0] + nx * (x[1] + ny * x[2]);
   };
-  // links
-  std::vector<uint64_t> keys(n_links);
-  std::vector<double> qs(n_links);
+  // links: checks, second fluid node, cache flags
+  std::vector<int64_t> lk_s(n_links), lk_ff(n_links);
+  std::vector<int> lk_rule(n_links);
   bool moving = false;
   for (int64_t k = 0; k < n_links; ++k) {
     const lbm_link& L = links[k];
     if (L.node < 0 || L.node >= N) return fail(LBM_ERR_INVALID_ARG, "link %lld: node out of range", (long long)k);
-    if (m[L.node] & (M_SOLID | M_OPEN))
+    if (m[L.node] & (H_SOLID | H_OPEN))
       return fail(LBM_ERR_INVALID_ARG, "link %lld: node %lld is not a fluid node", (long long)k, (long long)L.node);
     if (L.dir < 1 || L.dir >= Q) return fail(LBM_ERR_INVALID_ARG, "link %lld: dir %d out of range", (long long)k, L.dir);
     if (!(L.q > 0.0 && L.q <= 1.0)) return fail(LBM_ERR_INVALID_ARG, "link %lld: q = %g not in (0,1]", (long long)k, L.q);
@@ -366,35 +394,36 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
       return fail(LBM_ERR_INVALID_ARG, "link %lld: body %d out of range", (long long)k, L.body);
     for (int a = 0; a < 3; ++a)
       if (!std::isfinite(L.uw[a])) return fail(LBM_ERR_INVALID_ARG, "link %lld: non-finite wall velocity", (long long)k);
-    bool wrapped = false;
-    const int64_t s = neighbour(L.node, L.dir, 1, &wrapped);
-    if (s < 0 || !(m[s] & M_SOLID))
+    const int64_t s = neighbour(L.node, L.dir, 1);
+    if (s < 0 || !(m[s] & H_SOLID))
       return fail(LBM_ERR_INVALID_ARG, "link %lld: neighbour of node %lld in direction %d is not a solid node",
                   (long long)k, (long long)L.node, L.dir);
-    const int64_t ff = neighbour(L.node, L.dir, -1, &wrapped);
-    const int fallback = (ff < 0 || (m[ff] & (M_SOLID | M_OPEN))) ? 1 : 0;
+    int64_t ff = neighbour(L.node, L.dir, -1);
+    if (ff < 0 || (m[ff] & (H_SOLID | H_OPEN))) ff = L.node;  // no second fluid node: use x_f
     const int rule = L.bc >= 0 ? L.bc : c.bc;
     if (rule == LBM_BC_VIBB) {
-      m[L.node] |= M_CACHE;
-      if (!fallback) m[ff] |= M_CACHE;
+      m[L.node] |= H_CACHE;
+      m[ff] |= H_CACHE;
     }
     for (int a = 0; a < D; ++a) moving |= L.uw[a] != 0.0;
-    keys[k] = pack_key(L.node, L.dir, rule, fallback, wrapped ? 1 : 0, L.body);
-    qs[k] = L.q;
+    lk_s[k] = s;
+    lk_ff[k] = ff;
+    lk_rule[k] = rule;
   }
+  for (int64_t k = 0; k < n_links; ++k) m[lk_s[k]] |= H_GHOST;
   // open inlet reads the moments of the first fluid column
   if (c.inlet)
     for (int64_t y = 0; y < ny; ++y)
-      if ((m[nx * y] & M_OPEN) && nx > 1) {
-        if (m[nx * y + 1] & (M_SOLID | M_OPEN))
+      if ((m[nx * y] & H_OPEN) && nx > 1) {
+        if (m[nx * y + 1] & (H_SOLID | H_OPEN))
           return fail(LBM_ERR_INVALID_ARG, "inlet node (0,%lld) has no fluid node at x = 1", (long long)y);
-        m[nx * y + 1] |= M_CACHE;
+        m[nx * y + 1] |= H_CACHE;
       }
-  // order by (node, dir) -- the usual input order already -- then stably
-  // by body; reject duplicate (node, dir)
+  // link order: (node, dir) -- usually the input order already -- then
+  // stably by body; reject duplicate (node, dir)
   std::vector<int64_t> order(n_links);
   for (int64_t k = 0; k < n_links; ++k) order[k] = k;
-  auto nodedir = [&](int64_t k) { return (keys[k] >> KEY_NODE_SHIFT) * 32 + (keys[k] & 31); };
+  auto nodedir = [&](int64_t k) { return (uint64_t)links[k].node * 32 + (uint64_t)links[k].dir; };
   bool sorted = true;
   for (int64_t k = 1; k < n_links && sorted; ++k) sorted = nodedir(k - 1) < nodedir(k);
   if (!sorted) {
@@ -418,7 +447,7 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
   // completeness: count (fluid node, dir) pairs with a solid neighbour
   int64_t expected = 0, n_fluid = 0;
   for (int64_t n = 0; n < N; ++n) {
-    if (m[n] & (M_SOLID | M_OPEN)) continue;
+    if (m[n] & (H_SOLID | H_OPEN)) continue;
     ++n_fluid;
     int64_t x[3];
     coords(n, x);
@@ -431,58 +460,164 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
           y[a] = (y[a] + len[a]) % len[a];
         }
       if (out) continue;  // only open columns can sit there (faces are solid otherwise)
-      if (m[y[0] + nx * (y[1] + ny * y[2])] & M_SOLID) ++expected;
+      if (m[y[0] + nx * (y[1] + ny * y[2])] & H_SOLID) ++expected;
     }
   }
   if (expected != n_links)
     return fail(LBM_ERR_INVALID_ARG, "%lld fluid-to-solid neighbour pairs but %lld links: every cut link needs a record",
                 (long long)expected, (long long)n_links);
-  int64_t n_cached = 0;
-  for (int64_t n = 0; n < N; ++n) n_cached += (m[n] & M_CACHE) ? 1 : 0;
 
-  // device arrays
-  CUDA_TRY(cudaStreamSynchronize(h->stream));
-  drop_graphs(h);
-  free_links(h);
-  std::vector<uint64_t> skeys(n_links);
-  for (int64_t k = 0; k < n_links; ++k) skeys[k] = keys[order[k]];
-  lbm_status st = LBM_OK;
-  const size_t rb = h->rb;
-  if (n_links > 0) {
-    st = dev_alloc(h, (void**)&h->keys, sizeof(uint64_t) * n_links);
-    if (st == LBM_OK) st = dev_alloc(h, &h->q, rb * n_links);
-    if (st == LBM_OK && moving) st = dev_alloc(h, &h->uw, rb * D * n_links);
-    if (st != LBM_OK) {
-      free_links(h);
-      return st;
+  // ---- compacted layout: stored = fluid, open and ghost nodes, in row order
+  std::vector<int32_t> sidx(N, -1);
+  std::vector<int32_t> node_of;
+  node_of.reserve((size_t)n_fluid + (size_t)n_links + 64);
+  for (int64_t n = 0; n < N; ++n)
+    if (!(m[n] & H_SOLID) || (m[n] & H_GHOST)) {
+      sidx[n] = (int32_t)node_of.size();
+      node_of.push_back((int32_t)n);
     }
-    CUDA_TRY(cudaMemcpy(h->keys, skeys.data(), sizeof(uint64_t) * n_links, cudaMemcpyHostToDevice));
-    if (rb == 8) {
-      std::vector<double> tq(n_links), tw(moving ? D * n_links : 0);
-      for (int64_t k = 0; k < n_links; ++k) {
-        tq[k] = qs[order[k]];
-        if (moving)
-          for (int a = 0; a < D; ++a) tw[a * n_links + k] = links[order[k]].uw[a];
+  const int64_t S = (int64_t)node_of.size();
+  const int64_t rows = ny * nz;
+  std::vector<int32_t> row_first(rows, -1), row_last(rows, -1);
+  for (int64_t r = 0; r < rows; ++r)
+    for (int64_t x = 0; x < nx; ++x) {
+      const int32_t k = sidx[x + nx * r];
+      if (k < 0) continue;
+      if (row_first[r] < 0) row_first[r] = k;
+      row_last[r] = k;
+    }
+  // neighbour-row slots in use: source-row offsets (dy, dz) = -(cy, cz)
+  // and the range of x offsets pulled from each such row
+  int nslots = 0;
+  int slot_dy[8] = {0}, slot_dz[8] = {0}, slot_dxlo[8], slot_dxhi[8];
+  for (int sl = 0; sl < 8; ++sl) {
+    slot_dxlo[sl] = 1;
+    slot_dxhi[sl] = -1;
+  }
+  for (int d = 1; d < Q; ++d) {
+    const int dy = -cy_of(h, d), dz = -cz_of(h, d), dx = -cx_of(h, d);
+    if (dy == 0 && dz == 0) continue;
+    const int sl = row_slot(dy, dz);
+    slot_dy[sl] = dy;
+    slot_dz[sl] = dz;
+    slot_dxlo[sl] = std::min(slot_dxlo[sl], dx);
+    slot_dxhi[sl] = std::max(slot_dxhi[sl], dx);
+    nslots = std::max(nslots, sl + 1);
+  }
+  // fluid runs and their neighbour-row bases
+  std::vector<RunRec> runs;
+  std::vector<uint32_t> word(S, 0);
+  for (int64_t r = 0; r < rows; ++r) {
+    const int64_t y = r % ny, z = r / ny;
+    int64_t x = 0;
+    while (x < nx) {
+      const int64_t n = x + nx * r;
+      if (m[n] & (H_SOLID | H_OPEN)) {
+        ++x;
+        continue;
       }
-      CUDA_TRY(cudaMemcpy(h->q, tq.data(), 8 * n_links, cudaMemcpyHostToDevice));
-      if (moving) CUDA_TRY(cudaMemcpy(h->uw, tw.data(), 8 * D * n_links, cudaMemcpyHostToDevice));
-    } else {
-      std::vector<float> tq(n_links), tw(moving ? D * n_links : 0);
-      for (int64_t k = 0; k < n_links; ++k) {
-        tq[k] = (float)qs[order[k]];
-        if (moving)
-          for (int a = 0; a < D; ++a) tw[a * n_links + k] = (float)links[order[k]].uw[a];
+      int64_t xe = x;
+      while (xe + 1 < nx && !(m[xe + 1 + nx * r] & (H_SOLID | H_OPEN))) ++xe;
+      RunRec rec{};
+      rec.x0 = (int32_t)x;
+      rec.k0 = sidx[n];
+      rec.y = (int32_t)y;
+      rec.z = (int32_t)z;
+      for (int sl = 0; sl < nslots; ++sl) {
+        const int64_t yy = (y + slot_dy[sl] + ny) % ny, zz = (z + slot_dz[sl] + nz) % nz;
+        const int64_t rr = yy + ny * zz;
+        const int32_t base = sidx[x + nx * rr];
+        // the pull addressing needs the pulled part of row' stored and
+        // contiguous: x0 + min dx .. x_end + max dx (inside the row)
+        for (int64_t xx = std::max<int64_t>(x + slot_dxlo[sl], 0); xx <= std::min<int64_t>(xe + slot_dxhi[sl], nx - 1);
+             ++xx)
+          if (base < 0 || sidx[xx + nx * rr] != base + (int32_t)(xx - x))
+            return fail(LBM_ERR_INVALID_ARG,
+                        "layout: neighbour row of the fluid run at (%lld..%lld, %lld, %lld) is not fully stored",
+                        (long long)x, (long long)xe, (long long)y, (long long)z);
+        rec.base[sl] = base;
       }
-      CUDA_TRY(cudaMemcpy(h->q, tq.data(), 4 * n_links, cudaMemcpyHostToDevice));
-      if (moving) CUDA_TRY(cudaMemcpy(h->uw, tw.data(), 4 * D * n_links, cudaMemcpyHostToDevice));
+      const uint32_t rid = (uint32_t)runs.size();
+      if (rid > W_RUN) return fail(LBM_ERR_UNSUPPORTED, "too many fluid runs");
+      for (int64_t xx = x; xx <= xe; ++xx) {
+        const int64_t nn = xx + nx * r;
+        word[sidx[nn]] = rid | ((m[nn] & H_CACHE) ? W_CACHE : 0u);
+      }
+      runs.push_back(rec);
+      x = xe + 1;
     }
   }
-  CUDA_TRY(cudaMemcpy(h->mask, m.data(), (size_t)N, cudaMemcpyHostToDevice));
+  int64_t n_cached = 0;
+  for (int64_t n = 0; n < N; ++n) {
+    if (sidx[n] < 0) continue;
+    if (m[n] & H_OPEN)
+      word[sidx[n]] = W_OPEN;
+    else if (m[n] & H_SOLID)
+      word[sidx[n]] = W_GHOST;
+    else
+      n_cached += (m[n] & H_CACHE) ? 1 : 0;
+  }
+  // link records in the chosen order
+  std::vector<LinkRec> recs(n_links);
+  std::vector<double> qs(n_links);
+  std::vector<double> uws(moving ? (size_t)D * n_links : 0);
+  for (int64_t j = 0; j < n_links; ++j) {
+    const int64_t k = order[j];
+    const lbm_link& L = links[k];
+    recs[j].kf = (uint32_t)sidx[L.node];
+    recs[j].kff = (uint32_t)sidx[lk_ff[k]];
+    recs[j].ks = (uint32_t)sidx[lk_s[k]];
+    recs[j].meta = (uint32_t)L.dir | ((uint32_t)lk_rule[k] << 5) | ((uint32_t)(L.body + 1) << 7);
+    qs[j] = L.q;
+    if (moving)
+      for (int a = 0; a < D; ++a) uws[a * n_links + j] = L.uw[a];
+  }
+
+  // ---- device
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  drop_graphs(h);
+  release_geometry(h);
+  h->has_geometry = h->has_state = false;
+  lbm_status st = LBM_OK;
+  const size_t rb = h->rb;
+  for (int k = 0; k < 2 && st == LBM_OK; ++k) st = acquire(h->f[k], (size_t)Q * S * rb);
+  if (st == LBM_OK) st = acquire(h->mom, (size_t)S * 4 * rb);
+  if (st == LBM_OK) st = upload(h->word, word.data(), sizeof(uint32_t) * S);
+  if (st == LBM_OK) st = upload(h->node_of, node_of.data(), sizeof(int32_t) * S);
+  if (st == LBM_OK) st = upload(h->runs, runs.data(), sizeof(RunRec) * runs.size());
+  if (st == LBM_OK) st = upload(h->row_first, row_first.data(), sizeof(int32_t) * rows);
+  if (st == LBM_OK) st = upload(h->row_last, row_last.data(), sizeof(int32_t) * rows);
+  if (st == LBM_OK) st = upload(h->recs, recs.data(), sizeof(LinkRec) * n_links);
+  if (st == LBM_OK) {
+    if (rb == 8) {
+      st = upload(h->q, qs.data(), 8 * n_links);
+      if (st == LBM_OK && moving) st = upload(h->uw, uws.data(), 8 * uws.size());
+    } else {
+      std::vector<float> tq(qs.begin(), qs.end()), tw(uws.begin(), uws.end());
+      st = upload(h->q, tq.data(), 4 * n_links);
+      if (st == LBM_OK && moving) st = upload(h->uw, tw.data(), 4 * tw.size());
+    }
+  }
+  if (st == LBM_OK && h->mom.bytes) {
+    cudaError_t e = cudaMemsetAsync(h->mom.p, 0, h->mom.bytes, h->stream);
+    if (e != cudaSuccess) st = fail(LBM_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+  }
+  if (st != LBM_OK) {
+    release_geometry(h);
+    return st;
+  }
+  h->lay.S = S;
+  h->lay.word = (const uint32_t*)h->word.p;
+  h->lay.node_of = (const int32_t*)h->node_of.p;
+  h->lay.runs = (const RunRec*)h->runs.p;
+  h->lay.row_first = (const int32_t*)h->row_first.p;
+  h->lay.row_last = (const int32_t*)h->row_last.p;
+  h->sidx.swap(sidx);
   h->n_links = n_links;
   h->n_fluid = n_fluid;
   h->n_cached = n_cached;
+  h->n_runs = (int64_t)runs.size();
   h->has_geometry = true;
-  h->has_state = false;
   return LBM_OK;
 }
 
@@ -503,12 +638,12 @@ lbm_status lbm_init_equilibrium(lbm_handle h, const double* rho, const double* u
   cudaError_t e = cudaSuccess;
   if (rho) e = cudaMemcpyAsync(drho, rho, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream);
   if (u && e == cudaSuccess) e = cudaMemcpyAsync(du, u, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess && h->mom.bytes) e = cudaMemsetAsync(h->mom.p, 0, h->mom.bytes, h->stream);
   if (e == cudaSuccess) {
-    CUDA_TRY(cudaMemsetAsync(h->mom, 0, (size_t)4 * N * h->rb, h->stream));
-    h->ops.init(h->f[0], h->mom, h->mask, drho, du, h->p, h->stream);
+    h->ops.init(h->f[0].p, h->mom.p, h->lay, drho, du, h->p, h->stream);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->force, 0, sizeof(double) * 2 * 3 * MAX_BODIES, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->force.p, 0, h->force.bytes, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   cudaFree(drho);
   cudaFree(du);
@@ -573,14 +708,19 @@ lbm_status lbm_moments(lbm_handle h, double* rho, double* u) {
   if (drho != du) return fail(LBM_ERR_INVALID_ARG, "rho and u must both be host or both device pointers");
   const int64_t N = h->N;
   if (drho) {
-    h->ops.moments(h->f[h->cur], h->mask, rho, u, h->p, h->stream);
+    CUDA_TRY(cudaMemsetAsync(rho, 0, sizeof(double) * N, h->stream));
+    CUDA_TRY(cudaMemsetAsync(u, 0, sizeof(double) * h->D * N, h->stream));
+    h->ops.moments(h->f[h->cur].p, h->lay, rho, u, h->p, h->stream);
     CUDA_TRY(cudaGetLastError());
     return LBM_OK;
   }
   double* tmp = nullptr;
   CUDA_TRY(cudaMalloc(&tmp, sizeof(double) * (1 + h->D) * N));
-  h->ops.moments(h->f[h->cur], h->mask, tmp, tmp + N, h->p, h->stream);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = cudaMemsetAsync(tmp, 0, sizeof(double) * (1 + h->D) * N, h->stream);
+  if (e == cudaSuccess) {
+    h->ops.moments(h->f[h->cur].p, h->lay, tmp, tmp + N, h->p, h->stream);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaMemcpyAsync(rho, tmp, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(u, tmp + N, sizeof(double) * h->D * N, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -594,7 +734,7 @@ lbm_status lbm_force(lbm_handle h, int32_t body, double F[3]) {
   if (!h || !F) return fail(LBM_ERR_INVALID_ARG, "null argument");
   if (body < 0 || body >= MAX_BODIES) return fail(LBM_ERR_INVALID_ARG, "body %d out of range", body);
   if (!h->has_state || h->step == 0) return fail(LBM_ERR_STATE, "no step has run");
-  const double* slot = h->force + 3 * MAX_BODIES * ((h->step - 1) & 1) + 3 * body;
+  const double* slot = (const double*)h->force.p + 3 * MAX_BODIES * ((h->step - 1) & 1) + 3 * body;
   CUDA_TRY(cudaMemcpyAsync(F, slot, sizeof(double) * 3, cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   return LBM_OK;
@@ -609,9 +749,13 @@ lbm_status lbm_get_distributions(lbm_handle h, double* f) {
   CUDA_TRY(cudaMalloc(&tmp, sizeof(double) * N));
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < h->Q && e == cudaSuccess; ++i) {
-    h->ops.get_dir(h->f[h->cur], h->mask, i, tmp, h->p, h->stream);
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(f + (int64_t)i * N, tmp, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream);
+    e = cudaMemsetAsync(tmp, 0, sizeof(double) * N, h->stream);
+    if (e == cudaSuccess) {
+      h->ops.get_dir(h->f[h->cur].p, h->lay, i, tmp, h->p, h->stream);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(f + (int64_t)i * N, tmp, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   }
   cudaFree(tmp);
@@ -630,13 +774,13 @@ lbm_status lbm_set_distributions(lbm_handle h, const double* f) {
   for (int i = 0; i < h->Q && e == cudaSuccess; ++i) {
     e = cudaMemcpyAsync(tmp, f + (int64_t)i * N, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) {
-      h->ops.set_dir(h->f[h->cur], h->mask, i, tmp, h->p, h->stream);
+      h->ops.set_dir(h->f[h->cur].p, h->lay, i, tmp, h->p, h->stream);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   }
   if (e == cudaSuccess) {
-    h->ops.refresh(h->f[h->cur], h->mask, h->mom, h->p, h->stream);
+    h->ops.refresh(h->f[h->cur].p, h->lay, h->mom.p, h->p, h->stream);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -650,16 +794,19 @@ lbm_status lbm_gather(lbm_handle h, const int64_t* nodes, int64_t n, double* out
   g_msg[0] = 0;
   if (!h || n < 0 || (n > 0 && (!nodes || !out))) return fail(LBM_ERR_INVALID_ARG, "null or negative argument");
   if (!h->has_state) return fail(LBM_ERR_STATE, "no state");
-  for (int64_t k = 0; k < n; ++k)
+  std::vector<int64_t> sk(n);
+  for (int64_t k = 0; k < n; ++k) {
     if (nodes[k] < 0 || nodes[k] >= h->N) return fail(LBM_ERR_INVALID_ARG, "node %lld out of range", (long long)nodes[k]);
+    sk[k] = h->sidx[nodes[k]];
+  }
   if (n == 0) return LBM_OK;
   int64_t* dn = nullptr;
   double* dout = nullptr;
   CUDA_TRY(cudaMalloc(&dn, sizeof(int64_t) * n));
   cudaError_t e = cudaMalloc(&dout, sizeof(double) * h->Q * n);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dn, nodes, sizeof(int64_t) * n, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dn, sk.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) {
-    h->ops.gather(h->f[h->cur], h->mask, dn, n, dout, h->p, h->stream);
+    h->ops.gather(h->f[h->cur].p, h->lay, dn, n, dout, h->p, h->stream);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, sizeof(double) * h->Q * n, cudaMemcpyDeviceToHost, h->stream);
@@ -679,7 +826,7 @@ lbm_status lbm_check(lbm_handle h) {
   int hv = 0;
   cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), h->stream);
   if (e == cudaSuccess) {
-    h->ops.check(h->f[h->cur], h->mask, flag, h->p, h->stream);
+    h->ops.check(h->f[h->cur].p, h->lay, flag, h->p, h->stream);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hv, flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
@@ -703,11 +850,13 @@ lbm_status lbm_query(lbm_handle h, lbm_info* info) {
   info->n_links = h->n_links;
   info->n_cached = h->n_cached;
   info->step = h->step;
-  info->device_bytes = h->device_bytes;
+  info->device_bytes = device_bytes(h);
   info->Q = h->Q;
   info->D = h->D;
   info->precision = h->cfg.precision;
   info->real_bytes = (int32_t)h->rb;
+  info->n_stored = h->lay.S;
+  info->n_runs = h->n_runs;
   return LBM_OK;
 }
 

@@ -81,6 +81,8 @@ class lbm_info(ctypes.Structure):
         ("D", ctypes.c_int32),
         ("precision", ctypes.c_int32),
         ("real_bytes", ctypes.c_int32),
+        ("n_stored", ctypes.c_int64),
+        ("n_runs", ctypes.c_int64),
     ]
 
 

@@ -270,8 +270,8 @@ def test_invalid_geometry_is_rejected(L):
 
 
 def test_bad_configs_are_rejected(L):
-    for kw in (dict(tau=0.5), dict(stencil=0, nz=2), dict(collision=1), dict(stencil=1, inlet=1, periodic=(0, 1, 1)),
-               dict(precision=7)):
+    for kw in (dict(tau=0.5), dict(stencil=0, nz=2), dict(stencil=1, collision=1), dict(collision=5),
+               dict(stencil=1, inlet=1, periodic=(0, 1, 1)), dict(precision=7), dict(vibb_density=3)):
         base = dict(stencil=0, nx=8, ny=8, nz=1, tau=0.8)
         base.update(kw)
         with pytest.raises(L.LBMError):
@@ -369,3 +369,22 @@ def test_sphere_pack_32_local_density(L, prec):
     the 384^3 porous workload."""
     geo = G.sphere_pack(32, porosity=0.40, rmin=3.0, rmax=6.0, seed=7)
     _compare(L, geo, 200, _p(L, prec), tau=0.7, g=(1e-5, 0, 0), bc=2, vibb_density=1)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+@pytest.mark.parametrize("bc", [0, 1, 2])
+def test_mrt_rotating_cylinder(L, bc, prec):
+    """MRT collision (Sec. 2, Eq. mrt, the paper's own operator) with every
+    link rule around a rotating off-grid cylinder."""
+    geo = G.build(0, (45, 33, 1), (1, 1, 1), [G.ball((20.37, 15.61, 0), 6.3, omega=(0, 0, 0.004), force_id=0)])
+    _compare(L, geo, 200, _p(L, prec), tau=0.62, g=(2e-5, 1e-5, 0), bc=bc, collision=1)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_mrt_open_channel_cylinder(L, prec):
+    geo = G.cylinder_channel(nx=120, ny_fluid=30, center=(30.37, 15.61), radius=4.3)
+    y = (np.arange(geo.N) // geo.nx) % geo.ny
+    u0 = np.zeros((geo.N, 3))
+    u0[:, 0] = np.where(geo.solid == 0, 4 * 0.05 * (y - 0.5) * (30.5 - y) / 30 ** 2, 0.0)
+    _compare(L, geo, 200, _p(L, prec), nbody=1, init_u=u0, tau=0.56, bc=2, collision=1, inlet_umax=0.05,
+             inlet_y0=0.5, inlet_y1=30.5)

@@ -575,3 +575,26 @@ def test_vibb_local_density_reading(stencil):
                 wall = 6 * w[ip] * float(e[opp[ip]] @ uw)
                 expect = (O.feq(stencil, rf(0), uf(2 * q - 1))[ip] + rf(0) * (af + (af - aff) * (2 * q - 1)) + wall)
                 assert abs(b - expect) < 5e-15
+
+
+def test_mrt_poiseuille_curvature_and_halfway_convergence():
+    """MRT (Sec. 2): steady Poiseuille flow has bulk curvature -g/nu with
+    nu = (1/s_7 - 1/2)/3, and Bouzidi walls at q = 0.3 converge at second
+    order."""
+    errs = []
+    for H in (8, 16, 32):
+        g = G.channel(0, 2, H, q_lo=0.3, q_hi=0.3)
+        cfg = _cfg_for(g, tau=0.8, g=(1e-6, 0, 0), bc=1, collision=1)
+        st = O.init(cfg, g.solid)
+        nu = 0.1
+        Hw = g.info["y_hi"] - g.info["y_lo"]
+        O.run(cfg, g.solid, g.links, st, int(32 * Hw * Hw / (nu * np.pi ** 2)))
+        y = np.arange(1, H + 1)
+        ux = st.u.reshape(g.ny, g.nx, 3)[1:H + 1, 0, 0]
+        ex = G.poiseuille_profile(y, g.info["y_lo"], g.info["y_hi"], 1e-6, nu)
+        if H == 32:
+            d2 = ux[2:] - 2 * ux[1:-1] + ux[:-2]
+            np.testing.assert_allclose(d2[2:-2], -1e-6 / nu, rtol=1e-7)
+        errs.append(np.sqrt(((ux - ex) ** 2).sum() / (ex ** 2).sum()))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert orders.min() > 1.8, (errs, orders)
