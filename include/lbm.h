@@ -214,6 +214,34 @@ lbm_status lbm_query(lbm_handle h, lbm_info* info);
 lbm_status lbm_set_profiling(lbm_handle h, int32_t on);
 lbm_status lbm_kernel_times(lbm_handle h, int64_t launches[3], double ms[3]);
 
+/* For callers that cannot allocate device memory (code inside a CUDA graph
+ * capture or on a real-time path, or a framework whose own pool owns all
+ * device memory): the momentum-exchange force on `body` of the step that
+ * follows a given state, computed from memory the caller owns.  No
+ * counterpart in the paper: it is a packaging of lbm_force for such callers.
+ *  cfg      the lattice's configuration (stencil, sizes, periodic axes,
+ *           open columns, rho0, g, bc, vibb_density; precision is ignored).
+ *  f_post   device, FP64 [Q][N]: post-collision populations f+(x, t) as
+ *           returned by lbm_get_distributions.
+ *  solid    device, N bytes (nonzero = solid); links: device, n_links
+ *           lbm_link records as given to lbm_set_geometry.
+ *  F        device, 3 doubles: receives the force of step t -> t+1, the value
+ *           lbm_force(body) reports after lbm_step(1) from the same state
+ *           (moments are recomputed from f+, so the two agree to rounding).
+ * Work is queued on cfg->cuda_stream (NULL: the legacy default stream) and
+ * the call returns without synchronising.  It allocates nothing: its block
+ * partial sums live in a static device array of 3 x 65,536 doubles
+ * (1.5 MiB, held by every GPU that loads the library until exit), so
+ * n_links is limited to LBM_NOALLOC_MAX_LINKS; larger counts return
+ * LBM_ERR_INVALID_ARG.  The first call on a device looks up that array's
+ * device address (make it before any stream capture).  All calls share the
+ * array: calls that overlap on the GPU race; calls ordered on one stream do
+ * not, and each call overwrites every entry it reads.  Deterministic: the
+ * same inputs give the same bits.  Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+#define LBM_NOALLOC_MAX_LINKS 16777216
+lbm_status lbm_force_noalloc(const lbm_config* cfg, const double* f_post, const uint8_t* solid,
+                             const lbm_link* links, int64_t n_links, int32_t body, double* F);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* lbm_last_error(void);
 

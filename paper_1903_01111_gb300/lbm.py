@@ -105,6 +105,7 @@ _sig = {
     "lbm_query": [_H, _P(lbm_info)],
     "lbm_set_profiling": [_H, ctypes.c_int32],
     "lbm_kernel_times": [_H, _P(ctypes.c_int64), _P(ctypes.c_double)],
+    "lbm_force_noalloc": [_P(lbm_config), _vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32, _vp],
 }
 for _name, _args in _sig.items():
     _fn = getattr(_lib, _name)
@@ -239,6 +240,20 @@ def lbm_kernel_times(h):
     _check(_lib.lbm_kernel_times(h, n, ms))
     return list(n), list(ms)
 
+
+def lbm_force_noalloc(cfg: lbm_config, f_post, solid, links, n_links: int, body: int, F) -> None:
+    """Momentum-exchange force of the next step from caller-owned device
+    memory (torch CUDA tensors or raw device addresses); allocates nothing.
+    Queued on cfg.cuda_stream without synchronising."""
+    _check(_lib.lbm_force_noalloc(ctypes.byref(cfg), _ptr_or_int(f_post), _ptr_or_int(solid), _ptr_or_int(links),
+                                  int(n_links), int(body), _ptr_or_int(F)))
+
+
+def _ptr_or_int(a):
+    return a if isinstance(a, int) else _ptr(a)
+
+
+LBM_NOALLOC_MAX_LINKS = 16777216
 
 KERNEL_NAMES = ("k_links", "k_open", "k_bulk")
 
