@@ -85,6 +85,8 @@ def _load():
         lib.oracle_run.argtypes = [P(OracleConfig), P(u8), ctypes.c_void_p, i64, P(d), P(d), P(d), i64, P(d),
                                    ctypes.c_int]
         lib.oracle_moments.argtypes = [P(OracleConfig), P(u8), P(d), P(d), P(d)]
+        lib.oracle_run_dual.argtypes = [P(OracleConfig), P(u8), ctypes.c_void_p, i64, P(d), P(d), ctypes.c_void_p,
+                                        ctypes.c_void_p, i64, P(d), P(d), ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -211,3 +213,25 @@ def moments(cfg: OracleConfig, solid, fp):
     _check(_load().oracle_moments(ctypes.byref(cfg), solid.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
                                   _dp(fp), _dp(r), _dp(uu)))
     return r, uu.reshape(N, 3)
+
+
+def run_dual(cfg: OracleConfig, solid, links, dq, dtau, nsteps: int, nbody: int = 1, rho=None, u=None):
+    """Forward-mode (dual number) derivatives of the force of the last of
+    ``nsteps`` steps from the oracle_init state, with respect to 4 parameters:
+    ``dq`` (n_links, 4) derivatives of each link's q, ``dtau`` (4,).
+    Returns F (nbody, 3) and dF (nbody, 3, 4)."""
+    N = cfg.nx * cfg.ny * cfg.nz
+    solid = np.ascontiguousarray(solid, np.uint8).reshape(-1)
+    links = np.ascontiguousarray(links, dtype=LINK_DTYPE)
+    dq = np.ascontiguousarray(dq, np.float64).reshape(len(links), 4)
+    dtau = np.ascontiguousarray(dtau, np.float64).reshape(4)
+    F = np.zeros(nbody * 3)
+    dF = np.zeros(nbody * 3 * 4)
+    rho_p = None if rho is None else np.ascontiguousarray(rho, np.float64).reshape(N)
+    u_p = None if u is None else np.ascontiguousarray(u, np.float64).reshape(N, 3)
+    _check(_load().oracle_run_dual(ctypes.byref(cfg), solid.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                   links.ctypes.data if links.size else None, int(links.size), _dp(dq), _dp(dtau),
+                                   None if rho_p is None else rho_p.ctypes.data,
+                                   None if u_p is None else u_p.ctypes.data, int(nsteps), _dp(F), _dp(dF),
+                                   int(nbody)))
+    return F.reshape(nbody, 3), dF.reshape(nbody, 3, 4)

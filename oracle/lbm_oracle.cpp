@@ -97,16 +97,74 @@ struct oracle_link {
 
 namespace {
 
+// Forward-mode dual number with K derivative components: every arithmetic
+// operation applies the chain rule to the derivative part.
+template <int K>
+struct Dual {
+  double v;
+  double d[K];
+  Dual(double x = 0.0) : v(x) {
+    for (int k = 0; k < K; ++k) d[k] = 0.0;
+  }
+};
+template <int K>
+Dual<K> operator+(const Dual<K>& a, const Dual<K>& b) {
+  Dual<K> r(a.v + b.v);
+  for (int k = 0; k < K; ++k) r.d[k] = a.d[k] + b.d[k];
+  return r;
+}
+template <int K>
+Dual<K> operator-(const Dual<K>& a, const Dual<K>& b) {
+  Dual<K> r(a.v - b.v);
+  for (int k = 0; k < K; ++k) r.d[k] = a.d[k] - b.d[k];
+  return r;
+}
+template <int K>
+Dual<K> operator-(const Dual<K>& a) {
+  Dual<K> r(-a.v);
+  for (int k = 0; k < K; ++k) r.d[k] = -a.d[k];
+  return r;
+}
+template <int K>
+Dual<K> operator*(const Dual<K>& a, const Dual<K>& b) {
+  Dual<K> r(a.v * b.v);
+  for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+  return r;
+}
+template <int K>
+Dual<K> operator/(const Dual<K>& a, const Dual<K>& b) {
+  Dual<K> r(a.v / b.v);
+  for (int k = 0; k < K; ++k) r.d[k] = (a.d[k] * b.v - a.v * b.d[k]) / (b.v * b.v);
+  return r;
+}
+template <int K> Dual<K> operator+(const Dual<K>& a, double b) { return a + Dual<K>(b); }
+template <int K> Dual<K> operator+(double a, const Dual<K>& b) { return Dual<K>(a) + b; }
+template <int K> Dual<K> operator-(const Dual<K>& a, double b) { return a - Dual<K>(b); }
+template <int K> Dual<K> operator-(double a, const Dual<K>& b) { return Dual<K>(a) - b; }
+template <int K> Dual<K> operator*(const Dual<K>& a, double b) { return a * Dual<K>(b); }
+template <int K> Dual<K> operator*(double a, const Dual<K>& b) { return Dual<K>(a) * b; }
+template <int K> Dual<K> operator/(const Dual<K>& a, double b) { return a / Dual<K>(b); }
+template <int K> Dual<K> operator/(double a, const Dual<K>& b) { return Dual<K>(a) / b; }
+template <int K> bool operator<=(const Dual<K>& a, double b) { return a.v <= b; }
+template <int K> bool operator>(const Dual<K>& a, double b) { return a.v > b; }
+
+inline double value_of(double x) { return x; }
+template <int K>
+double value_of(const Dual<K>& x) {
+  return x.v;
+}
+
 template <class T>
 struct Oracle {
   oracle_config c;
+  T tau;  // relaxation time (a scalar of type T so that it can carry derivatives)
   int Q, D;
   int e[19][3];
   double w[19];
   int opp[19];
   int64_t N;
 
-  explicit Oracle(const oracle_config& cfg) : c(cfg) {
+  explicit Oracle(const oracle_config& cfg) : c(cfg), tau(cfg.tau) {
     if (c.stencil == 0) {
       Q = 9;
       D = 2;
@@ -166,7 +224,7 @@ struct Oracle {
     return w[i] * s;
   }
   // BGK form of the Guo term: (1 - 1/(2 tau)) times the source.
-  T force_term(int i, const T u[3]) const { return (1.0 - 0.5 / c.tau) * force_source(i, u); }
+  T force_term(int i, const T u[3]) const { return (1.0 - 0.5 / tau) * force_source(i, u); }
 
   // Moments of Sec. 2 plus the half-force velocity shift, then the collision:
   // BGK  f+ = f - (f - feq)/tau + F_i, or MRT  f+ = f - M^-1 S (m - meq) + F_i.
@@ -179,7 +237,7 @@ struct Oracle {
     }
     for (int a = 0; a < 3; ++a) u[a] = (j[a] + 0.5 * c.g[a]) / rho;
     if (c.collision == 0) {
-      for (int i = 0; i < Q; ++i) fp[i] = f[i] - (f[i] - feq(i, rho, u)) / c.tau + force_term(i, u);
+      for (int i = 0; i < Q; ++i) fp[i] = f[i] - (f[i] - feq(i, rho, u)) / tau + force_term(i, u);
       return;
     }
     // MRT, Eq. (mrt): m = M f; equilibrium moments of Sec. 2 written with the
@@ -202,9 +260,9 @@ struct Oracle {
     meq[6] = -jy;
     meq[7] = (jx * jx - jy * jy) / rho;
     meq[8] = jx * jy / rho;
-    const double nu = (c.tau - 0.5) / 3.0;
-    const double sv = 1.0 / (3.0 * nu + 0.5);
-    const double s[9] = {0.3, 1.5, 1.5, 0.3, 1.2, 0.3, 1.2, sv, sv};
+    const T nu = (tau - 0.5) / 3.0;
+    const T sv = 1.0 / (3.0 * nu + 0.5);
+    const T s[9] = {0.3, 1.5, 1.5, 0.3, 1.2, 0.3, 1.2, sv, sv};
     // M^-1 = M^T diag(1/|row_k|^2) because the rows of M are orthogonal.
     double norm2[9];
     for (int k = 0; k < 9; ++k) {
@@ -235,7 +293,7 @@ struct Oracle {
   // Missing population f_i(x_f, t+1) of one link (i = opp(i')), from the
   // post-collision populations at x_f (fp_f) and x_ff (fp_ff), and the
   // moments at time t at both nodes.
-  T link_value(int rule, int ip, double q, const double uw[3], const T* fp_f, const T* fp_ff, const T& rf,
+  T link_value(int rule, int ip, const T& q, const double uw[3], const T* fp_f, const T* fp_ff, const T& rf,
                const T uf[3], const T& rff, const T uff[3]) const {
     const int i = opp[ip];
     // moving-wall momentum term 6 w_i' rho0 (e_i . u_w) / C^2 (Ladd)
@@ -292,7 +350,7 @@ std::vector<uint8_t> node_types(const Oracle<T>& o, const uint8_t* solid) {
 // exchange of this step per body.  Returns 0, or -1 with g_err set.
 template <class T>
 int step_once(const Oracle<T>& o, const std::vector<uint8_t>& type, const oracle_link* links, int64_t nl, T* fp,
-              T* rho, T* u, std::vector<T>& fnew, double* force, int nbody) {
+              T* rho, T* u, std::vector<T>& fnew, T* force, int nbody, const T* qv) {
   const int Q = o.Q;
   const int64_t N = o.N;
   // 1. open boundary columns at time t (Sec. 4.3)
@@ -353,11 +411,11 @@ int step_once(const Oracle<T>& o, const std::vector<uint8_t>& type, const oracle
     const T uf[3] = {u[3 * f], u[3 * f + 1], u[3 * f + 2]};
     const T uff[3] = {u[3 * ff], u[3 * ff + 1], u[3 * ff + 2]};
     const int rule = L.bc >= 0 ? L.bc : o.c.bc;
-    const T val = o.link_value(rule, ip, L.q, L.uw, fpf, fpff, rho[f], uf, rho[ff], uff);
+    const T val = o.link_value(rule, ip, qv[k], L.uw, fpf, fpff, rho[f], uf, rho[ff], uff);
     fnew[i * N + f] = val;
     // momentum exchange (Ladd): (f+_i'(x_f,t) + f_i(x_f,t+1)) e_i' on the solid
     if (L.body >= 0 && L.body < nbody)
-      for (int a = 0; a < 3; ++a) force[3 * L.body + a] += (double)((fpf[ip] + val) * o.e[ip][a]);
+      for (int a = 0; a < 3; ++a) force[3 * L.body + a] = force[3 * L.body + a] + (fpf[ip] + val) * (double)o.e[ip][a];
   }
   // 4. moments and collision at fluid nodes
   T f[19], fo[19];
@@ -365,7 +423,7 @@ int step_once(const Oracle<T>& o, const std::vector<uint8_t>& type, const oracle
     if (type[n] != NODE_FLUID) continue;
     for (int i = 0; i < Q; ++i) {
       f[i] = fnew[i * N + n];
-      if (std::isnan((double)f[i])) {
+      if (std::isnan(value_of(f[i]))) {
         int64_t x[3];
         o.coords(n, x);
         snprintf(g_err, sizeof g_err,
@@ -499,8 +557,10 @@ int oracle_run(const oracle_config* cfg, const uint8_t* solid, const oracle_link
   }
   std::vector<double> fnew((size_t)o.Q * o.N);
   std::vector<double> fbuf(nbody > 0 ? nbody * 3 : 3);
+  std::vector<double> qv(nl);
+  for (int64_t k = 0; k < nl; ++k) qv[k] = links[k].q;
   for (int64_t s = 0; s < nsteps; ++s) {
-    if (step_once(o, type, links, nl, fp, rho, u, fnew, fbuf.data(), nbody) != 0) return -1;
+    if (step_once(o, type, links, nl, fp, rho, u, fnew, fbuf.data(), nbody, qv.data()) != 0) return -1;
   }
   if (force)
     for (int b = 0; b < nbody * 3; ++b) force[b] = fbuf[b];
@@ -526,6 +586,56 @@ int oracle_moments(const oracle_config* cfg, const uint8_t* solid, const double*
     }
     rho[n] = r;
     for (int a = 0; a < 3; ++a) u[3 * n + a] = (j[a] - 0.5 * cfg->g[a]) / r;
+  }
+  return 0;
+}
+
+// Forward-mode derivatives (dual numbers, K = 4 parameters) of the
+// momentum-exchange force of the last of nsteps steps from the initial state
+// of oracle_init.  dq: n_links x 4 derivatives of each link's q; dtau: 4
+// derivatives of tau.  F: nbody x 3 forces; dF: nbody x 3 x 4 derivatives.
+int oracle_run_dual(const oracle_config* cfg, const uint8_t* solid, const oracle_link* links, int64_t nl,
+                    const double* dq, const double* dtau, const double* rho_in, const double* u_in, int64_t nsteps,
+                    double* F, double* dF, int nbody) {
+  constexpr int K = 4;
+  using D = Dual<K>;
+  if (!check_config(cfg)) return -1;
+  Oracle<D> o(*cfg);
+  for (int k = 0; k < K; ++k) o.tau.d[k] = dtau[k];
+  const std::vector<uint8_t> type = node_types(o, solid);
+  const int64_t N = o.N;
+  for (int64_t k = 0; k < nl; ++k) {
+    const oracle_link& L = links[k];
+    if (L.node < 0 || L.node >= N || L.dir <= 0 || L.dir >= o.Q || !(L.q > 0.0 && L.q <= 1.0) ||
+        type[L.node] != NODE_FLUID) {
+      snprintf(g_err, sizeof g_err, "link %lld is invalid", (long long)k);
+      return -1;
+    }
+  }
+  std::vector<D> qv(nl);
+  for (int64_t k = 0; k < nl; ++k) {
+    qv[k] = D(links[k].q);
+    for (int j = 0; j < K; ++j) qv[k].d[j] = dq[k * K + j];
+  }
+  std::vector<D> fp((size_t)o.Q * N), rho(N), u(3 * N), fnew((size_t)o.Q * N);
+  for (int64_t n = 0; n < N; ++n) {
+    if (type[n] != NODE_FLUID) continue;
+    const D r0(rho_in ? rho_in[n] : cfg->rho0);
+    const D u0[3] = {D(u_in ? u_in[3 * n] : 0.0), D(u_in ? u_in[3 * n + 1] : 0.0), D(u_in ? u_in[3 * n + 2] : 0.0)};
+    D f[19], fo[19], uu[3], r;
+    for (int i = 0; i < o.Q; ++i) f[i] = o.feq(i, r0, u0);
+    o.collide(f, fo, r, uu);
+    rho[n] = r;
+    for (int a = 0; a < 3; ++a) u[3 * n + a] = uu[a];
+    for (int i = 0; i < o.Q; ++i) fp[i * N + n] = fo[i];
+  }
+  std::vector<D> fbuf(nbody > 0 ? nbody * 3 : 3);
+  for (int64_t s = 0; s < nsteps; ++s)
+    if (step_once(o, type, links, nl, fp.data(), rho.data(), u.data(), fnew, fbuf.data(), nbody, qv.data()) != 0)
+      return -1;
+  for (int b = 0; b < nbody * 3; ++b) {
+    F[b] = fbuf[b].v;
+    for (int k = 0; k < K; ++k) dF[b * K + k] = fbuf[b].d[k];
   }
   return 0;
 }

@@ -389,3 +389,26 @@ def sphere_pack(n=384, porosity=0.40, rmin=6.0, rmax=14.0, seed=0, batch=4096) -
     links = _links(D3Q19, shape, (True, True, True), bodies, mask, (False, False))
     return Geometry(D3Q19, n, n, n, (True, True, True), mask, links, (False, False), bodies,
                     dict(kind="sphere_pack", porosity=1.0 - solid.value / N, spheres=len(radii), seed=seed))
+
+
+def ball_q_derivatives(geo: Geometry, body_index: int) -> np.ndarray:
+    """Derivatives of q with respect to (c_x, c_y, c_z, R) of ball
+    ``geo.bodies[body_index]`` for every link whose wall crossing lies on that
+    ball (zero rows elsewhere): with d = x_w - c and x_w = x_f + q e,
+    |x_f + q e - c|^2 = R^2 gives dq/dc = d / (d.e) and dq/dR = R / (d.e)."""
+    b = geo.bodies[body_index]
+    E = velocity_set(geo.stencil).astype(np.float64)
+    out = np.zeros((len(geo.links), 4))
+    x, y, z = geo.coords(geo.links["node"])
+    xf = np.stack([x, y, z], 1).astype(np.float64)
+    e = E[geo.links["dir"]]
+    xw = xf + geo.links["q"][:, None] * e
+    d = xw - b["c"]
+    for a, L in enumerate(geo.shape):
+        if geo.periodic[a]:
+            d[:, a] -= L * np.floor(d[:, a] / L + 0.5)
+    on = np.abs(np.sqrt((d * d).sum(1)) - b["r"]) < 1e-9 * max(1.0, b["r"])
+    de = (d * e).sum(1)
+    out[on, :3] = d[on] / de[on, None]
+    out[on, 3] = b["r"] / de[on]
+    return out

@@ -598,3 +598,48 @@ def test_mrt_poiseuille_curvature_and_halfway_convergence():
         errs.append(np.sqrt(((ux - ex) ** 2).sum() / (ex ** 2).sum()))
     orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert orders.min() > 1.8, (errs, orders)
+
+
+def _cylinder_case(c, R, tau):
+    bodies = [G.ball((c[0], c[1], 0), R, force_id=0)]
+    return G.build(0, (34, 24, 1), (1, 1, 1), bodies)
+
+
+@pytest.mark.parametrize("bc,vd", [(2, 0), (2, 1), (1, 0)])
+def test_dual_gradient_matches_finite_differences(bc, vd):
+    """Forward-mode derivatives of the drag after 60 steps with respect to the
+    cylinder centre, radius and tau equal central differences of the plain
+    oracle with the geometry rebuilt at the perturbed parameters (the link
+    set does not change for these small steps)."""
+    c, R, tau = (15.37, 11.61), 5.23, 0.72
+    gvec = (2e-5, 0.0, 0.0)
+    geo = _cylinder_case(c, R, tau)
+    cfg = O.make_config(stencil=0, nx=geo.nx, ny=geo.ny, nz=1, tau=tau, g=gvec, bc=bc, vibb_density=vd)
+    dq = G.ball_q_derivatives(geo, 0)
+    dq[:, 2] = dq[:, 3]  # parameters: (c_x, c_y, R, tau)
+    dq[:, 3] = 0.0
+    F, dF = O.run_dual(cfg, geo.solid, geo.links, dq, [0, 0, 0, 1.0], 60)
+    st = O.init(cfg, geo.solid)
+    F0 = O.run(cfg, geo.solid, geo.links, st, 60)
+    assert np.allclose(F, F0, rtol=0, atol=1e-15)
+    h = 1e-4  # fourth-order central difference: truncation ~h^4, roundoff ~1e-15/h
+    fd = np.zeros(4)
+    for k in range(4):
+        vals = []
+        for sgn in (2, 1, -1, -2):
+            cc, RR, tt = list(c), R, tau
+            if k < 2:
+                cc[k] += sgn * h
+            elif k == 2:
+                RR += sgn * h
+            else:
+                tt += sgn * h
+            g2 = _cylinder_case(cc, RR, tt)
+            assert np.array_equal(g2.links["node"], geo.links["node"]) and np.array_equal(g2.links["dir"],
+                                                                                          geo.links["dir"])
+            cfg2 = O.make_config(stencil=0, nx=geo.nx, ny=geo.ny, nz=1, tau=tt, g=gvec, bc=bc, vibb_density=vd)
+            s2 = O.init(cfg2, g2.solid)
+            vals.append(O.run(cfg2, g2.solid, g2.links, s2, 60)[0, 0])
+        fd[k] = (8 * (vals[1] - vals[2]) - (vals[0] - vals[3])) / (12 * h)
+    err = np.abs(dF[0, 0] - fd)
+    assert np.all(err <= 1e-5 * np.abs(fd) + 1e-9 * np.abs(fd).max()), (dF[0, 0], fd)
