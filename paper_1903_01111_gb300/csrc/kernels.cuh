@@ -36,13 +36,18 @@
 
 namespace lbm {
 
+// bulk_min_blocks: resident 256-thread blocks per SM the bulk kernel is
+// compiled for (FP32: 5, FP64: 2; 6 for FP32 forces spills and ran slower on
+// the porous workload).
 struct F64 {
   using T = double;
   static constexpr bool shifted = false;
+  static constexpr int bulk_min_blocks = 2;
 };
 struct F32S {
   using T = float;
   static constexpr bool shifted = true;
+  static constexpr int bulk_min_blocks = 5;
 };
 
 // One moment-cache record per node: (r, ux, uy, uz) with r = rho (F64) or
@@ -198,7 +203,7 @@ __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Pa
 // One thread per stored node; block (0) also clears the force slot of the
 // next step.
 template <class L, class P>
-__global__ void __launch_bounds__(256) k_bulk(const typename P::T* __restrict__ fin, typename P::T* __restrict__ fout,
+__global__ void __launch_bounds__(256, P::bulk_min_blocks) k_bulk(const typename P::T* __restrict__ fin, typename P::T* __restrict__ fout,
                                               Layout lay, Mom4<typename P::T>* __restrict__ mom,
                                               double* __restrict__ force_next, Params p) {
   using T = typename P::T;
@@ -351,7 +356,9 @@ __global__ void __launch_bounds__(256) k_links(typename P::T* __restrict__ f, co
   }
   __syncthreads();
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  double F0 = 0.0, F1 = 0.0, F2 = 0.0;
+  // lane and warp partial sums in the storage precision (FP32 sums of the
+  // small shifted terms), block sums and the accumulator in FP64
+  T F0 = 0, F1 = 0, F2 = 0;
   int body = -1;
   if (k < nl) {
     const LinkRec rec = recs[k];
@@ -387,12 +394,13 @@ __global__ void __launch_bounds__(256) k_links(typename P::T* __restrict__ f, co
                                 p.vibb_local_rho);
     f[(size_t)i * N + s] = val;
     if (body >= 0) {
-      // momentum exchange (f+_i'(x_f,t) + f_i(x_f,t+1)) e_i', FP64; shifted
-      // storage adds back the two rest parts w rho0
-      const double t = (double)fpf + (double)val + (P::shifted ? 2.0 * (double)w * p.rho0 : 0.0);
-      F0 = t * (double)ex;
-      F1 = t * (double)ey;
-      F2 = t * (double)ez;
+      // momentum exchange (f+_i'(x_f,t) + f_i(x_f,t+1)) e_i'.  In shifted
+      // storage this sums (h+_i' + h_i) e_i'; the rest part 2 w_i' rho0 e_i'
+      // of every link is a geometric constant that the host adds in FP64.
+      const T t = fpf + val;
+      F0 = t * ex;
+      F1 = t * ey;
+      F2 = t * ez;
     }
   }
   // block reduction: one atomic per component when the block has one body
@@ -404,9 +412,9 @@ __global__ void __launch_bounds__(256) k_links(typename P::T* __restrict__ f, co
   const int uniform = __syncthreads_and(body == b0 || body < 0);
   if (!uniform) {
     if (body >= 0) {
-      atomicAdd(&force[3 * body + 0], F0);
-      atomicAdd(&force[3 * body + 1], F1);
-      atomicAdd(&force[3 * body + 2], F2);
+      atomicAdd(&force[3 * body + 0], (double)F0);
+      atomicAdd(&force[3 * body + 1], (double)F1);
+      atomicAdd(&force[3 * body + 2], (double)F2);
     }
     return;
   }
@@ -419,27 +427,16 @@ __global__ void __launch_bounds__(256) k_links(typename P::T* __restrict__ f, co
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) {
-    red[0][warp] = F0;
-    red[1][warp] = F1;
-    red[2][warp] = F2;
+    red[0][warp] = (double)F0;
+    red[1][warp] = (double)F1;
+    red[2][warp] = (double)F2;
   }
   __syncthreads();
-  if (warp == 0) {
+  if (threadIdx.x < 3) {
     const int nw = (blockDim.x + 31) >> 5;
-    F0 = lane < nw ? red[0][lane] : 0.0;
-    F1 = lane < nw ? red[1][lane] : 0.0;
-    F2 = lane < nw ? red[2][lane] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      F0 += __shfl_down_sync(0xffffffffu, F0, o);
-      F1 += __shfl_down_sync(0xffffffffu, F1, o);
-      F2 += __shfl_down_sync(0xffffffffu, F2, o);
-    }
-    if (lane == 0) {
-      atomicAdd(&force[3 * b0 + 0], F0);
-      atomicAdd(&force[3 * b0 + 1], F1);
-      atomicAdd(&force[3 * b0 + 2], F2);
-    }
+    double acc = 0.0;
+    for (int wi = 0; wi < nw; ++wi) acc += red[threadIdx.x][wi];
+    atomicAdd(&force[3 * b0 + threadIdx.x], acc);
   }
 }
 

@@ -73,6 +73,9 @@ struct lbm_lattice_s {
   DeviceBuf recs, q, uw;
   int64_t n_links = 0, n_fluid = 0, n_cached = 0, n_runs = 0;
   DeviceBuf force;  // [2][MAX_BODIES][3]
+  // shifted storage: sum over each body's links of 2 w_i' rho0 e_i' (FP64),
+  // the rest part of the momentum exchange that the link kernel leaves out
+  std::vector<double> force_rest = std::vector<double>(3 * MAX_BODIES, 0.0);
   int cur = 0;      // buffer holding f+(t)
   int64_t step = 0;
   bool has_geometry = false, has_state = false;
@@ -557,6 +560,18 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
     else
       n_cached += (m[n] & H_CACHE) ? 1 : 0;
   }
+  // rest part of the momentum exchange per body (shifted storage)
+  std::vector<double> rest(3 * MAX_BODIES, 0.0);
+  if (c.precision == LBM_FP32_SHIFTED)
+    for (int64_t k = 0; k < n_links; ++k) {
+      const lbm_link& L = links[k];
+      if (L.body < 0) continue;
+      const double w = h->Q == 9 ? D2Q9::w(L.dir) : D3Q19::w(L.dir);
+      const double t = 2.0 * w * c.rho0;
+      rest[3 * L.body + 0] += t * cx_of(h, L.dir);
+      rest[3 * L.body + 1] += t * cy_of(h, L.dir);
+      rest[3 * L.body + 2] += t * cz_of(h, L.dir);
+    }
   // link records in the chosen order
   std::vector<LinkRec> recs(n_links);
   std::vector<double> qs(n_links);
@@ -617,6 +632,7 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
   h->n_fluid = n_fluid;
   h->n_cached = n_cached;
   h->n_runs = (int64_t)runs.size();
+  h->force_rest.swap(rest);
   h->has_geometry = true;
   return LBM_OK;
 }
@@ -737,6 +753,7 @@ lbm_status lbm_force(lbm_handle h, int32_t body, double F[3]) {
   const double* slot = (const double*)h->force.p + 3 * MAX_BODIES * ((h->step - 1) & 1) + 3 * body;
   CUDA_TRY(cudaMemcpyAsync(F, slot, sizeof(double) * 3, cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
+  for (int a = 0; a < 3; ++a) F[a] += h->force_rest[3 * body + a];
   return LBM_OK;
 }
 
