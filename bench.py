@@ -31,7 +31,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "MLUPS and % HBM roofline (FP32 vs FP64)"
+METRIC = "MLUPS and % HBM roofline (FP32 vs FP64); adjoint/forward step cost ratio"
 WORKLOAD = ("D3Q19 BGK body-force flow through a periodic random overlapping sphere pack: 384^3 lattice, "
             "radii U[6,14], seed 0, porosity 0.40, tau 0.7, g 1e-6, VIBB links (rho_d = rho_f for q > 1/2)")
 Q3 = 19
@@ -172,8 +172,8 @@ def run_precision(lbm, torch, geo, precision, steps, warmup, dist, peak):
     bulk_ms = kms[2] / max(n_launch[2], 1)
     link_ms = kms[0] / max(n_launch[0], 1)
     bulk_bytes = nf * (2 * Q3 * s + 1)  # algorithmic bytes per bulk launch
-    # per link: packed key 8 B, q, f+_i'(x_f), f+_i'(x_ff), moments (1 + D) at x_f and x_ff, one write
-    link_bytes = nl * (8 + s + 2 * s + 2 * (1 + 3) * s + s)
+    # per link: its 16 B record, q, f+_i'(x_f), f+_i'(x_ff), the moment records at x_f and x_ff, one write
+    link_bytes = nl * (16 + s + 2 * s + 2 * 4 * s + s)
     bulk_gbs = bulk_bytes / (bulk_ms * 1e-3) / 1e9
     link_gbs = link_bytes / (link_ms * 1e-3) / 1e9
     return {
@@ -245,6 +245,151 @@ def run_sweep(lbm, torch, steps, peak):
                 "mlups": nf * n / (ms * 1e-3) / 1e6, "ms_per_step": ms / n, "steps": n,
                 "bytes_per_node": 2 * Q * s + 1, "bulk_avg_ms": bulk_ms, "roofline": r}
     return out
+
+
+def run_adjoint(lbm, n_steps=20000, checkpoint_every=500, fd=True):
+    """Drag gradient on the 1024 x 256 channel cylinder (radius 16.494, centre
+    (256.343, 128.626), u_max 0.1, Re 40 on the mean inflow and the diameter):
+    FP32-shifted forward and adjoint with FP64 sensitivity accumulation, cost
+    per step of the backward sweep (recompute + adjoint) over a forward step,
+    and an FP64 fourth-order central-difference check (steps 1e-3, 2e-3) of
+    dJ/dR and dJ/dtau; the centre and radius keep every cut link at least
+    4e-3 (in theta) away from the q = 1/2 branch switch."""
+    from paper_1903_01111_gb300.autograd import CylinderSpec, branch_margin, force_only, run
+
+    ubar = 2.0 / 3.0 * 0.1
+    R = 16.494
+    nu = ubar * 2 * R / 40.0
+    tau = 3 * nu + 0.5
+    theta = np.array([256.343, 128.626, R, tau])
+    spec = CylinderSpec(kind="channel", nx=1024, ny_fluid=256, u_max=0.1, n_steps=n_steps,
+                        checkpoint_every=checkpoint_every, precision=lbm.LBM_FP32_SHIFTED)
+    J32, g32 = run(spec, theta)
+    sec = spec.last["seconds"]
+    out = {"workload": "D2Q9 1024x256 channel, cylinder R 16.494 at (256.343, 128.626), u_max 0.1, Re 40, "
+                       f"tau {tau:.4f}, {n_steps} steps, checkpoints every {checkpoint_every}",
+           "J_drag": J32, "grad_fp32": {"cx": g32[0], "cy": g32[1], "R": g32[2], "tau": g32[3]},
+           "forward_ms_per_step": sec[0] / n_steps * 1e3,
+           "backward_ms_per_step": (sec[1] + sec[2]) / n_steps * 1e3,
+           "recompute_ms_per_step": sec[1] / n_steps * 1e3, "adjoint_ms_per_step": sec[2] / n_steps * 1e3,
+           "ratio_backward_to_forward": (sec[1] + sec[2]) / sec[0],
+           "ratio_adjoint_kernels_to_forward": sec[2] / sec[0]}
+    if fd:
+        spec64 = CylinderSpec(kind="channel", nx=1024, ny_fluid=256, u_max=0.1, n_steps=n_steps,
+                              checkpoint_every=checkpoint_every, precision=lbm.LBM_FP64)
+        J64, g64 = run(spec64, theta)
+        checks = {"branch_margin": branch_margin(spec64, theta)}
+        h = 1e-3
+
+        def diff(k, step):
+            tp, tm = theta.copy(), theta.copy()
+            tp[k] += step
+            tm[k] -= step
+            return (force_only(spec64, tp) - force_only(spec64, tm)) / (2 * step)
+
+        for k, name in ((2, "R"), (3, "tau")):
+            fd_k = (4 * diff(k, h) - diff(k, 2 * h)) / 3
+            checks[name] = {"adjoint_fp64": g64[k], "fd_fp64": fd_k, "rel_err_fp64": abs(g64[k] - fd_k) / abs(fd_k),
+                            "adjoint_fp32": g32[k], "rel_err_fp32_vs_fd": abs(g32[k] - fd_k) / abs(fd_k)}
+        out["fd_check"] = checks
+    return out
+
+
+def run_batch(lbm, torch, peak, n_domains=256, seed=0, steps=2000, warmup=10, adjoint_steps=1024, K=32):
+    """Batched channels: n_domains D2Q9 channels (sizes U[64,512] x U[64,256]
+    fluid rows, 1-8 non-overlapping cylinders with radii U[4,20], Re U[10,100]
+    on the channel height, u_max 0.1, VIBB cylinders, half-way walls,
+    velocity inlet and zero-gradient outlet) stacked in one lattice, FP32
+    shifted storage, autotuned launch shapes, graph replays; against the same
+    channels each run as its own FP64 lattice (per-domain launches on one
+    stream).  Both arms run `steps` steps from the Poiseuille initial state
+    and are timed over the last steps - warmup; the drag of every cylinder
+    after the last step is compared.  Then the batched adjoint of the summed
+    drag (every cylinder, FP32 with FP64 accumulation)."""
+    from paper_1903_01111_gb300 import batch as B
+
+    t0 = time.perf_counter()
+    specs = B.draw_channels(n_domains, seed)
+    b = B.stack(specs)
+    t_build = time.perf_counter() - t0
+    u0 = b.initial_velocity()
+    stream = torch.cuda.Stream()
+    lat = lbm.batch_lattice(b, precision=lbm.LBM_FP32_SHIFTED, bc=lbm.LBM_BC_VIBB, stream=stream.cuda_stream)
+    info = lat.info()
+    lat.init_equilibrium(u=u0)
+    tuning, tune_ms = lat.autotune(20)
+    lat.step(warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(steps - warmup)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms32 = e0.elapsed_time(e1)
+    F32 = lat.forces()
+    lat.check()
+    # kernel times of a few more steps (direct launches between events)
+    lbm.lbm_set_profiling(lat.h, True)
+    lat.step(50)
+    nlaunch, kms = lbm.lbm_kernel_times(lat.h)
+    lbm.lbm_set_profiling(lat.h, False)
+    lat.close()
+    nf = b.n_fluid
+    s = 4
+    bulk_ms = kms[2] / max(nlaunch[2], 1)
+    bulk_bytes = nf * (2 * 9 * s + 1)
+    mlups32 = nf * (steps - warmup) / (ms32 * 1e-3) / 1e6
+    # per-domain FP64 lattices on one stream
+    lats = []
+    for spec, geo in zip(specs, b.parts):
+        one = lbm.Lattice(geo, precision=lbm.LBM_FP64, bc=lbm.LBM_BC_VIBB, tau=spec.tau, stream=stream.cuda_stream,
+                          **spec.inlet())
+        one.init_equilibrium(u=spec.initial_velocity(geo))
+        lats.append(one)
+    for one in lats:
+        one.step(warmup)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for one in lats:
+        one.step(steps - warmup)
+    torch.cuda.synchronize()
+    s64 = time.perf_counter() - t1
+    F64 = np.concatenate([one.forces(len(spec.cylinders)) for one, spec in zip(lats, specs)])
+    for one in lats:
+        one.close()
+    mlups64 = nf * (steps - warmup) / s64 / 1e6
+    rel = np.abs(F32[:, 0] - F64[:, 0]) / np.abs(F64[:, 0])
+    # batched adjoint of the summed drag
+    lat = lbm.batch_lattice(b, precision=lbm.LBM_FP32_SHIFTED, bc=lbm.LBM_BC_VIBB, stream=stream.cuda_stream)
+    lat.set_tuning(bulk_shape=tuning.bulk_shape, link_threads=tuning.link_threads, graph_steps=tuning.graph_steps)
+    lat.init_equilibrium(u=u0)
+    w = np.zeros((b.n_bodies, 3))
+    w[:, 0] = 1.0
+    J, dq, dtau, sec = lbm.lbm_adjoint_step(lat.h, -1, w, adjoint_steps, K)
+    lat.close()
+    return {
+        "workload": f"{n_domains} D2Q9 channels (seed {seed}): nx U[64,512], fluid rows U[64,256], 1-8 cylinders "
+                    "r U[4,20], Re U[10,100] on the channel height, u_max 0.1; stacked in one lattice",
+        "lattice": [b.geometry.nx, b.geometry.ny], "fluid_nodes": nf, "links": int(info.n_links),
+        "bodies": int(b.n_bodies), "stored_nodes": int(info.n_stored), "build_s": t_build,
+        "tuning": tuning.as_dict(), "autotune_best_ms_per_step": tune_ms,
+        "fp32_batched": {"value": mlups32, "unit": "MLUPS", "ms_per_step": ms32 / (steps - warmup),
+                         "steps_timed": steps - warmup,
+                         "roofline": dict(roofline_entry(bulk_bytes, nf * FLOPS_PER_NODE[9], bulk_ms, s, peak),
+                                          kernel="k_bulk", bytes_per_launch=bulk_bytes, avg_launch_ms=bulk_ms),
+                         "kernel_ms": {"k_links": kms[0] / max(nlaunch[0], 1), "k_open": kms[1] / max(nlaunch[1], 1),
+                                       "k_bulk": bulk_ms}},
+        "fp64_per_domain": {"value": mlups64, "unit": "MLUPS", "ms_per_step": s64 * 1e3 / (steps - warmup),
+                            "launches_per_step": 3 * n_domains},
+        "speedup_fp32_batched_vs_fp64_per_domain": mlups32 / mlups64,
+        "drag_fp32_batched_vs_fp64": {"after_steps": steps, "max_rel": float(rel.max()),
+                                      "median_rel": float(np.median(rel)), "cylinders": int(rel.size)},
+        "adjoint": {"steps": adjoint_steps, "checkpoint_every": K, "J_sum_drag": J,
+                    "forward_ms_per_step": sec[0] / adjoint_steps * 1e3,
+                    "backward_ms_per_step": (sec[1] + sec[2]) / adjoint_steps * 1e3,
+                    "ratio_backward_to_forward": (sec[1] + sec[2]) / sec[0],
+                    "dJ_dtau_range": [float(np.min(dtau)), float(np.max(dtau))]},
+    }
 
 
 def run_e2e(lbm, torch, geo, steps):
@@ -340,6 +485,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--sweep-steps", type=int, default=100)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -371,6 +518,8 @@ def main():
         r64["clocks"] = clocks64.stop()
     e2e = None if args.no_e2e else run_e2e(lbm, torch, geo, args.steps)
     sweep = None if args.no_sweep else run_sweep(lbm, torch, args.sweep_steps, peak)
+    adjoint = None if args.no_adjoint else run_adjoint(lbm)
+    batched = None if args.no_batch else run_batch(lbm, torch, peak)
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = run_oracle(96, 16)
@@ -395,6 +544,10 @@ def main():
     }
     if sweep is not None:
         line["roofline_sweep"] = sweep
+    if adjoint is not None:
+        line["adjoint"] = adjoint
+    if batched is not None:
+        line["batched"] = batched
     if r64 is not None:
         line["fp64"] = {"value": r64["mlups"], "unit": "MLUPS", "ms_per_step": r64["ms_per_step"],
                         "roofline": r64["roofline"], "kernels": r64["kernels"],

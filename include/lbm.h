@@ -52,7 +52,7 @@ enum { LBM_BC_DEFAULT = -1, LBM_BC_HALFWAY = 0, LBM_BC_BOUZIDI = 1, LBM_BC_VIBB 
 enum { LBM_FP64 = 0, LBM_FP32_SHIFTED = 1 };
 enum { LBM_VIBB_RHO_PRINTED = 0, LBM_VIBB_RHO_LOCAL = 1 };
 
-#define LBM_MAX_BODIES 64
+#define LBM_MAX_BODIES 32768
 
 typedef struct lbm_lattice_s* lbm_handle;
 
@@ -63,7 +63,10 @@ typedef struct lbm_lattice_s* lbm_handle;
  *             force g enters by Guo forcing (velocity u = (sum f e + g/2)/rho,
  *             source (1 - 1/(2 tau)) w_i [3 (e_i - u) + 9 (e_i.u) e_i].g);
  *             the paper names a constant body force (Sec. 4.1) but no scheme.
- *             LBM_MRT (Sec. 2, Eq. mrt) is not built yet: LBM_ERR_UNSUPPORTED.
+ *             LBM_MRT (Sec. 2, Eq. mrt), D2Q9 only (D3Q19: LBM_ERR_UNSUPPORTED):
+ *             relaxation of f - feq in the moment basis M with rates s = 0.3
+ *             (moments 0, 3, 5), 1.5 (1, 2), 1.2 (4, 6), 1/tau (7, 8), and
+ *             the Guo source projected with (1 - s_k/2) per moment.
  *  bc         default link rule for links whose own rule is LBM_BC_DEFAULT.
  *  nx,ny,nz   lattice size; N = nx*ny*nz nodes.
  *  periodic   per axis, 1 = periodic.  On a non-periodic axis every node of
@@ -126,7 +129,43 @@ typedef struct {
   int32_t Q, D, precision, real_bytes;
   int64_t n_stored;      /* nodes with storage: fluid, open-column and ghost nodes */
   int64_t n_runs;        /* runs of consecutive fluid nodes along x */
+  int32_t n_bodies;      /* force accumulators: largest link body + 1 (at least 1) */
+  int32_t n_domains;     /* domains of a batch (1 without lbm_set_domains) */
 } lbm_info;
+
+/* One domain of a batch: an independent flow occupying the rows [lo, lo+n)
+ * of the last axis (y for D2Q9, z for D3Q19) and the columns x < nx.  The
+ * paper simulates one flow at a time; a batch packs many small ones (each
+ * its own geometry, tau, body force and inlet profile) into one lattice so
+ * that one launch per kernel advances them all.
+ *  lo, n      rows of the domain; the domains tile the axis in order.
+ *  nx         width: every node with x >= nx in these rows is solid, and the
+ *             outlet column (cfg.outlet) is x = nx - 1.
+ *  tau, g     relaxation time and body force of the domain (cfg.tau and cfg.g
+ *             are not used when domains are set).
+ *  inlet_*    inlet profile of the domain (cfg.inlet), with y counted from
+ *             row lo: u_in(y) = 4 umax (y - y0)(y1 - y)/(y1 - y0)^2. */
+typedef struct {
+  int32_t lo, n, nx, reserved;
+  double tau;
+  double g[3];
+  double inlet_umax, inlet_y0, inlet_y1;
+} lbm_domain;
+
+/* Launch shapes of the step (lbm_set_tuning, lbm_autotune).
+ *  bulk_shape     0..5: (threads per block, nodes per thread) of the bulk
+ *                 kernel = (256,1) (128,1) (512,1) (256,2) (128,2) (512,2);
+ *                 3..5 are D2Q9 only.  -1 on input: the stencil's default.
+ *  link_threads   64, 128 or 256 threads per block of the link kernel.
+ *  graph_steps    time steps per CUDA graph replayed by lbm_step (even,
+ *                 2..64).
+ * Shapes with the same nodes per thread give the same bits (force sums may
+ * differ in the last place, as FP64 atomics are unordered); one and two
+ * nodes per thread are separate compilations of the same arithmetic and
+ * agree to rounding. */
+typedef struct {
+  int32_t bulk_shape, link_threads, graph_steps, reserved;
+} lbm_tuning;
 
 /* Create a lattice: validates cfg, allocates the device state (two
  * population buffers, the moment cache, the node mask, two force slots).
@@ -135,6 +174,15 @@ lbm_status lbm_create_lattice(const lbm_config* cfg, lbm_handle* out);
 
 /* Free a lattice and everything it owns (synchronises its stream). */
 lbm_status lbm_destroy(lbm_handle h);
+
+/* Split the lattice into n independent domains (lbm_domain); call before
+ * lbm_set_geometry.  lbm_set_geometry then also checks that the first and
+ * last row of every domain hold no fluid or open node (so no population
+ * crosses between domains) and that nodes beyond a domain's width are
+ * solid.  A periodic x axis needs every nx equal to cfg.nx.  n = 0 returns to
+ * one domain run by cfg.  d: host array, copied.
+ * Errors: INVALID_ARG (names the first bad domain), STATE (geometry set). */
+lbm_status lbm_set_domains(lbm_handle h, const lbm_domain* d, int32_t n);
 
 /* Node classification and cut links (Sec. 3: fluid, solid and boundary
  * nodes; missing populations are those that would stream from solid
@@ -178,6 +226,10 @@ lbm_status lbm_moments(lbm_handle h, double* rho, double* u);
  * Errors: STATE, INVALID_ARG, CUDA. */
 lbm_status lbm_force(lbm_handle h, int32_t body, double F[3]);
 
+/* Forces on bodies 0..n-1 as lbm_force, in one copy: F[b*3 + a] (host);
+ * bodies without links give 0.  Errors: STATE, INVALID_ARG, CUDA. */
+lbm_status lbm_forces(lbm_handle h, int32_t n, double* F);
+
 /* Copy the state out as FP64 post-collision populations f+_i(x,t), [Q][N]
  * on the host (solid and open-column nodes get 0).  Synchronises.
  * Errors: STATE, OOM, CUDA. */
@@ -187,6 +239,34 @@ lbm_status lbm_get_distributions(lbm_handle h, double* f);
  * host; the moment cache is recomputed from them with the lbm_moments
  * formulas.  Does not change the step counter.  Errors: STATE, OOM, CUDA. */
 lbm_status lbm_set_distributions(lbm_handle h, const double* f);
+
+/* Discrete adjoint of lbm_step, for gradients of drag and lift (the paper
+ * has no gradients; this is the exact transpose of the step this library
+ * computes).  Runs n_steps of lbm_step from the current state, keeping a
+ * checkpoint every checkpoint_every steps, then sweeps backwards, recomputing
+ * each segment from its checkpoint, and returns for the objective
+ * J = dJ_dF . F_body (body >= 0; dJ_dF: 3 doubles) or
+ * J = sum_b dJ_dF[3b..3b+2] . F_b (body = -1; dJ_dF: 3 x n_bodies doubles,
+ * see lbm_query), F the momentum-exchange force of the last step (lbm_force):
+ *   *J        J itself;
+ *   dJ_dq     host, n_links doubles in the order given to lbm_set_geometry:
+ *             dJ/dq of every link (explicit dependence through the link
+ *             rules, summed over all steps in FP64);
+ *   dJ_dtau   host, one double per domain (one without lbm_set_domains):
+ *             dJ/dtau (collision and Guo forcing of every step, and of the
+ *             initial collision when the state is the one lbm_init_equilibrium
+ *             made);
+ *   seconds   NULL or 3 doubles: forward, recompute and adjoint wall time.
+ * Gradients with respect to a body's position or radius follow by the chain
+ * rule with dq/d(parameter) of each link.  BGK collision only (MRT:
+ * LBM_ERR_UNSUPPORTED); all link rules and open columns.  Work and the
+ * state's own precision as in lbm_step (FP32 shifted storage gives FP32
+ * adjoint states with FP64 time accumulation of dJ/dq and dJ/dtau).
+ * Device memory: (n_steps / checkpoint_every + checkpoint_every + 2) states,
+ * allocated for the call.  The lattice ends in the forward state after
+ * n_steps.  Synchronises.  Errors: STATE, INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
+lbm_status lbm_adjoint_step(lbm_handle h, int32_t body, const double dJ_dF[3], int64_t n_steps,
+                            int64_t checkpoint_every, double* J, double* dJ_dq, double* dJ_dtau, double seconds[3]);
 
 /* Post-collision populations f+_i(x, t) of n listed nodes, FP64 unshifted,
  * written to out[k*Q + i] (host).  nodes: n host indices in [0, N).  Solid
@@ -241,6 +321,22 @@ lbm_status lbm_kernel_times(lbm_handle h, int64_t launches[3], double ms[3]);
 #define LBM_NOALLOC_MAX_LINKS 16777216
 lbm_status lbm_force_noalloc(const lbm_config* cfg, const double* f_post, const uint8_t* solid,
                              const lbm_link* links, int64_t n_links, int32_t body, double* F);
+
+/* Launch shapes (lbm_tuning).  lbm_set_tuning validates and applies them
+ * (from the next lbm_step); lbm_get_tuning reads the current ones.
+ * Errors: INVALID_ARG. */
+lbm_status lbm_set_tuning(lbm_handle h, const lbm_tuning* t);
+lbm_status lbm_get_tuning(lbm_handle h, lbm_tuning* t);
+
+/* Autotuner: times the bulk shapes (with 256-thread link blocks), then the
+ * link block sizes, then the graph lengths, each over steps_per_trial steps
+ * (>= 2) from the current state after one untimed warm-up replay, and keeps
+ * the fastest.  The state, the step counter and the force of the last step
+ * are restored afterwards (a scratch copy of one state is allocated for the
+ * call).  best: NULL or receives the chosen shapes; ms_per_step: NULL or
+ * receives the chosen configuration's time per step.  Synchronises.
+ * Errors: STATE, INVALID_ARG, OOM, CUDA. */
+lbm_status lbm_autotune(lbm_handle h, int32_t steps_per_trial, lbm_tuning* best, double* ms_per_step);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* lbm_last_error(void);

@@ -1,0 +1,457 @@
+// Discrete adjoint of one lattice-Boltzmann step (BGK + Guo forcing, pull
+// streaming, half-way / Bouzidi / VIBB links, open columns): the transpose of
+// the step's Jacobian applied to lambda(s+1) = dJ/df+(s+1), giving
+// lambda(s) = dJ/df+(s), plus the explicit derivatives of the step with
+// respect to tau (summed in FP64) and to every link's q (accumulated per link
+// in FP64 over time).
+//
+// The state of a step is f+(s); the moments a link rule uses are the
+// functions rho = sum f+, u = (sum f+ e - g/2)/rho of it (refreshed from
+// f+(s) before the adjoint step), so that every dependence is through f+(s).
+//
+// Per step (one stream, in this order):
+//   k_adj_bulk   per fluid node x: pre-collision f(s+1) from the pull sources
+//                (ghost slots hold the link values of step s), the collision
+//                transpose mu = (dC/df)^T lambda(s+1)(x), and mu_i scattered to
+//                the pull source of direction i -- streaming is a permutation,
+//                so these writes never collide; the ghost slot of a cut link
+//                receives the adjoint weight of its link value.  Cached nodes
+//                also refresh their moments from f+(s) for the link kernel.
+//   k_adj_links  per link: the link value's transpose into x_f and x_ff
+//                (populations and, through the moments, all directions), by
+//                atomics; dJ/dq accumulated per link.
+//   k_adj_open   inlet (non-equilibrium extrapolation) and outlet (copy)
+//                transposes into the first and last fluid columns.
+// Every kernel clears the lambda entries it consumes (lambda(s+1) at fluid
+// nodes, the ghost and open entries of lambda(s)), so that the buffer of
+// lambda(s+1) is zero when it becomes the output of the next step back.
+#pragma once
+#include "kernels.cuh"
+
+namespace lbm {
+
+template <class T>
+__device__ __forceinline__ void atomic_add_real(T* p, T v) {
+  atomicAdd(p, v);
+}
+
+// Collision transpose at one node.  f: pre-collision populations (storage
+// form); lam: lambda(s+1) of this node; mu: output.  Returns the node's
+// sum_i lam_i dC_i/dtau.
+template <class L, class P>
+__device__ __forceinline__ double collide_adjoint(const typename P::T (&f)[L::Q], const typename P::T (&lam)[L::Q],
+                                                  typename P::T (&mu)[L::Q], const Params& p, const Relax& rx) {
+  using T = typename P::T;
+  T r = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    r += f[i];
+    jx += (T)L::cx(i) * f[i];
+    jy += (T)L::cy(i) * f[i];
+    jz += (T)L::cz(i) * f[i];
+  }
+  const T rho = P::shifted ? (T)p.rho0 + r : r;
+  const T gx = (T)rx.g[0], gy = (T)rx.g[1], gz = (T)rx.g[2];
+  const T ux = (jx + (T)0.5 * gx) / rho, uy = (jy + (T)0.5 * gy) / rho, uz = (jz + (T)0.5 * gz) / rho;
+  const T omega = (T)rx.omega;
+  const T uu15 = (T)1.5 * (ux * ux + uy * uy + uz * uz);
+  const T ug = ux * gx + uy * gy + uz * gz;
+  T A = 0, B0 = 0, B1 = 0, B2 = 0;
+  double dtau = 0.0;
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    const T ex = (T)L::cx(i), ey = (T)L::cy(i), ez = (T)L::cz(i);
+    const T w = (T)L::w(i);
+    const T eu = ex * ux + ey * uy + ez * uz;
+    const T poly = (T)3 * eu + (T)4.5 * eu * eu - uu15;
+    const T feq = P::shifted ? w * (r + rho * poly) : w * rho * ((T)1 + poly);
+    const T eg = ex * gx + ey * gy + ez * gz;
+    const T src = rx.has_force ? w * ((T)3 * (eg - ug) + (T)9 * eu * eg) : (T)0;
+    // d feq_i / d rho at fixed u, and the u-derivatives of feq_i and of the source
+    A += lam[i] * w * ((T)1 + poly);
+    const T c1 = omega * w * rho, c2 = ((T)1 - (T)0.5 * omega) * w;
+    B0 += lam[i] * (c1 * ((T)3 * ex + (T)9 * eu * ex - (T)3 * ux) + c2 * ((T)-3 * gx + (T)9 * ex * eg));
+    B1 += lam[i] * (c1 * ((T)3 * ey + (T)9 * eu * ey - (T)3 * uy) + c2 * ((T)-3 * gy + (T)9 * ey * eg));
+    B2 += lam[i] * (c1 * ((T)3 * ez + (T)9 * eu * ez - (T)3 * uz) + c2 * ((T)-3 * gz + (T)9 * ez * eg));
+    // dC_i/dtau = (f_i - feq_i + src_i / 2) / tau^2
+    dtau += (double)lam[i] * (double)(f[i] - feq + (T)0.5 * src);
+  }
+  const T ir = (T)1 / rho;
+#pragma unroll
+  for (int j = 0; j < L::Q; ++j) {
+    const T ex = (T)L::cx(j), ey = (T)L::cy(j), ez = (T)L::cz(j);
+    mu[j] = ((T)1 - omega) * lam[j] + omega * A + (B0 * (ex - ux) + B1 * (ey - uy) + B2 * (ez - uz)) * ir;
+  }
+  return dtau * (rx.omega * rx.omega);
+}
+
+// Adds v to target[key] over the block (key < 0: nothing to add): one atomic
+// when every contributing thread has the same key, else one per thread.
+__device__ __forceinline__ void block_add_keyed(double v, int key, double* target) {
+  __shared__ double red[32];
+  __shared__ int kref;
+  if (threadIdx.x == 0) kref = -1;
+  __syncthreads();
+  if (key >= 0) atomicMax(&kref, key);
+  __syncthreads();
+  const int k0 = kref;
+  if (!__syncthreads_and(key < 0 || key == k0)) {
+    if (key >= 0 && v != 0.0) atomicAdd(target + key, v);
+    return;
+  }
+  if (k0 < 0) return;
+  if (key < 0) v = 0.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double acc = 0.0;
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) acc += red[w];
+    atomicAdd(target + k0, acc);
+  }
+}
+
+template <class L, class P>
+__global__ void __launch_bounds__(256) k_adj_bulk(const typename P::T* __restrict__ fin,
+                                                  typename P::T* __restrict__ lam_next,
+                                                  typename P::T* __restrict__ lam_out, Layout lay, Params p,
+                                                  double* __restrict__ dtau, Mom4<typename P::T>* __restrict__ mom) {
+  using T = typename P::T;
+  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t S = (size_t)lay.S;
+  double dt = 0.0;
+  int key = -1;
+  if (k < (uint64_t)lay.S) {
+    const uint32_t w = lay.word[k];
+    if (!(w & (W_GHOST | W_OPEN))) {
+      const RunRec run = lay.runs[w & W_RUN];
+      key = lay.ndom > 1 ? run.dom : 0;
+      const Relax rx = lay.ndom > 1 ? relax_domain(lay.dom, key) : relax_params(p);
+      uint32_t src[L::Q];
+      pull_sources<L>(k, run, lay, p, src);
+      T f[L::Q], lam[L::Q], mu[L::Q];
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        f[i] = fin[(size_t)i * S + src[i]];
+        lam[i] = lam_next[(size_t)i * S + k];
+        lam_next[(size_t)i * S + k] = (T)0;
+      }
+      if (w & W_CACHE) {
+        // moments of f+(s) at this node (the k_refresh formula)
+        T r = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+          const T v = fin[(size_t)i * S + k];
+          r += v;
+          jx += (T)L::cx(i) * v;
+          jy += (T)L::cy(i) * v;
+          jz += (T)L::cz(i) * v;
+        }
+        const T rho = P::shifted ? (T)p.rho0 + r : r;
+        mom[k] = Mom4<T>{r, (jx - (T)(0.5 * rx.g[0])) / rho, (jy - (T)(0.5 * rx.g[1])) / rho,
+                         L::D == 3 ? (jz - (T)(0.5 * rx.g[2])) / rho : (T)0};
+      }
+      dt = collide_adjoint<L, P>(f, lam, mu, p, rx);
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) lam_out[(size_t)i * S + src[i]] = mu[i];
+    }
+  }
+  block_add_keyed(dt, key, dtau);
+}
+
+// Adds (a_r, a_u) -- adjoints of a node's moments rho and u -- to all
+// directions of that node: d rho/df+_j = 1, d u_a/df+_j = (e_ja - u_a)/rho.
+template <class L, class T>
+__device__ __forceinline__ void scatter_moment_adjoint(T* __restrict__ lam, size_t S, uint32_t k, T ar, T a0, T a1,
+                                                       T a2, const Mom4<T>& m, T rho) {
+  const T ir = (T)1 / rho;
+#pragma unroll
+  for (int j = 0; j < L::Q; ++j) {
+    const T v = ar + (a0 * ((T)L::cx(j) - m.ux) + a1 * ((T)L::cy(j) - m.uy) + a2 * ((T)L::cz(j) - m.uz)) * ir;
+    atomic_add_real(lam + (size_t)j * S + k, v);
+  }
+}
+
+// One thread per link.  lam: lambda(s) under construction (ghost slots hold
+// the weights of the link values).  final_step: add the objective's direct
+// terms J = sum_b wbody[b] . F_b(step) (wbody: [nbody][3] FP64).
+template <class L, class P>
+__global__ void __launch_bounds__(256) k_adj_links(const typename P::T* __restrict__ f,
+                                                   const Mom4<typename P::T>* __restrict__ mom,
+                                                   typename P::T* __restrict__ lam, const LinkRec* __restrict__ recs,
+                                                   const typename P::T* __restrict__ qv,
+                                                   const typename P::T* __restrict__ uwv, int64_t nl, Params p,
+                                                   int64_t S_, double* __restrict__ dq_acc, int final_step,
+                                                   const double* __restrict__ wbody) {
+  using T = typename P::T;
+  __shared__ DirTable<T, L::Q> tab;
+  if (threadIdx.x < L::Q) {
+    const int d = threadIdx.x;
+    tab.off[d] = 0;
+    tab.opp[d] = L::opp(d);
+    tab.w[d] = (T)L::w(d);
+    tab.e[d][0] = (T)L::cx(d);
+    tab.e[d][1] = (T)L::cy(d);
+    tab.e[d][2] = (T)L::cz(d);
+  }
+  __syncthreads();
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= nl) return;
+  const size_t S = (size_t)S_;
+  const LinkRec rec = recs[k];
+  const int ip = (int)(rec.meta & 31);
+  const int rule = (int)((rec.meta >> 5) & 3);
+  const int body = (int)(rec.meta >> 7) - 1;
+  const uint32_t kf = rec.kf, kff = rec.kff, ks = rec.ks;
+  const int i = tab.opp[ip];
+  const T ex = tab.e[ip][0], ey = tab.e[ip][1], ez = tab.e[ip][2];
+  const T w = tab.w[ip];
+  const T q = qv[k];
+  T uw0 = 0, uw1 = 0, uw2 = 0;
+  if (uwv) {
+    uw0 = uwv[k];
+    uw1 = uwv[nl + k];
+    if (L::D == 3) uw2 = uwv[2 * nl + k];
+  }
+  T om = lam[(size_t)i * S + ks];  // weight of this link's value (consumed here)
+  lam[(size_t)i * S + ks] = (T)0;
+  if (final_step && body >= 0) {
+    // J = w_b . sum (f+_i'(x_f) + L) e_i'
+    const double* wb = wbody + 3 * body;
+    const T c = (T)(wb[0] * (double)ex + wb[1] * (double)ey + wb[2] * (double)ez);
+    om += c;
+    atomic_add_real(lam + (size_t)ip * S + kf, c);
+  }
+  const T wall = -(T)6 * w * (T)p.rho0 * (ex * uw0 + ey * uw1 + ez * uw2);
+  const T fpf = f[(size_t)ip * S + kf];
+  const T two_q = (T)2 * q;
+  double dLdq = 0.0;
+  if (rule == 0) {
+    atomic_add_real(lam + (size_t)ip * S + kf, om);
+  } else if (rule == 1) {
+    if (q <= (T)0.5) {
+      const T fpff = f[(size_t)ip * S + kff];
+      atomic_add_real(lam + (size_t)ip * S + kf, two_q * om);
+      atomic_add_real(lam + (size_t)ip * S + kff, ((T)1 - two_q) * om);
+      dLdq = 2.0 * ((double)fpf - (double)fpff);
+    } else {
+      const T fpi = f[(size_t)i * S + kf];
+      const T inv2q = (T)1 / two_q;
+      atomic_add_real(lam + (size_t)ip * S + kf, om * inv2q);
+      atomic_add_real(lam + (size_t)i * S + kf, om * ((T)1 - inv2q));
+      dLdq = -((double)fpf + (double)wall - (double)fpi) / (2.0 * (double)q * (double)q);
+    }
+  } else {
+    const T fpff = f[(size_t)ip * S + kff];
+    const Mom4<T> mf = mom[kf], mff = mom[kff];
+    const T rhof = P::shifted ? (T)p.rho0 + mf.r : mf.r;
+    const T rhoff = P::shifted ? (T)p.rho0 + mff.r : mff.r;
+    const bool local = p.vibb_local_rho && q > (T)0.5;
+    const T rd = local ? mf.r : two_q * mf.r + ((T)1 - two_q) * mff.r;
+    const T rhod = P::shifted ? (T)p.rho0 + rd : rd;
+    const T euf = ex * mf.ux + ey * mf.uy + ez * mf.uz;
+    const T euff = ex * mff.ux + ey * mff.uy + ez * mff.uz;
+    const T polyf = (T)3 * euf + (T)4.5 * euf * euf - (T)1.5 * (mf.ux * mf.ux + mf.uy * mf.uy + mf.uz * mf.uz);
+    const T polyff =
+        (T)3 * euff + (T)4.5 * euff * euff - (T)1.5 * (mff.ux * mff.ux + mff.uy * mff.uy + mff.uz * mff.uz);
+    const T neq_f = fpf - (P::shifted ? w * (mf.r + rhof * polyf) : w * rhof * ((T)1 + polyf));
+    const T neq_ff = fpff - (P::shifted ? w * (mff.r + rhoff * polyff) : w * rhoff * ((T)1 + polyff));
+    const T nd = rhod * (two_q * neq_f / rhof + ((T)1 - two_q) * neq_ff / rhoff);
+    T af, aff, aw, daf, daff, daw;
+    if (q <= (T)0.5) {
+      af = two_q;
+      aff = (T)1 - two_q;
+      aw = 0;
+      daf = 2;
+      daff = -2;
+      daw = 0;
+    } else {
+      const T iq = (T)1 / q;
+      af = ((T)1 - q) * iq;
+      aff = 0;
+      aw = (two_q - (T)1) * iq;
+      daf = -iq * iq;
+      daff = 0;
+      daw = iq * iq;
+    }
+    const T i1q = (T)1 / ((T)1 + q);
+    const T bff = ((T)1 - q) * i1q, bw = two_q * i1q;
+    const T dbff = (T)-2 * i1q * i1q, dbw = (T)2 * i1q * i1q;
+    const T third = (T)(1.0 / 3.0), two_thirds = (T)(2.0 / 3.0);
+    const T cf = third * af, cff = third * aff + two_thirds * bff, cw = third * aw + two_thirds * bw;
+    const T dcf = third * daf, dcff = third * daff + two_thirds * dbff, dcw = third * daw + two_thirds * dbw;
+    const T udx = cf * mf.ux + cff * mff.ux + cw * uw0;
+    const T udy = cf * mf.uy + cff * mff.uy + cw * uw1;
+    const T udz = cf * mf.uz + cff * mff.uz + cw * uw2;
+    const T eud = ex * udx + ey * udy + ez * udz;
+    const T polyd = (T)3 * eud + (T)4.5 * eud * eud - (T)1.5 * (udx * udx + udy * udy + udz * udz);
+    // partial derivatives of L = feq_i'(rd, ud) + nd + wall
+    const T gd = w * ((T)1 + polyd) + nd / rhod;                     // d/d rd
+    const T aud0 = w * rhod * ((T)3 * ex + (T)9 * eud * ex - (T)3 * udx);  // d/d ud
+    const T aud1 = w * rhod * ((T)3 * ey + (T)9 * eud * ey - (T)3 * udy);
+    const T aud2 = w * rhod * ((T)3 * ez + (T)9 * eud * ez - (T)3 * udz);
+    const T dn_f = rhod * two_q / rhof;                               // d nd / d neq_f
+    const T dn_ff = rhod * ((T)1 - two_q) / rhoff;
+    const T drd_f = local ? (T)1 : two_q, drd_ff = local ? (T)0 : (T)1 - two_q;
+    const T a_rf = gd * drd_f - dn_f * w * ((T)1 + polyf) - rhod * two_q * neq_f / (rhof * rhof);
+    const T a_rff = gd * drd_ff - dn_ff * w * ((T)1 + polyff) - rhod * ((T)1 - two_q) * neq_ff / (rhoff * rhoff);
+    const T wf = dn_f * w * rhof, wff = dn_ff * w * rhoff;
+    const T a_uf0 = aud0 * cf - wf * ((T)3 * ex + (T)9 * euf * ex - (T)3 * mf.ux);
+    const T a_uf1 = aud1 * cf - wf * ((T)3 * ey + (T)9 * euf * ey - (T)3 * mf.uy);
+    const T a_uf2 = aud2 * cf - wf * ((T)3 * ez + (T)9 * euf * ez - (T)3 * mf.uz);
+    const T a_uff0 = aud0 * cff - wff * ((T)3 * ex + (T)9 * euff * ex - (T)3 * mff.ux);
+    const T a_uff1 = aud1 * cff - wff * ((T)3 * ey + (T)9 * euff * ey - (T)3 * mff.uy);
+    const T a_uff2 = aud2 * cff - wff * ((T)3 * ez + (T)9 * euff * ez - (T)3 * mff.uz);
+    atomic_add_real(lam + (size_t)ip * S + kf, om * dn_f);
+    atomic_add_real(lam + (size_t)ip * S + kff, om * dn_ff);
+    scatter_moment_adjoint<L, T>(lam, S, kf, om * a_rf, om * a_uf0, om * a_uf1, om * a_uf2, mf, rhof);
+    scatter_moment_adjoint<L, T>(lam, S, kff, om * a_rff, om * a_uff0, om * a_uff1, om * a_uff2, mff, rhoff);
+    const double drd_q = local ? 0.0 : 2.0 * ((double)mf.r - (double)mff.r);
+    dLdq = (double)gd * drd_q + (double)rhod * (2.0 * (double)neq_f / (double)rhof - 2.0 * (double)neq_ff / (double)rhoff) +
+           (double)aud0 * (double)(dcf * mf.ux + dcff * mff.ux + dcw * uw0) +
+           (double)aud1 * (double)(dcf * mf.uy + dcff * mff.uy + dcw * uw1) +
+           (double)aud2 * (double)(dcf * mf.uz + dcff * mff.uz + dcw * uw2);
+  }
+  dq_acc[k] += (double)om * dLdq;
+}
+
+// Open columns (D2Q9): inlet f+(0) = feq(rho1, u_in) + f+(1) - feq(rho1, u1)
+// and outlet f+(nx-1) = f+(nx-2), transposed into columns 1 and nx-2; the
+// open nodes' entries are then cleared (they are not state).
+template <class L, class P>
+__global__ void k_adj_open(typename P::T* __restrict__ lam, const Mom4<typename P::T>* __restrict__ mom, Layout lay,
+                           Params p) {
+  using T = typename P::T;
+  const int y = blockIdx.x * blockDim.x + threadIdx.x;
+  if (y >= p.ny) return;
+  const size_t S = (size_t)lay.S;
+  if (p.inlet) {
+    const int32_t k0 = lay.row_first[y];
+    if (k0 >= 0 && (lay.word[k0] & W_OPEN)) {
+      const uint32_t k1 = (uint32_t)k0 + 1;
+      const T uin = (T)inlet_velocity(p, lay, y);
+      const Mom4<T> m1 = mom[k1];
+      T l0[L::Q];
+      T sp = 0, B0 = 0, B1 = 0;
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        l0[i] = lam[(size_t)i * S + k0];
+        const T ex = (T)L::cx(i), ey = (T)L::cy(i), w = (T)L::w(i);
+        const T ein = ex * uin;
+        const T e1 = ex * m1.ux + ey * m1.uy;
+        const T pin = (T)3 * ein + (T)4.5 * ein * ein - (T)1.5 * uin * uin;
+        const T p1 = (T)3 * e1 + (T)4.5 * e1 * e1 - (T)1.5 * (m1.ux * m1.ux + m1.uy * m1.uy);
+        sp += l0[i] * w * (pin - p1);
+        B0 += l0[i] * w * ((T)3 * ex + (T)9 * e1 * ex - (T)3 * m1.ux);
+        B1 += l0[i] * w * ((T)3 * ey + (T)9 * e1 * ey - (T)3 * m1.uy);
+      }
+#pragma unroll
+      for (int j = 0; j < L::Q; ++j) {
+        lam[(size_t)j * S + k1] += l0[j] + sp - (B0 * ((T)L::cx(j) - m1.ux) + B1 * ((T)L::cy(j) - m1.uy));
+        lam[(size_t)j * S + k0] = (T)0;
+      }
+    }
+  }
+  if (p.outlet) {
+    const int32_t kl = lay.row_last[y];
+    if (kl >= 0 && (lay.word[kl] & W_OPEN)) {
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        lam[(size_t)i * S + kl - 1] += lam[(size_t)i * S + kl];
+        lam[(size_t)i * S + kl] = (T)0;
+      }
+    }
+  }
+}
+
+// tau-dependence of the initial collision f+(0) = C(feq(rho, u_in)), with
+// rho and u_in recovered from f+(0): rho = sum f+, u_in = (sum f+ e - g)/rho.
+template <class L, class P>
+__global__ void __launch_bounds__(256) k_adj_init(const typename P::T* __restrict__ f0,
+                                                  const typename P::T* __restrict__ lam, Layout lay, Params p,
+                                                  double* __restrict__ dtau) {
+  using T = typename P::T;
+  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t S = (size_t)lay.S;
+  double dt = 0.0;
+  int key = -1;
+  if (k < (uint64_t)lay.S && !(lay.word[k] & (W_GHOST | W_OPEN))) {
+    const uint32_t run = lay.word[k] & W_RUN;
+    key = lay.ndom > 1 ? lay.runs[run].dom : 0;
+    const Relax rx = relax_of_run(p, lay, run);
+    const double g[3] = {rx.g[0], rx.g[1], rx.g[2]};
+    double r = 0.0, j[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      const double v = (double)f0[(size_t)i * S + k] + (P::shifted ? L::w(i) * p.rho0 : 0.0);
+      r += v;
+      j[0] += L::cx(i) * v;
+      j[1] += L::cy(i) * v;
+      j[2] += L::cz(i) * v;
+    }
+    const double uin[3] = {(j[0] - g[0]) / r, (j[1] - g[1]) / r, (j[2] - g[2]) / r};
+    const double u[3] = {uin[0] + 0.5 * g[0] / r, uin[1] + 0.5 * g[1] / r, uin[2] + 0.5 * g[2] / r};
+    const double uu_in = uin[0] * uin[0] + uin[1] * uin[1] + uin[2] * uin[2];
+    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const double ug = u[0] * g[0] + u[1] * g[1] + u[2] * g[2];
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      const double ein = L::cx(i) * uin[0] + L::cy(i) * uin[1] + L::cz(i) * uin[2];
+      const double eu = L::cx(i) * u[0] + L::cy(i) * u[1] + L::cz(i) * u[2];
+      const double eg = L::cx(i) * g[0] + L::cy(i) * g[1] + L::cz(i) * g[2];
+      const double f0i = L::w(i) * r * (1.0 + 3.0 * ein + 4.5 * ein * ein - 1.5 * uu_in);
+      const double feq = L::w(i) * r * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
+      const double src = L::w(i) * (3.0 * (eg - ug) + 9.0 * eu * eg);
+      dt += (double)lam[(size_t)i * S + k] * (f0i - feq + 0.5 * src);
+    }
+    dt *= rx.omega * rx.omega;
+  }
+  block_add_keyed(dt, key, dtau);
+}
+
+struct AdjointOps {
+  void (*bulk)(const void* fin, void* lam_next, void* lam_out, const Layout& lay, const Params& p, double* dtau,
+               void* mom, cudaStream_t s);
+  void (*links)(const void* f, const void* mom, void* lam, const LinkRec* recs, const void* q, const void* uw,
+                int64_t nl, const Params& p, int64_t S, double* dq_acc, int final_step, const double* wbody,
+                cudaStream_t s);
+  void (*open)(void* lam, const void* mom, const Layout& lay, const Params& p, cudaStream_t s);
+  void (*init)(const void* f0, const void* lam, const Layout& lay, const Params& p, double* dtau, cudaStream_t s);
+};
+
+template <class L, class P>
+struct AdjointLaunch {
+  using T = typename P::T;
+  static void bulk(const void* fin, void* lam_next, void* lam_out, const Layout& lay, const Params& p, double* dtau,
+                   void* mom, cudaStream_t s) {
+    if (lay.S == 0) return;
+    k_adj_bulk<L, P><<<blocks_for(lay.S, 256), 256, 0, s>>>((const T*)fin, (T*)lam_next, (T*)lam_out, lay, p, dtau,
+                                                           (Mom4<T>*)mom);
+  }
+  static void links(const void* f, const void* mom, void* lam, const LinkRec* recs, const void* q, const void* uw,
+                    int64_t nl, const Params& p, int64_t S, double* dq_acc, int final_step, const double* wbody,
+                    cudaStream_t s) {
+    if (nl == 0) return;
+    k_adj_links<L, P><<<blocks_for(nl, 256), 256, 0, s>>>((const T*)f, (const Mom4<T>*)mom, (T*)lam, recs,
+                                                         (const T*)q, (const T*)uw, nl, p, S, dq_acc, final_step,
+                                                         wbody);
+  }
+  static void open(void* lam, const void* mom, const Layout& lay, const Params& p, cudaStream_t s) {
+    k_adj_open<L, P><<<blocks_for(p.ny, 128), 128, 0, s>>>((T*)lam, (const Mom4<T>*)mom, lay, p);
+  }
+  static void init(const void* f0, const void* lam, const Layout& lay, const Params& p, double* dtau,
+                   cudaStream_t s) {
+    if (lay.S == 0) return;
+    k_adj_init<L, P><<<blocks_for(lay.S, 256), 256, 0, s>>>((const T*)f0, (const T*)lam, lay, p, dtau);
+  }
+  static AdjointOps ops() { return AdjointOps{bulk, links, open, init}; }
+};
+
+AdjointOps adj_d2q9_f64();
+AdjointOps adj_d2q9_f32s();
+AdjointOps adj_d3q19_f64();
+AdjointOps adj_d3q19_f32s();
+
+}  // namespace lbm

@@ -63,11 +63,29 @@ constexpr uint32_t W_CACHE = 1u << 29;
 constexpr uint32_t W_OPEN = 1u << 30;
 constexpr uint32_t W_GHOST = 1u << 31;
 
-// One fluid run: x0, its storage index k0, its row (y, z), and for each
-// neighbour row (slot order below) the storage index of (x0, row').
+// One fluid run: x0, its storage index k0, its row (y, z), for each
+// neighbour row (slot order below) the storage index of (x0, row'), and the
+// domain the row belongs to.
 struct __align__(16) RunRec {
   int32_t x0, k0, y, z;
   int32_t base[8];
+  int32_t dom, pad_[3];
+};
+
+// Run parameters of one domain of a batch (several independent flows
+// stacked along the last axis of one lattice, each with its own relaxation
+// time, body force and inlet profile).  A lattice of one domain reads Params.
+struct DomPar {
+  double omega, fpre3;    // 1/tau, 3 (1 - 1/(2 tau))
+  double g[3];
+  double inlet_umax, inlet_y0, inlet_y1;  // inlet rows relative to lo
+  int32_t lo, has_force;  // first row (y in 2-D, z in 3-D) of the domain
+};
+
+// Collision parameters of one node, from Params or from its domain.
+struct Relax {
+  double omega, fpre3, g[3];
+  int has_force;
 };
 
 // Neighbour-row slots by source-row offset (dy, dz).  D2Q9: (1,0), (-1,0).
@@ -84,10 +102,28 @@ struct Layout {
   const RunRec* runs;
   const int32_t* row_first;    // [ny*nz] storage index of the row's first stored node (-1: none)
   const int32_t* row_last;     // [ny*nz] ... last stored node
+  const DomPar* dom;           // [ndom] when ndom > 1, else null
+  const int32_t* row_dom;      // [ny*nz] domain of each row when ndom > 1
+  int32_t ndom;
 };
 
+__device__ __forceinline__ Relax relax_params(const Params& p) {
+  return Relax{p.omega, p.fpre3, {p.g[0], p.g[1], p.g[2]}, p.has_force};
+}
+
+__device__ __forceinline__ Relax relax_domain(const DomPar* __restrict__ dp, int d) {
+  const DomPar& q = dp[d];
+  return Relax{q.omega, q.fpre3, {q.g[0], q.g[1], q.g[2]}, q.has_force};
+}
+
+// Relaxation of a node of fluid run `run` (any kernel but the bulk one,
+// which resolves the single-domain case at compile time).
+__device__ __forceinline__ Relax relax_of_run(const Params& p, const Layout& lay, uint32_t run) {
+  return lay.ndom > 1 ? relax_domain(lay.dom, lay.runs[run].dom) : relax_params(p);
+}
+
 // One link: storage indices of x_f, x_ff (x_f if no second fluid node) and
-// the ghost x_s; meta = dir | rule << 5 | (body + 1) << 7.
+// the ghost x_s; meta = dir | rule << 5 | (body + 1) << 7 (25 bits of body).
 struct __align__(16) LinkRec {
   uint32_t kf, kff, ks, meta;
 };
@@ -114,8 +150,9 @@ __device__ __forceinline__ int src_coord(int c, int x, int xm, int xp) { return 
 // Moments, collision and store of one fluid node.  f holds the pre-collision
 // populations f(x, t+1) in storage form; n < 2^31.
 template <class L, class P>
-__device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Params& p, typename P::T* __restrict__ fout,
-                                              size_t S, uint32_t n_, Mom4<typename P::T>* __restrict__ mom, bool cache) {
+__device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Params& p, const Relax& rx,
+                                              typename P::T* __restrict__ fout, size_t S, uint32_t n_,
+                                              Mom4<typename P::T>* __restrict__ mom, bool cache) {
   using T = typename P::T;
   T r = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
@@ -129,12 +166,12 @@ __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Pa
     if (L::cz(i) < 0) jz -= f[i];
   }
   const T rho = P::shifted ? (T)p.rho0 + r : r;
-  const T gx = (T)p.g[0], gy = (T)p.g[1], gz = (T)p.g[2];
+  const T gx = (T)rx.g[0], gy = (T)rx.g[1], gz = (T)rx.g[2];
   const T inv = (T)1 / rho;
   // Guo forcing: velocity shifted by half the body force
   const T ux = (jx + (T)0.5 * gx) * inv, uy = (jy + (T)0.5 * gy) * inv, uz = (jz + (T)0.5 * gz) * inv;
   if (cache) mom[n_] = Mom4<T>{r, ux, uy, L::D == 3 ? uz : (T)0};
-  const T omega = (T)p.omega;
+  const T omega = (T)rx.omega;
   const T uu15 = (T)1.5 * (ux * ux + uy * uy + uz * uz);
   if constexpr (L::Q == 9) {
     if (p.collision == 1) {
@@ -152,7 +189,7 @@ __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Pa
         const T feq = P::shifted ? w * (r + rho * poly) : (w * rho) * ((T)1 + poly);
         n[i] = f[i] - feq;
         const T eg = (T)L::cx(i) * gx_ + (T)L::cy(i) * gy_;
-        src[i] = p.has_force ? w * ((T)3 * (eg - ug2) + (T)9 * eu * eg) : (T)0;
+        src[i] = rx.has_force ? w * ((T)3 * (eg - ug2) + (T)9 * eu * eg) : (T)0;
       }
       T dm[9];
 #pragma unroll
@@ -181,7 +218,7 @@ __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Pa
   }
   // Guo source (1 - 1/(2 tau)) w_i [3 (e_i - u).g + 9 (e_i.u)(e_i.g)]
   //   = 3 (1 - 1/(2 tau)) w_i [(e_i.g)(1 + 3 e_i.u) - u.g]
-  const T fpre3 = (T)p.fpre3;
+  const T fpre3 = (T)rx.fpre3;
   const T ug = ux * gx + uy * gy + uz * gz;
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
@@ -190,7 +227,7 @@ __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Pa
     const T poly = (T)3 * eu + (T)4.5 * eu * eu - uu15;
     const T feq = P::shifted ? w * (r + rho * poly) : (w * rho) * ((T)1 + poly);
     T out = f[i] + omega * (feq - f[i]);
-    if (p.has_force) {
+    if (rx.has_force) {
       const T eg = (T)L::cx(i) * gx + (T)L::cy(i) * gy + (T)L::cz(i) * gz;
       out += fpre3 * w * (eg * ((T)1 + (T)3 * eu) - ug);
     }
@@ -198,44 +235,25 @@ __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Pa
   }
 }
 
-// ------------------------------------------------------------------ bulk --
-
-// One thread per stored node; block (0) also clears the force slot of the
-// next step.
-template <class L, class P>
-__global__ void __launch_bounds__(256, P::bulk_min_blocks) k_bulk(const typename P::T* __restrict__ fin, typename P::T* __restrict__ fout,
-                                              Layout lay, Mom4<typename P::T>* __restrict__ mom,
-                                              double* __restrict__ force_next, Params p) {
-  using T = typename P::T;
-  if (force_next && blockIdx.x == 0)
-    for (int t = threadIdx.x; t < 3 * MAX_BODIES; t += blockDim.x) force_next[t] = 0.0;
-  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= (uint64_t)lay.S) return;
-  const size_t S = (size_t)lay.S;
-  const uint32_t w = __ldg(lay.word + k);
-  if (w & (W_GHOST | W_OPEN)) {
-#pragma unroll
-    for (int i = 0; i < L::Q; ++i) fout[(size_t)i * S + k] = (T)0;
-    return;
-  }
-  const RunRec run = lay.runs[w & W_RUN];
+// Storage indices of the pull sources x - e_i of fluid node k of run `run`.
+template <class L>
+__device__ __forceinline__ void pull_sources(uint32_t k, const RunRec& run, const Layout& lay, const Params& p,
+                                             uint32_t (&src)[L::Q]) {
   const int nx = p.nx;
   const int x = run.x0 + (int)(k - (uint32_t)run.k0);
   const bool left = x == 0, right = x == nx - 1;
-  T f[L::Q];
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
     // source x - e_i: offsets (dx, dy, dz) = -(cx, cy, cz)
     const int dx = -L::cx(i), dy = -L::cy(i), dz = -L::cz(i);
-    uint32_t src;
     if (dy == 0 && dz == 0) {
       if (dx == 0) {
-        src = k;
+        src[i] = k;
       } else if ((dx < 0 && left) || (dx > 0 && right)) {
         const int row = run.y + p.ny * run.z;
-        src = (uint32_t)(dx < 0 ? lay.row_last[row] : lay.row_first[row]);
+        src[i] = (uint32_t)(dx < 0 ? lay.row_last[row] : lay.row_first[row]);
       } else {
-        src = k + dx;
+        src[i] = k + dx;
       }
     } else {
       if ((dx < 0 && left) || (dx > 0 && right)) {
@@ -243,14 +261,90 @@ __global__ void __launch_bounds__(256, P::bulk_min_blocks) k_bulk(const typename
         yy = yy < 0 ? yy + p.ny : (yy >= p.ny ? yy - p.ny : yy);
         zz = zz < 0 ? zz + p.nz : (zz >= p.nz ? zz - p.nz : zz);
         const int row = yy + p.ny * zz;
-        src = (uint32_t)(dx < 0 ? lay.row_last[row] : lay.row_first[row]);
+        src[i] = (uint32_t)(dx < 0 ? lay.row_last[row] : lay.row_first[row]);
       } else {
-        src = (uint32_t)(run.base[row_slot(dy, dz)] + (x + dx - run.x0));
+        src[i] = (uint32_t)(run.base[row_slot(dy, dz)] + (x + dx - run.x0));
       }
     }
-    f[i] = __ldg(fin + (size_t)i * S + src);
   }
-  collide_store<L, P>(f, p, fout, S, k, mom, (w & W_CACHE) != 0);
+}
+
+// ------------------------------------------------------------------ bulk --
+
+// Shapes of the bulk kernel the autotuner chooses from: threads per block
+// and nodes per thread (a thread with two nodes takes k and k + ceil(S/2),
+// both ranges coalesced, and has 2Q loads in flight).  Two nodes per thread
+// are built for D2Q9 only (D3Q19 threads already have 19 loads in flight).
+struct BulkShape {
+  int threads, npt;
+};
+constexpr BulkShape kBulkShapes[] = {{256, 1}, {128, 1}, {512, 1}, {256, 2}, {128, 2}, {512, 2}};
+constexpr int kNumBulkShapes = 6;
+
+template <class L>
+constexpr int bulk_max_npt() {
+  return L::Q == 9 ? 2 : 1;
+}
+
+// Default shape: two nodes per thread for D2Q9, one for D3Q19, 256 threads.
+template <class L>
+constexpr int bulk_default_shape() {
+  return L::Q == 9 ? 3 : 0;
+}
+
+// Resident blocks per SM a shape is compiled for: the register budget of
+// 256-thread blocks at the precision's count (one fewer for two nodes per
+// thread in FP32, whose registers would otherwise spill), scaled to BT.
+template <class P, int BT, int NPT>
+constexpr int bulk_blocks_per_sm() {
+  constexpr int base = (NPT == 2 && P::bulk_min_blocks > 2) ? P::bulk_min_blocks - 1 : P::bulk_min_blocks;
+  return base * 256 / BT < 1 ? 1 : base * 256 / BT;
+}
+
+// MULTI: the lattice holds several domains; each node's collision reads its
+// run's domain parameters.  Block (0) also clears the force slot of the
+// next step.
+template <class L, class P, bool MULTI, int BT, int NPT>
+__global__ void __launch_bounds__(BT, (bulk_blocks_per_sm<P, BT, NPT>())) k_bulk(const typename P::T* __restrict__ fin,
+                                                                       typename P::T* __restrict__ fout, Layout lay,
+                                                                       Mom4<typename P::T>* __restrict__ mom,
+                                                                       double* __restrict__ force_next, Params p) {
+  using T = typename P::T;
+  if (force_next && blockIdx.x == 0)
+    for (int t = threadIdx.x; t < 3 * p.nbody; t += BT) force_next[t] = 0.0;
+  const uint32_t t = blockIdx.x * BT + threadIdx.x;
+  const size_t S = (size_t)lay.S;
+  const uint32_t stride = (uint32_t)((S + NPT - 1) / NPT);
+  uint32_t k[NPT], w[NPT];
+  int dom[NPT];
+  bool live[NPT];
+  T f[NPT][L::Q];
+#pragma unroll
+  for (int j = 0; j < NPT; ++j) {
+    k[j] = t + (uint32_t)j * stride;
+    live[j] = t < stride && (uint64_t)k[j] < S;
+    w[j] = live[j] ? __ldg(lay.word + k[j]) : W_GHOST;
+    dom[j] = 0;
+    if (live[j] && !(w[j] & (W_GHOST | W_OPEN))) {
+      const RunRec run = lay.runs[w[j] & W_RUN];
+      if (MULTI) dom[j] = run.dom;
+      uint32_t src[L::Q];
+      pull_sources<L>(k[j], run, lay, p, src);
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) f[j][i] = __ldg(fin + (size_t)i * S + src[i]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NPT; ++j) {
+    if (!live[j]) continue;
+    if (w[j] & (W_GHOST | W_OPEN)) {
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) fout[(size_t)i * S + k[j]] = (T)0;
+      continue;
+    }
+    const Relax rx = MULTI ? relax_domain(lay.dom, dom[j]) : relax_params(p);
+    collide_store<L, P>(f[j], p, rx, fout, S, k[j], mom, (w[j] & W_CACHE) != 0);
+  }
 }
 
 // ----------------------------------------------------------------- links --
@@ -364,7 +458,7 @@ __global__ void __launch_bounds__(256) k_links(typename P::T* __restrict__ f, co
     const LinkRec rec = recs[k];
     const int ip = (int)(rec.meta & 31);
     const int rule = (int)((rec.meta >> 5) & 3);
-    body = (int)((rec.meta >> 7) & 127) - 1;
+    body = (int)(rec.meta >> 7) - 1;
     const uint32_t node = rec.kf, ff = rec.kff, s = rec.ks;
     const int i = tab.opp[ip];
     const T ex = tab.e[ip][0], ey = tab.e[ip][1], ez = tab.e[ip][2];
@@ -442,6 +536,21 @@ __global__ void __launch_bounds__(256) k_links(typename P::T* __restrict__ f, co
 
 // ------------------------------------------------------------ open sides --
 
+// Inlet velocity of row y: 4 u_max (y - y0)(y1 - y)/(y1 - y0)^2, with y
+// counted from the first row of the row's domain.
+__device__ __forceinline__ double inlet_velocity(const Params& p, const Layout& lay, int y) {
+  double umax = p.inlet_umax, y0 = p.inlet_y0, y1 = p.inlet_y1, yy = (double)y;
+  if (lay.ndom > 1) {
+    const DomPar& d = lay.dom[lay.row_dom[y]];
+    umax = d.inlet_umax;
+    y0 = d.inlet_y0;
+    y1 = d.inlet_y1;
+    yy = (double)(y - d.lo);
+  }
+  const double h = y1 - y0;
+  return 4.0 * umax * (yy - y0) * (y1 - yy) / (h * h);
+}
+
 // Sec. 4.3: inlet column x = 0 by non-equilibrium extrapolation from x = 1
 // with the parabolic velocity u_in(y); outlet column x = nx-1 copies x = nx-2.
 // One thread per row (D2Q9); the open node is the first (inlet) or last
@@ -457,8 +566,7 @@ __global__ void k_open(typename P::T* __restrict__ f, const Mom4<typename P::T>*
     const int32_t k0 = lay.row_first[y];
     if (k0 >= 0 && (lay.word[k0] & W_OPEN)) {
       const uint32_t k1 = (uint32_t)k0 + 1;
-      const double h = p.inlet_y1 - p.inlet_y0;
-      const T uin = (T)(4.0 * p.inlet_umax * ((double)y - p.inlet_y0) * (p.inlet_y1 - (double)y) / (h * h));
+      const T uin = (T)inlet_velocity(p, lay, y);
       const Mom4<T> m1 = mom[k1];
       const T rho1 = P::shifted ? (T)p.rho0 + m1.r : m1.r;
 #pragma unroll
@@ -497,6 +605,7 @@ __global__ void k_init(typename P::T* __restrict__ f, Mom4<typename P::T>* __res
     return;
   }
   const int64_t n = lay.node_of[k];
+  const Relax rx = relax_of_run(p, lay, w & W_RUN);
   const double rho = rho_in ? rho_in[n] : p.rho0;
   const double ux = u_in ? u_in[3 * n] : 0.0, uy = u_in ? u_in[3 * n + 1] : 0.0;
   const double uz = (u_in && L::D == 3) ? u_in[3 * n + 2] : 0.0;
@@ -507,7 +616,7 @@ __global__ void k_init(typename P::T* __restrict__ f, Mom4<typename P::T>* __res
     const double poly = 3.0 * eu + 4.5 * eu * eu - 1.5 * (ux * ux + uy * uy + uz * uz);
     fl[i] = P::shifted ? (T)(L::w(i) * ((rho - p.rho0) + rho * poly)) : (T)(L::w(i) * rho * (1.0 + poly));
   }
-  collide_store<L, P>(fl, p, f, S, (uint32_t)k, mom, (w & W_CACHE) != 0);
+  collide_store<L, P>(fl, p, rx, f, S, (uint32_t)k, mom, (w & W_CACHE) != 0);
 }
 
 // rho = sum f+, u = (sum f+ e - g/2)/rho of the post-collision state (the
@@ -521,6 +630,7 @@ __global__ void k_moments(const typename P::T* __restrict__ f, Layout lay, doubl
   if (k >= lay.S || !is_fluid(lay.word[k])) return;
   const size_t S = (size_t)lay.S;
   const int64_t N = p.N, n = lay.node_of[k];
+  const Relax rx = relax_of_run(p, lay, lay.word[k] & W_RUN);
   T r = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
@@ -532,9 +642,9 @@ __global__ void k_moments(const typename P::T* __restrict__ f, Layout lay, doubl
   }
   const double rho = P::shifted ? p.rho0 + (double)r : (double)r;
   rho_out[n] = rho;
-  u_out[n] = ((double)jx - 0.5 * p.g[0]) / rho;
-  u_out[N + n] = ((double)jy - 0.5 * p.g[1]) / rho;
-  if (L::D == 3) u_out[2 * N + n] = ((double)jz - 0.5 * p.g[2]) / rho;
+  u_out[n] = ((double)jx - 0.5 * rx.g[0]) / rho;
+  u_out[N + n] = ((double)jy - 0.5 * rx.g[1]) / rho;
+  if (L::D == 3) u_out[2 * N + n] = ((double)jz - 0.5 * rx.g[2]) / rho;
 }
 
 // Moment cache refresh from a post-collision state (after the caller sets
@@ -546,6 +656,7 @@ __global__ void k_refresh(const typename P::T* __restrict__ f, Layout lay, Mom4<
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= lay.S || !(lay.word[k] & W_CACHE) || !is_fluid(lay.word[k])) return;
   const size_t S = (size_t)lay.S;
+  const Relax rx = relax_of_run(p, lay, lay.word[k] & W_RUN);
   T r = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
@@ -556,8 +667,8 @@ __global__ void k_refresh(const typename P::T* __restrict__ f, Layout lay, Mom4<
     jz += (T)L::cz(i) * v;
   }
   const T rho = P::shifted ? (T)p.rho0 + r : r;
-  mom[k] = Mom4<T>{r, (jx - (T)(0.5 * p.g[0])) / rho, (jy - (T)(0.5 * p.g[1])) / rho,
-                   L::D == 3 ? (jz - (T)(0.5 * p.g[2])) / rho : (T)0};
+  mom[k] = Mom4<T>{r, (jx - (T)(0.5 * rx.g[0])) / rho, (jy - (T)(0.5 * rx.g[1])) / rho,
+                   L::D == 3 ? (jz - (T)(0.5 * rx.g[2])) / rho : (T)0};
 }
 
 template <class L>
@@ -624,10 +735,12 @@ __global__ void k_check(const typename P::T* __restrict__ f, Layout lay, int* __
 struct KernelOps {
   int Q, D;
   size_t real_bytes;
+  int default_shape, max_npt;
+  // shape: index into kBulkShapes; threads: link kernel block size (64, 128 or 256)
   void (*bulk)(const void* fin, void* fout, const Layout& lay, void* mom, double* force_next, const Params& p,
-               cudaStream_t s);
+               int shape, cudaStream_t s);
   void (*links)(void* f, const void* mom, const LinkRec* recs, const void* q, const void* uw, int64_t nl,
-                double* force, const Params& p, int64_t S, cudaStream_t s);
+                double* force, const Params& p, int64_t S, int threads, cudaStream_t s);
   void (*open)(void* f, const void* mom, const Layout& lay, const Params& p, cudaStream_t s);
   void (*init)(void* f, void* mom, const Layout& lay, const double* rho, const double* u, const Params& p,
                cudaStream_t s);
@@ -645,16 +758,44 @@ inline unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b
 template <class L, class P>
 struct Launch {
   using T = typename P::T;
+  template <bool M, int BT, int NPT>
+  static void bulk_shape(const void* fin, void* fout, const Layout& lay, void* mom, double* force_next,
+                         const Params& p, cudaStream_t s) {
+    k_bulk<L, P, M, BT, NPT><<<blocks_for((lay.S + NPT - 1) / NPT, BT), BT, 0, s>>>((const T*)fin, (T*)fout, lay,
+                                                                                   (Mom4<T>*)mom, force_next, p);
+  }
+  template <bool M>
+  static void bulk_m(const void* fin, void* fout, const Layout& lay, void* mom, double* fn, const Params& p,
+                     int shape, cudaStream_t s) {
+    switch (shape) {
+      case 1: return bulk_shape<M, 128, 1>(fin, fout, lay, mom, fn, p, s);
+      case 2: return bulk_shape<M, 512, 1>(fin, fout, lay, mom, fn, p, s);
+      default: break;
+    }
+    if constexpr (bulk_max_npt<L>() >= 2) {
+      switch (shape) {
+        case 3: return bulk_shape<M, 256, 2>(fin, fout, lay, mom, fn, p, s);
+        case 4: return bulk_shape<M, 128, 2>(fin, fout, lay, mom, fn, p, s);
+        case 5: return bulk_shape<M, 512, 2>(fin, fout, lay, mom, fn, p, s);
+        default: break;
+      }
+    }
+    bulk_shape<M, 256, 1>(fin, fout, lay, mom, fn, p, s);
+  }
   static void bulk(const void* fin, void* fout, const Layout& lay, void* mom, double* force_next, const Params& p,
-                   cudaStream_t s) {
+                   int shape, cudaStream_t s) {
     if (lay.S == 0) return;
-    k_bulk<L, P><<<blocks_for(lay.S, 256), 256, 0, s>>>((const T*)fin, (T*)fout, lay, (Mom4<T>*)mom, force_next, p);
+    if (lay.ndom > 1)
+      bulk_m<true>(fin, fout, lay, mom, force_next, p, shape, s);
+    else
+      bulk_m<false>(fin, fout, lay, mom, force_next, p, shape, s);
   }
   static void links(void* f, const void* mom, const LinkRec* recs, const void* q, const void* uw, int64_t nl,
-                    double* force, const Params& p, int64_t S, cudaStream_t s) {
+                    double* force, const Params& p, int64_t S, int threads, cudaStream_t s) {
     if (nl == 0) return;
-    k_links<L, P><<<blocks_for(nl, 256), 256, 0, s>>>((T*)f, (const Mom4<T>*)mom, recs, (const T*)q, (const T*)uw, nl,
-                                                     force, p, S);
+    const int bt = (threads == 64 || threads == 128) ? threads : 256;
+    k_links<L, P><<<blocks_for(nl, bt), bt, 0, s>>>((T*)f, (const Mom4<T>*)mom, recs, (const T*)q, (const T*)uw, nl,
+                                                   force, p, S);
   }
   static void open(void* f, const void* mom, const Layout& lay, const Params& p, cudaStream_t s) {
     k_open<L, P><<<blocks_for(p.ny, 128), 128, 0, s>>>((T*)f, (const Mom4<T>*)mom, lay, p);
@@ -690,7 +831,8 @@ struct Launch {
     k_gather<L, P><<<blocks_for(n, 256), 256, 0, s>>>((const T*)f, lay, sk, n, out, p);
   }
   static KernelOps ops() {
-    return KernelOps{L::Q, L::D, sizeof(T), bulk, links, open, init, moments, refresh, get_dir, set_dir, check, gather};
+    return KernelOps{L::Q,    L::D,    sizeof(T), bulk_default_shape<L>(), bulk_max_npt<L>(), bulk, links, open, init,
+                     moments, refresh, get_dir, set_dir, check,     gather};
   }
 };
 

@@ -11,16 +11,8 @@
 
 namespace lbm {
 
-// mask bits of the device node mask
-enum : uint8_t { M_SOLID = 1, M_CACHE = 2, M_OPEN = 4 };
-
-// packed link key: node << 16 | body+1 << 9 | wrap << 8 | fffb << 7 | rule << 5 | dir
-constexpr int KEY_NODE_SHIFT = 16;
-__host__ __device__ inline uint64_t pack_key(int64_t node, int dir, int rule, int ff_fallback, int wrap, int body) {
-  return ((uint64_t)node << KEY_NODE_SHIFT) | ((uint64_t)(body + 1) << 9) | ((uint64_t)wrap << 8) |
-         ((uint64_t)ff_fallback << 7) | ((uint64_t)rule << 5) | (uint64_t)dir;
-}
-constexpr int MAX_BODIES = 64;
+// Largest number of force accumulators (bodies) of a lattice.
+constexpr int MAX_BODIES = 32768;
 
 struct D2Q9 {
   static constexpr int Q = 9, D = 2;
@@ -85,6 +77,7 @@ struct Params {
   int inlet, outlet;
   int vibb_local_rho;   // rho_d = rho_f when q > 1/2
   int periodic[3];
+  int nbody;            // force accumulators per slot (max body id + 1, >= 1)
 };
 
 // Error message shared by every translation unit of the library (set by a

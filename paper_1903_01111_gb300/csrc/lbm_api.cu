@@ -2,10 +2,11 @@
 //
 // A lattice owns two population buffers (ping-pong) over the stored nodes of
 // the compacted layout (fluid, open-column and ghost nodes, see
-// kernels.cuh), the moment cache, the layout tables, the link records and
-// two FP64 force slots.  lbm_step replays a captured CUDA graph of two steps
-// and launches single steps directly for an odd remainder; with profiling on
-// it launches kernel by kernel between CUDA events.
+// kernels.cuh), the moment cache, the layout tables, the link records, the
+// domain table of a batch and two FP64 force slots.  lbm_step replays
+// captured CUDA graphs (graph_steps steps, then two) and launches single
+// steps directly for an odd remainder; with profiling on it launches kernel
+// by kernel between CUDA events.  lbm_autotune picks the launch shapes.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -16,6 +17,7 @@
 #include <new>
 #include <vector>
 
+#include "adjoint.cuh"
 #include "kernels.cuh"
 #include "lbm.h"
 
@@ -59,6 +61,7 @@ struct DeviceBuf {
 struct lbm_lattice_s {
   lbm_config cfg{};
   KernelOps ops{};
+  AdjointOps adj{};
   Params p{};
   int Q = 0, D = 0;
   int64_t N = 0;
@@ -68,20 +71,28 @@ struct lbm_lattice_s {
   // layout
   DeviceBuf word, node_of, runs, row_first, row_last;
   Layout lay{};
+  // batch: domains along the last axis (empty: one domain run by cfg)
+  std::vector<lbm_domain> domains;
+  DeviceBuf dom, row_dom;
+  int nbody = 1;  // force accumulators per slot
+  lbm_tuning tune{-1, 256, 2, 0};
   std::vector<int32_t> sidx;  // dense -> storage index (-1: not stored), host
   // links
   DeviceBuf recs, q, uw;
   int64_t n_links = 0, n_fluid = 0, n_cached = 0, n_runs = 0;
-  DeviceBuf force;  // [2][MAX_BODIES][3]
+  DeviceBuf force;  // [2][nbody][3]
   // shifted storage: sum over each body's links of 2 w_i' rho0 e_i' (FP64),
   // the rest part of the momentum exchange that the link kernel leaves out
-  std::vector<double> force_rest = std::vector<double>(3 * MAX_BODIES, 0.0);
+  std::vector<double> force_rest = std::vector<double>(3, 0.0);
+  std::vector<int64_t> link_order;  // device link j = caller's link link_order[j]
+  bool from_init = false;           // state is the one lbm_init_equilibrium made
   int cur = 0;      // buffer holding f+(t)
   int64_t step = 0;
   bool has_geometry = false, has_state = false;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};   // two steps, per parity of the buffer
+  cudaGraphExec_t graphG[2] = {nullptr, nullptr};  // tune.graph_steps steps
   // profiling
   bool profiling = false;
   std::vector<cudaEvent_t> ev;
@@ -94,8 +105,8 @@ struct lbm_lattice_s {
 namespace {
 
 int64_t device_bytes(const lbm_handle h) {
-  const DeviceBuf* all[] = {&h->f[0], &h->f[1], &h->mom, &h->word, &h->node_of, &h->runs, &h->row_first,
-                            &h->row_last, &h->recs, &h->q, &h->uw, &h->force};
+  const DeviceBuf* all[] = {&h->f[0], &h->f[1], &h->mom,  &h->word, &h->node_of, &h->runs, &h->row_first,
+                            &h->row_last, &h->recs, &h->q,    &h->uw,   &h->force,   &h->dom,  &h->row_dom};
   int64_t s = 0;
   for (auto* b : all) s += (int64_t)b->bytes;
   return s;
@@ -128,16 +139,16 @@ lbm_status upload(DeviceBuf& b, const void* src, size_t bytes) {
 }
 
 void drop_graphs(lbm_handle h) {
-  for (int k = 0; k < 2; ++k)
-    if (h->graph[k]) {
-      cudaGraphExecDestroy(h->graph[k]);
-      h->graph[k] = nullptr;
-    }
+  for (int k = 0; k < 2; ++k) {
+    if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+    if (h->graphG[k]) cudaGraphExecDestroy(h->graphG[k]);
+    h->graph[k] = h->graphG[k] = nullptr;
+  }
 }
 
 void release_geometry(lbm_handle h) {
-  DeviceBuf* all[] = {&h->f[0], &h->f[1], &h->mom, &h->word, &h->node_of, &h->runs,
-                      &h->row_first, &h->row_last, &h->recs, &h->q, &h->uw};
+  DeviceBuf* all[] = {&h->f[0], &h->f[1], &h->mom, &h->word, &h->node_of, &h->runs, &h->row_first,
+                      &h->row_last, &h->recs, &h->q, &h->uw, &h->dom, &h->row_dom};
   for (auto* b : all) release(*b);
   h->lay = Layout{};
 }
@@ -146,13 +157,19 @@ int cx_of(const lbm_handle h, int i) { return h->Q == 9 ? D2Q9::cx(i) : D3Q19::c
 int cy_of(const lbm_handle h, int i) { return h->Q == 9 ? D2Q9::cy(i) : D3Q19::cy(i); }
 int cz_of(const lbm_handle h, int i) { return h->Q == 9 ? D2Q9::cz(i) : D3Q19::cz(i); }
 
+// Enqueue one time step from buffer fc (f+(t)) into fn, adding the force to
+// `slot` and clearing `next`.
+lbm_status enqueue_step_buf(lbm_handle h, void* fc, void* fn, double* slot, double* next, bool timed);
+
 // Enqueue one time step on the stream (parity = buffer holding f+(t)).
 lbm_status enqueue_step(lbm_handle h, int parity, int64_t step_index, bool timed) {
-  void* fc = h->f[parity].p;
-  void* fn = h->f[parity ^ 1].p;
   double* force = (double*)h->force.p;
-  double* slot = force + 3 * MAX_BODIES * (step_index & 1);
-  double* next = force + 3 * MAX_BODIES * ((step_index + 1) & 1);
+  const int64_t nb3 = 3 * (int64_t)h->nbody;
+  return enqueue_step_buf(h, h->f[parity].p, h->f[parity ^ 1].p, force + nb3 * (step_index & 1),
+                          force + nb3 * ((step_index + 1) & 1), timed);
+}
+
+lbm_status enqueue_step_buf(lbm_handle h, void* fc, void* fn, double* slot, double* next, bool timed) {
   auto timed_launch = [&](int kid, auto&& fn_launch) -> lbm_status {
     if (!timed) {
       fn_launch();
@@ -177,14 +194,14 @@ lbm_status enqueue_step(lbm_handle h, int parity, int64_t step_index, bool timed
   lbm_status st;
   st = timed_launch(0, [&] {
     h->ops.links(fc, h->mom.p, (const LinkRec*)h->recs.p, h->q.p, h->uw.p, h->n_links, slot, h->p, h->lay.S,
-                 h->stream);
+                 h->tune.link_threads, h->stream);
   });
   if (st != LBM_OK) return st;
   if (h->p.inlet || h->p.outlet) {
     st = timed_launch(1, [&] { h->ops.open(fc, h->mom.p, h->lay, h->p, h->stream); });
     if (st != LBM_OK) return st;
   }
-  st = timed_launch(2, [&] { h->ops.bulk(fc, fn, h->lay, h->mom.p, next, h->p, h->stream); });
+  st = timed_launch(2, [&] { h->ops.bulk(fc, fn, h->lay, h->mom.p, next, h->p, h->tune.bulk_shape, h->stream); });
   if (st != LBM_OK) return st;
   CUDA_TRY(cudaGetLastError());
   return LBM_OK;
@@ -203,19 +220,20 @@ lbm_status harvest_events(lbm_handle h) {
   return LBM_OK;
 }
 
-lbm_status build_graph(lbm_handle h, int parity) {
+// A graph of `steps` (even) steps from the buffer `parity`; graphs are
+// replayed from even step counts only, so the force slots alternate 0, 1.
+lbm_status build_graph(lbm_handle h, int parity, int steps, cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-  // graphs are replayed from even step counts only: force slots 0 then 1
-  lbm_status st = enqueue_step(h, parity, 0, false);
-  if (st == LBM_OK) st = enqueue_step(h, parity ^ 1, 1, false);
+  lbm_status st = LBM_OK;
+  for (int k = 0; k < steps && st == LBM_OK; ++k) st = enqueue_step(h, parity ^ (k & 1), k, false);
   cudaError_t e = cudaStreamEndCapture(h->stream, &g);
   if (st != LBM_OK) {
     if (g) cudaGraphDestroy(g);
     return st;
   }
   if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "stream capture: %s", cudaGetErrorString(e));
-  e = cudaGraphInstantiate(&h->graph[parity], g, 0);
+  e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
   return LBM_OK;
@@ -270,6 +288,10 @@ lbm_status lbm_create_lattice(const lbm_config* cfg, lbm_handle* out) {
     h->ops = c.precision == LBM_FP64 ? ops_d2q9_f64() : ops_d2q9_f32s();
   else
     h->ops = c.precision == LBM_FP64 ? ops_d3q19_f64() : ops_d3q19_f32s();
+  if (c.stencil == LBM_D2Q9)
+    h->adj = c.precision == LBM_FP64 ? adj_d2q9_f64() : adj_d2q9_f32s();
+  else
+    h->adj = c.precision == LBM_FP64 ? adj_d3q19_f64() : adj_d3q19_f32s();
   h->Q = h->ops.Q;
   h->D = h->ops.D;
   h->N = N;
@@ -293,6 +315,8 @@ lbm_status lbm_create_lattice(const lbm_config* cfg, lbm_handle* out) {
   p.inlet_y1 = c.inlet_y1;
   p.vibb_local_rho = c.vibb_density == LBM_VIBB_RHO_LOCAL ? 1 : 0;
   for (int a = 0; a < 3; ++a) p.periodic[a] = c.periodic[a] ? 1 : 0;
+  p.nbody = 1;
+  h->tune.bulk_shape = h->ops.default_shape;
 
   if (c.cuda_stream) {
     h->stream = (cudaStream_t)c.cuda_stream;
@@ -304,7 +328,7 @@ lbm_status lbm_create_lattice(const lbm_config* cfg, lbm_handle* out) {
     }
     h->own_stream = true;
   }
-  lbm_status st = acquire(h->force, sizeof(double) * 2 * 3 * MAX_BODIES);
+  lbm_status st = acquire(h->force, sizeof(double) * 2 * 3);
   if (st == LBM_OK) {
     cudaError_t e = cudaMemsetAsync(h->force.p, 0, h->force.bytes, h->stream);
     if (e != cudaSuccess) st = fail(LBM_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
@@ -332,6 +356,33 @@ lbm_status lbm_destroy(lbm_handle h) {
   return LBM_OK;
 }
 
+lbm_status lbm_set_domains(lbm_handle h, const lbm_domain* d, int32_t n) {
+  g_msg[0] = 0;
+  if (!h || n < 0 || (n > 0 && !d)) return fail(LBM_ERR_INVALID_ARG, "null or negative argument");
+  if (h->has_geometry) return fail(LBM_ERR_STATE, "set the domains before the geometry");
+  const lbm_config& c = h->cfg;
+  const int64_t len = h->D == 2 ? c.ny : c.nz;
+  int64_t next = 0;
+  for (int32_t k = 0; k < n; ++k) {
+    const lbm_domain& q = d[k];
+    if (q.lo != next) return fail(LBM_ERR_INVALID_ARG, "domain %d starts at row %d, expected %lld", k, q.lo, (long long)next);
+    if (q.n < 3) return fail(LBM_ERR_INVALID_ARG, "domain %d has %d rows (at least 3)", k, q.n);
+    if (q.nx < 1 || q.nx > c.nx) return fail(LBM_ERR_INVALID_ARG, "domain %d: width %d not in 1..%d", k, q.nx, c.nx);
+    if (c.periodic[0] && q.nx != c.nx)
+      return fail(LBM_ERR_INVALID_ARG, "domain %d: a periodic x axis needs the full width %d", k, c.nx);
+    if (!(q.tau > 0.5) || !std::isfinite(q.tau)) return fail(LBM_ERR_INVALID_ARG, "domain %d: tau must be > 1/2", k);
+    for (int a = 0; a < 3; ++a)
+      if (!std::isfinite(q.g[a])) return fail(LBM_ERR_INVALID_ARG, "domain %d: g must be finite", k);
+    if (c.inlet && !(q.inlet_y1 > q.inlet_y0))
+      return fail(LBM_ERR_INVALID_ARG, "domain %d: the inlet needs inlet_y1 > inlet_y0", k);
+    next = (int64_t)q.lo + q.n;
+  }
+  if (n > 0 && next != len)
+    return fail(LBM_ERR_INVALID_ARG, "domains cover %lld of %lld rows", (long long)next, (long long)len);
+  h->domains.assign(d, d + n);
+  return LBM_OK;
+}
+
 lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* links, int64_t n_links) {
   g_msg[0] = 0;
   if (!h || !solid || n_links < 0 || (n_links > 0 && !links)) return fail(LBM_ERR_INVALID_ARG, "null or negative argument");
@@ -339,16 +390,49 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
   const int64_t N = h->N, nx = c.nx, ny = c.ny, nz = c.nz;
   const int Q = h->Q, D = h->D;
   if (n_links >= ((int64_t)1 << 31)) return fail(LBM_ERR_UNSUPPORTED, "at most 2^31 - 1 links");
+  // domains: row r = y + ny z belongs to domain rdom[r]; width of each row
+  const int ndom = (int)h->domains.size();
+  const int64_t rows = ny * nz;
+  std::vector<int32_t> rdom(rows, 0);
+  std::vector<int64_t> rwidth(rows, nx);
+  for (int k = 0; k < ndom; ++k) {
+    const lbm_domain& q = h->domains[k];
+    for (int64_t r = 0; r < rows; ++r) {
+      const int64_t a = D == 2 ? r % ny : r / ny;  // stacking axis: y (2-D) or z (3-D)
+      if (a >= q.lo && a < (int64_t)q.lo + q.n) {
+        rdom[r] = k;
+        rwidth[r] = q.nx;
+      }
+    }
+  }
   // node classes
   std::vector<uint8_t> m(N);
   for (int64_t n = 0; n < N; ++n) m[n] = solid[n] ? H_SOLID : 0;
-  if (c.inlet || c.outlet)
-    for (int64_t z = 0; z < nz; ++z)
-      for (int64_t y = 0; y < ny; ++y) {
-        const int64_t row = nx * (y + ny * z);
-        if (c.inlet && !(m[row] & H_SOLID)) m[row] |= H_OPEN;
-        if (c.outlet && !(m[row + nx - 1] & H_SOLID)) m[row + nx - 1] |= H_OPEN;
+  if (ndom > 0) {
+    for (int64_t r = 0; r < rows; ++r)
+      for (int64_t x = rwidth[r]; x < nx; ++x)
+        if (!(m[x + nx * r] & H_SOLID))
+          return fail(LBM_ERR_INVALID_ARG, "node (%lld, row %lld) lies beyond the width %lld of domain %d: it must be solid",
+                      (long long)x, (long long)r, (long long)rwidth[r], rdom[r]);
+    for (int k = 0; k < ndom; ++k) {
+      const lbm_domain& q = h->domains[k];
+      for (int64_t r = 0; r < rows; ++r) {
+        const int64_t a = D == 2 ? r % ny : r / ny;
+        if (a != q.lo && a != (int64_t)q.lo + q.n - 1) continue;
+        for (int64_t x = 0; x < nx; ++x)
+          if (!(m[x + nx * r] & H_SOLID))
+            return fail(LBM_ERR_INVALID_ARG,
+                        "domain %d: its first and last rows must be solid (node %lld of row %lld is not)", k,
+                        (long long)x, (long long)r);
       }
+    }
+  }
+  if (c.inlet || c.outlet)
+    for (int64_t r = 0; r < rows; ++r) {
+      const int64_t row = nx * r;
+      if (c.inlet && !(m[row] & H_SOLID)) m[row] |= H_OPEN;
+      if (c.outlet && !(m[row + rwidth[r] - 1] & H_SOLID)) m[row + rwidth[r] - 1] |= H_OPEN;
+    }
   // faces of non-periodic axes must be solid (or open columns)
   const int64_t len[3] = {nx, ny, nz};
   for (int a = 0; a < 3; ++a) {
@@ -384,6 +468,7 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
   std::vector<int64_t> lk_s(n_links), lk_ff(n_links);
   std::vector<int> lk_rule(n_links);
   bool moving = false;
+  int nbody = 1;
   for (int64_t k = 0; k < n_links; ++k) {
     const lbm_link& L = links[k];
     if (L.node < 0 || L.node >= N) return fail(LBM_ERR_INVALID_ARG, "link %lld: node out of range", (long long)k);
@@ -395,6 +480,7 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
       return fail(LBM_ERR_INVALID_ARG, "link %lld: unknown rule %d", (long long)k, L.bc);
     if (L.body < -1 || L.body >= MAX_BODIES)
       return fail(LBM_ERR_INVALID_ARG, "link %lld: body %d out of range", (long long)k, L.body);
+    nbody = std::max(nbody, (int)L.body + 1);
     for (int a = 0; a < 3; ++a)
       if (!std::isfinite(L.uw[a])) return fail(LBM_ERR_INVALID_ARG, "link %lld: non-finite wall velocity", (long long)k);
     const int64_t s = neighbour(L.node, L.dir, 1);
@@ -440,9 +526,9 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
       return fail(LBM_ERR_INVALID_ARG, "duplicate link at node %lld direction %d",
                   (long long)(nodedir(order[k]) / 32), (int)(nodedir(order[k]) % 32));
   {
-    std::vector<int64_t> count(MAX_BODIES + 2, 0);
+    std::vector<int64_t> count(nbody + 2, 0);
     for (int64_t k = 0; k < n_links; ++k) count[links[k].body + 2]++;
-    for (int b = 1; b < MAX_BODIES + 2; ++b) count[b] += count[b - 1];
+    for (int b = 1; b < nbody + 2; ++b) count[b] += count[b - 1];
     std::vector<int64_t> byb(n_links);
     for (int64_t k = 0; k < n_links; ++k) byb[count[links[order[k]].body + 1]++] = order[k];
     order.swap(byb);
@@ -480,7 +566,6 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
       node_of.push_back((int32_t)n);
     }
   const int64_t S = (int64_t)node_of.size();
-  const int64_t rows = ny * nz;
   std::vector<int32_t> row_first(rows, -1), row_last(rows, -1);
   for (int64_t r = 0; r < rows; ++r)
     for (int64_t x = 0; x < nx; ++x) {
@@ -526,6 +611,7 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
       rec.k0 = sidx[n];
       rec.y = (int32_t)y;
       rec.z = (int32_t)z;
+      rec.dom = rdom[r];
       for (int sl = 0; sl < nslots; ++sl) {
         const int64_t yy = (y + slot_dy[sl] + ny) % ny, zz = (z + slot_dz[sl] + nz) % nz;
         const int64_t rr = yy + ny * zz;
@@ -561,7 +647,7 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
       n_cached += (m[n] & H_CACHE) ? 1 : 0;
   }
   // rest part of the momentum exchange per body (shifted storage)
-  std::vector<double> rest(3 * MAX_BODIES, 0.0);
+  std::vector<double> rest(3 * (size_t)nbody, 0.0);
   if (c.precision == LBM_FP32_SHIFTED)
     for (int64_t k = 0; k < n_links; ++k) {
       const lbm_link& L = links[k];
@@ -603,6 +689,29 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
   if (st == LBM_OK) st = upload(h->row_first, row_first.data(), sizeof(int32_t) * rows);
   if (st == LBM_OK) st = upload(h->row_last, row_last.data(), sizeof(int32_t) * rows);
   if (st == LBM_OK) st = upload(h->recs, recs.data(), sizeof(LinkRec) * n_links);
+  if (st == LBM_OK && ndom > 0) {
+    std::vector<DomPar> dp(ndom);
+    for (int k = 0; k < ndom; ++k) {
+      const lbm_domain& q = h->domains[k];
+      dp[k].omega = 1.0 / q.tau;
+      dp[k].fpre3 = 3.0 * (1.0 - 0.5 / q.tau);
+      for (int a = 0; a < 3; ++a) dp[k].g[a] = a < D ? q.g[a] : 0.0;
+      dp[k].has_force = (dp[k].g[0] != 0.0 || dp[k].g[1] != 0.0 || dp[k].g[2] != 0.0) ? 1 : 0;
+      dp[k].inlet_umax = q.inlet_umax;
+      dp[k].inlet_y0 = q.inlet_y0;
+      dp[k].inlet_y1 = q.inlet_y1;
+      dp[k].lo = q.lo;
+    }
+    st = upload(h->dom, dp.data(), sizeof(DomPar) * ndom);
+    if (st == LBM_OK) st = upload(h->row_dom, rdom.data(), sizeof(int32_t) * rows);
+  }
+  if (st == LBM_OK && h->force.bytes != sizeof(double) * 6 * (size_t)nbody) {
+    st = acquire(h->force, sizeof(double) * 6 * (size_t)nbody);
+    if (st == LBM_OK) {
+      cudaError_t e = cudaMemsetAsync(h->force.p, 0, h->force.bytes, h->stream);
+      if (e != cudaSuccess) st = fail(LBM_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    }
+  }
   if (st == LBM_OK) {
     if (rb == 8) {
       st = upload(h->q, qs.data(), 8 * n_links);
@@ -627,12 +736,30 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
   h->lay.runs = (const RunRec*)h->runs.p;
   h->lay.row_first = (const int32_t*)h->row_first.p;
   h->lay.row_last = (const int32_t*)h->row_last.p;
+  h->lay.dom = ndom > 0 ? (const DomPar*)h->dom.p : nullptr;
+  h->lay.row_dom = ndom > 0 ? (const int32_t*)h->row_dom.p : nullptr;
+  h->lay.ndom = std::max(ndom, 1);
+  // a single domain runs through Params like an unsplit lattice
+  Params& p = h->p;
+  const lbm_domain one{0, 0, 0, 0, c.tau, {c.g[0], c.g[1], c.g[2]}, c.inlet_umax, c.inlet_y0, c.inlet_y1};
+  const lbm_domain& d0 = ndom == 1 ? h->domains[0] : one;
+  p.tau = d0.tau;
+  p.omega = 1.0 / d0.tau;
+  p.fpre3 = 3.0 * (1.0 - 0.5 / d0.tau);
+  for (int a = 0; a < 3; ++a) p.g[a] = a < D ? d0.g[a] : 0.0;
+  p.has_force = (p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0);
+  p.inlet_umax = d0.inlet_umax;
+  p.inlet_y0 = d0.inlet_y0;
+  p.inlet_y1 = d0.inlet_y1;
+  h->nbody = nbody;
+  h->p.nbody = nbody;
   h->sidx.swap(sidx);
   h->n_links = n_links;
   h->n_fluid = n_fluid;
   h->n_cached = n_cached;
   h->n_runs = (int64_t)runs.size();
   h->force_rest.swap(rest);
+  h->link_order.swap(order);
   h->has_geometry = true;
   return LBM_OK;
 }
@@ -667,6 +794,7 @@ lbm_status lbm_init_equilibrium(lbm_handle h, const double* rho, const double* u
   h->cur = 0;
   h->step = 0;
   h->has_state = true;
+  h->from_init = true;
   return LBM_OK;
 }
 
@@ -689,7 +817,8 @@ lbm_status lbm_step(lbm_handle h, int64_t n) {
     return LBM_OK;
   }
   int64_t left = n;
-  // graphs run two steps and keep the force slot parity; align first
+  // graphs run an even number of steps and keep the force slot parity;
+  // align first
   if (left > 0 && (h->step & 1)) {
     lbm_status st = enqueue_step(h, h->cur, h->step, false);
     if (st != LBM_OK) return st;
@@ -697,9 +826,20 @@ lbm_status lbm_step(lbm_handle h, int64_t n) {
     ++h->step;
     --left;
   }
+  const int G = h->tune.graph_steps;
+  if (G > 2 && left >= G) {
+    if (!h->graphG[h->cur]) {
+      lbm_status st = build_graph(h, h->cur, G, &h->graphG[h->cur]);
+      if (st != LBM_OK) return st;
+    }
+    for (; left >= G; left -= G) {
+      CUDA_TRY(cudaGraphLaunch(h->graphG[h->cur], h->stream));
+      h->step += G;
+    }
+  }
   if (left >= 2) {
     if (!h->graph[h->cur]) {
-      lbm_status st = build_graph(h, h->cur);
+      lbm_status st = build_graph(h, h->cur, 2, &h->graph[h->cur]);
       if (st != LBM_OK) return st;
     }
     for (; left >= 2; left -= 2) {
@@ -750,10 +890,28 @@ lbm_status lbm_force(lbm_handle h, int32_t body, double F[3]) {
   if (!h || !F) return fail(LBM_ERR_INVALID_ARG, "null argument");
   if (body < 0 || body >= MAX_BODIES) return fail(LBM_ERR_INVALID_ARG, "body %d out of range", body);
   if (!h->has_state || h->step == 0) return fail(LBM_ERR_STATE, "no step has run");
-  const double* slot = (const double*)h->force.p + 3 * MAX_BODIES * ((h->step - 1) & 1) + 3 * body;
+  if (body >= h->nbody) {
+    F[0] = F[1] = F[2] = 0.0;
+    return LBM_OK;
+  }
+  const double* slot = (const double*)h->force.p + 3 * (int64_t)h->nbody * ((h->step - 1) & 1) + 3 * body;
   CUDA_TRY(cudaMemcpyAsync(F, slot, sizeof(double) * 3, cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   for (int a = 0; a < 3; ++a) F[a] += h->force_rest[3 * body + a];
+  return LBM_OK;
+}
+
+lbm_status lbm_forces(lbm_handle h, int32_t n, double* F) {
+  g_msg[0] = 0;
+  if (!h || n < 0 || (n > 0 && !F)) return fail(LBM_ERR_INVALID_ARG, "null or negative argument");
+  if (n > MAX_BODIES) return fail(LBM_ERR_INVALID_ARG, "%d bodies requested, at most %d", n, MAX_BODIES);
+  if (!h->has_state || h->step == 0) return fail(LBM_ERR_STATE, "no step has run");
+  const int m = std::min(n, h->nbody);
+  const double* slot = (const double*)h->force.p + 3 * (int64_t)h->nbody * ((h->step - 1) & 1);
+  if (m > 0) CUDA_TRY(cudaMemcpyAsync(F, slot, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  for (int64_t k = 0; k < 3 * (int64_t)m; ++k) F[k] += h->force_rest[k];
+  for (int64_t k = 3 * (int64_t)m; k < 3 * (int64_t)n; ++k) F[k] = 0.0;
   return LBM_OK;
 }
 
@@ -804,6 +962,7 @@ lbm_status lbm_set_distributions(lbm_handle h, const double* f) {
   cudaFree(tmp);
   if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "set_distributions: %s", cudaGetErrorString(e));
   h->has_state = true;
+  h->from_init = false;
   return LBM_OK;
 }
 
@@ -854,6 +1013,210 @@ lbm_status lbm_check(lbm_handle h) {
   return LBM_OK;
 }
 
+lbm_status lbm_adjoint_step(lbm_handle h, int32_t body, const double dJ_dF[3], int64_t n_steps,
+                            int64_t checkpoint_every, double* J, double* dJ_dq, double* dJ_dtau, double seconds[3]) {
+  g_msg[0] = 0;
+  if (!h || !dJ_dF || !J || !dJ_dtau || (h && h->n_links > 0 && !dJ_dq))
+    return fail(LBM_ERR_INVALID_ARG, "null argument");
+  if (!h->has_state) return fail(LBM_ERR_STATE, "initialise the state first");
+  if (h->cfg.collision != LBM_BGK) return fail(LBM_ERR_UNSUPPORTED, "the adjoint is built for BGK collision");
+  if (n_steps < 1 || checkpoint_every < 1) return fail(LBM_ERR_INVALID_ARG, "n_steps and checkpoint_every must be >= 1");
+  if (body < -1 || body >= MAX_BODIES) return fail(LBM_ERR_INVALID_ARG, "body %d out of range", body);
+  const bool from_init = h->from_init && h->step == 0;
+  const int nb = h->nbody;
+  const int ndom = std::max<int>((int)h->domains.size(), 1);
+  // objective weights per body
+  std::vector<double> wbody(3 * (size_t)nb, 0.0);
+  if (body >= 0) {
+    if (body < nb)
+      for (int a = 0; a < 3; ++a) wbody[3 * body + a] = dJ_dF[a];
+  } else {
+    for (size_t k = 0; k < wbody.size(); ++k) wbody[k] = dJ_dF[k];
+  }
+  const int64_t S = h->lay.S, Q = h->Q, nl = h->n_links;
+  const size_t sb = (size_t)Q * S * h->rb;  // bytes of one state
+  const int64_t K = std::min(checkpoint_every, n_steps);
+  const int64_t nck = (n_steps + K - 1) / K;
+  DeviceBuf ck, seg, lam[2], dq, scr;
+  lbm_status st = acquire(ck, sb * nck);
+  if (st == LBM_OK) st = acquire(seg, sb * K);
+  if (st == LBM_OK) st = acquire(lam[0], sb);
+  if (st == LBM_OK) st = acquire(lam[1], sb);
+  if (st == LBM_OK) st = acquire(dq, sizeof(double) * std::max<int64_t>(nl, 1));
+  if (st == LBM_OK) st = acquire(scr, sizeof(double) * (ndom + 9 * (size_t)nb));
+  auto cleanup = [&]() {
+    release(ck);
+    release(seg);
+    release(lam[0]);
+    release(lam[1]);
+    release(dq);
+    release(scr);
+  };
+  if (st != LBM_OK) {
+    cleanup();
+    return st;
+  }
+  char* ckp = (char*)ck.p;
+  char* segp = (char*)seg.p;
+  double* dtau = (double*)scr.p;       // [ndom]
+  double* fslot = dtau + ndom;         // scratch force slots of the recomputed steps, [2][nb][3]
+  double* wdev = fslot + 6 * (size_t)nb;  // objective weights [nb][3]
+  cudaEvent_t ev[2];
+  cudaEventCreate(&ev[0]);
+  cudaEventCreate(&ev[1]);
+  double t_fwd = 0.0, t_rec = 0.0, t_adj = 0.0;
+  auto timed = [&](double& acc, auto&& work) -> lbm_status {
+    cudaEventRecord(ev[0], h->stream);
+    lbm_status r = work();
+    cudaEventRecord(ev[1], h->stream);
+    cudaEventSynchronize(ev[1]);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    acc += ms * 1e-3;
+    return r;
+  };
+  cudaError_t e = cudaMemsetAsync(dq.p, 0, dq.bytes, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(scr.p, 0, scr.bytes, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(wdev, wbody.data(), sizeof(double) * wbody.size(), cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) st = fail(LBM_ERR_CUDA, "adjoint set-up: %s", cudaGetErrorString(e));
+  // forward with checkpoints
+  if (st == LBM_OK)
+    st = timed(t_fwd, [&]() -> lbm_status {
+      for (int64_t c = 0; c < nck; ++c) {
+        CUDA_TRY(cudaMemcpyAsync(ckp + sb * c, h->f[h->cur].p, sb, cudaMemcpyDeviceToDevice, h->stream));
+        const lbm_status r = lbm_step(h, std::min(K, n_steps - c * K));
+        if (r != LBM_OK) return r;
+      }
+      return LBM_OK;
+    });
+  std::vector<double> F(3 * (size_t)nb, 0.0);
+  if (st == LBM_OK) st = lbm_forces(h, nb, F.data());
+  if (st == LBM_OK) {
+    double Jv = 0.0;
+    for (size_t k = 0; k < F.size(); ++k) Jv += wbody[k] * F[k];
+    *J = Jv;
+  }
+  // backward: lambda(n) = 0 in both buffers; every adjoint step leaves the
+  // buffer it read zero again
+  int la = 0;
+  if (st == LBM_OK) {
+    e = cudaMemsetAsync(lam[0].p, 0, sb, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(lam[1].p, 0, sb, h->stream);
+    if (e != cudaSuccess) st = fail(LBM_ERR_CUDA, "adjoint: %s", cudaGetErrorString(e));
+  }
+  const bool open = h->p.inlet || h->p.outlet;
+  // the states f+(s0) .. f+(s0 + m - 1) of a segment from its first state
+  // (copied into seg[0]); the link and open kernels leave the link values
+  // of step s0 + j in the ghost slots of seg[j] for j < m - 1
+  auto enqueue_recompute = [&](int64_t m) -> lbm_status {
+    h->ops.refresh(segp, h->lay, h->mom.p, h->p, h->stream);
+    for (int64_t j = 0; j + 1 < m; ++j) {
+      const lbm_status r = enqueue_step_buf(h, segp + sb * j, segp + sb * (j + 1), fslot, fslot + 3 * (size_t)nb, false);
+      if (r != LBM_OK) return r;
+    }
+    CUDA_TRY(cudaGetLastError());
+    return LBM_OK;
+  };
+  // the transposed steps s0 + m - 1 .. s0 of a segment; lambda(s0 + m) in
+  // lam[l0]; `last`: the segment ends with the objective's step
+  auto enqueue_adjoint = [&](int64_t m, int l0, bool last) -> lbm_status {
+    int l = l0;
+    for (int64_t j = m - 1; j >= 0; --j) {
+      void* state = segp + sb * j;
+      if (j == m - 1) {
+        // the last state of the segment has no link values yet
+        h->ops.refresh(state, h->lay, h->mom.p, h->p, h->stream);
+        h->ops.links(state, h->mom.p, (const LinkRec*)h->recs.p, h->q.p, h->uw.p, nl, fslot, h->p, S,
+                     h->tune.link_threads, h->stream);
+        if (open) h->ops.open(state, h->mom.p, h->lay, h->p, h->stream);
+      }
+      h->adj.bulk(state, lam[l].p, lam[l ^ 1].p, h->lay, h->p, dtau, h->mom.p, h->stream);
+      h->adj.links(state, h->mom.p, lam[l ^ 1].p, (const LinkRec*)h->recs.p, h->q.p, h->uw.p, nl, h->p, S,
+                   (double*)dq.p, (last && j == m - 1) ? 1 : 0, wdev, h->stream);
+      if (open) h->adj.open(lam[l ^ 1].p, h->mom.p, h->lay, h->p, h->stream);
+      l ^= 1;
+    }
+    CUDA_TRY(cudaGetLastError());
+    return LBM_OK;
+  };
+  // segments other than the last replay captured graphs (keyed by length
+  // and the lambda buffer they start from)
+  struct SegGraph {
+    int kind;
+    int64_t m;
+    int l0;
+    cudaGraphExec_t g;
+  };
+  std::vector<SegGraph> seg_graphs;
+  auto replay = [&](int kind, int64_t m, int l0, auto&& enqueue) -> lbm_status {
+    for (const SegGraph& sg : seg_graphs)
+      if (sg.kind == kind && sg.m == m && sg.l0 == l0) {
+        CUDA_TRY(cudaGraphLaunch(sg.g, h->stream));
+        return LBM_OK;
+      }
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    const lbm_status r = enqueue();
+    const cudaError_t ec = cudaStreamEndCapture(h->stream, &g);
+    if (r != LBM_OK) {
+      if (g) cudaGraphDestroy(g);
+      return r;
+    }
+    if (ec != cudaSuccess) return fail(LBM_ERR_CUDA, "adjoint capture: %s", cudaGetErrorString(ec));
+    cudaGraphExec_t x = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&x, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) return fail(LBM_ERR_CUDA, "adjoint graph: %s", cudaGetErrorString(ei));
+    seg_graphs.push_back(SegGraph{kind, m, l0, x});
+    CUDA_TRY(cudaGraphLaunch(x, h->stream));
+    return LBM_OK;
+  };
+  for (int64_t c = nck - 1; c >= 0 && st == LBM_OK; --c) {
+    const int64_t s0 = c * K, m = std::min(K, n_steps - s0);
+    const bool last = c == nck - 1;
+    st = timed(t_rec, [&]() -> lbm_status {
+      CUDA_TRY(cudaMemcpyAsync(segp, ckp + sb * c, sb, cudaMemcpyDeviceToDevice, h->stream));
+      if (last) return enqueue_recompute(m);
+      return replay(0, m, 0, [&] { return enqueue_recompute(m); });
+    });
+    if (st != LBM_OK) break;
+    const int l0 = la;
+    st = timed(t_adj, [&]() -> lbm_status {
+      if (last) return enqueue_adjoint(m, l0, true);
+      return replay(1, m, l0, [&] { return enqueue_adjoint(m, l0, false); });
+    });
+    if (m & 1) la ^= 1;
+  }
+  for (const SegGraph& sg : seg_graphs) cudaGraphExecDestroy(sg.g);
+  if (st == LBM_OK && from_init) h->adj.init(ckp, lam[la].p, h->lay, h->p, dtau, h->stream);
+  // results
+  std::vector<double> dqh(std::max<int64_t>(nl, 1));
+  std::vector<double> dt(ndom, 0.0);
+  if (st == LBM_OK) {
+    e = cudaMemcpyAsync(dqh.data(), dq.p, sizeof(double) * nl, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dt.data(), dtau, sizeof(double) * ndom, cudaMemcpyDeviceToHost, h->stream);
+    // leave the moment cache consistent with the final state
+    h->ops.refresh(h->f[h->cur].p, h->lay, h->mom.p, h->p, h->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) st = fail(LBM_ERR_CUDA, "adjoint: %s", cudaGetErrorString(e));
+  }
+  if (st == LBM_OK) {
+    for (int64_t j = 0; j < nl; ++j) dJ_dq[h->link_order[j]] = dqh[j];
+    for (int k = 0; k < ndom; ++k) dJ_dtau[k] = dt[k];
+    if (seconds) {
+      seconds[0] = t_fwd;
+      seconds[1] = t_rec;
+      seconds[2] = t_adj;
+    }
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  cleanup();
+  return st;
+}
+
 lbm_status lbm_synchronize(lbm_handle h) {
   if (!h) return fail(LBM_ERR_INVALID_ARG, "null handle");
   CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -874,7 +1237,157 @@ lbm_status lbm_query(lbm_handle h, lbm_info* info) {
   info->real_bytes = (int32_t)h->rb;
   info->n_stored = h->lay.S;
   info->n_runs = h->n_runs;
+  info->n_bodies = h->nbody;
+  info->n_domains = std::max<int32_t>((int32_t)h->domains.size(), 1);
   return LBM_OK;
+}
+
+lbm_status lbm_set_tuning(lbm_handle h, const lbm_tuning* t) {
+  g_msg[0] = 0;
+  if (!h || !t) return fail(LBM_ERR_INVALID_ARG, "null argument");
+  lbm_tuning v = *t;
+  if (v.bulk_shape == -1) v.bulk_shape = h->ops.default_shape;
+  if (v.bulk_shape < 0 || v.bulk_shape >= kNumBulkShapes || kBulkShapes[v.bulk_shape].npt > h->ops.max_npt)
+    return fail(LBM_ERR_INVALID_ARG, "bulk_shape %d is not built for this stencil", t->bulk_shape);
+  if (v.link_threads != 64 && v.link_threads != 128 && v.link_threads != 256)
+    return fail(LBM_ERR_INVALID_ARG, "link_threads must be 64, 128 or 256");
+  if (v.graph_steps < 2 || v.graph_steps > 64 || (v.graph_steps & 1))
+    return fail(LBM_ERR_INVALID_ARG, "graph_steps must be even and in 2..64");
+  v.reserved = 0;
+  if (v.bulk_shape != h->tune.bulk_shape || v.link_threads != h->tune.link_threads ||
+      v.graph_steps != h->tune.graph_steps) {
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    drop_graphs(h);
+  }
+  h->tune = v;
+  return LBM_OK;
+}
+
+lbm_status lbm_get_tuning(lbm_handle h, lbm_tuning* t) {
+  g_msg[0] = 0;
+  if (!h || !t) return fail(LBM_ERR_INVALID_ARG, "null argument");
+  *t = h->tune;
+  return LBM_OK;
+}
+
+lbm_status lbm_autotune(lbm_handle h, int32_t steps_per_trial, lbm_tuning* best, double* ms_per_step) {
+  g_msg[0] = 0;
+  if (!h) return fail(LBM_ERR_INVALID_ARG, "null handle");
+  if (steps_per_trial < 2) return fail(LBM_ERR_INVALID_ARG, "steps_per_trial must be >= 2");
+  if (!h->has_state) return fail(LBM_ERR_STATE, "initialise the state first");
+  if (h->profiling) return fail(LBM_ERR_STATE, "switch profiling off first");
+  const size_t sb = (size_t)h->Q * h->lay.S * h->rb;
+  DeviceBuf save_f, save_m, save_force;
+  lbm_status st = acquire(save_f, sb);
+  if (st == LBM_OK) st = acquire(save_m, h->mom.bytes);
+  if (st == LBM_OK) st = acquire(save_force, h->force.bytes);
+  auto cleanup = [&]() {
+    release(save_f);
+    release(save_m);
+    release(save_force);
+  };
+  if (st != LBM_OK) {
+    cleanup();
+    return st;
+  }
+  const int cur0 = h->cur;
+  const int64_t step0 = h->step;
+  const bool from_init0 = h->from_init;
+  const lbm_tuning tune0 = h->tune;
+  auto copy = [&](void* dst, const void* src, size_t n) -> cudaError_t {
+    return n ? cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToDevice, h->stream) : cudaSuccess;
+  };
+  cudaError_t e = copy(save_f.p, h->f[cur0].p, sb);
+  if (e == cudaSuccess) e = copy(save_m.p, h->mom.p, h->mom.bytes);
+  if (e == cudaSuccess) e = copy(save_force.p, h->force.p, h->force.bytes);
+  if (e != cudaSuccess) {
+    cleanup();
+    return fail(LBM_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
+  }
+  // the trials start from the saved state at an even step count, so that
+  // the warm-up builds every graph the timed replays use
+  auto restore = [&](int64_t step) -> cudaError_t {
+    cudaError_t r = copy(h->f[cur0].p, save_f.p, sb);
+    if (r == cudaSuccess) r = copy(h->mom.p, save_m.p, h->mom.bytes);
+    if (r == cudaSuccess) r = copy(h->force.p, save_force.p, h->force.bytes);
+    h->cur = cur0;
+    h->step = step;
+    h->from_init = from_init0;
+    return r;
+  };
+  cudaEvent_t ev[2];
+  CUDA_TRY(cudaEventCreate(&ev[0]));
+  CUDA_TRY(cudaEventCreate(&ev[1]));
+  auto trial = [&](const lbm_tuning& t, double* ms) -> lbm_status {
+    lbm_status r = lbm_set_tuning(h, &t);
+    if (r != LBM_OK) return r;
+    double bestms = 1e300;
+    for (int rep = 0; rep < 2; ++rep) {
+      CUDA_TRY(restore(0));
+      r = lbm_step(h, t.graph_steps + 2);
+      if (r != LBM_OK) return r;
+      CUDA_TRY(cudaEventRecord(ev[0], h->stream));
+      r = lbm_step(h, steps_per_trial);
+      if (r != LBM_OK) return r;
+      CUDA_TRY(cudaEventRecord(ev[1], h->stream));
+      CUDA_TRY(cudaEventSynchronize(ev[1]));
+      float f_ms = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&f_ms, ev[0], ev[1]));
+      bestms = std::min(bestms, (double)f_ms / steps_per_trial);
+    }
+    *ms = bestms;
+    return LBM_OK;
+  };
+  lbm_tuning cand{h->ops.default_shape, 256, 8, 0}, chosen = cand;
+  double chosen_ms = 1e300;
+  auto consider = [&](const lbm_tuning& t) -> lbm_status {
+    double ms = 0.0;
+    const lbm_status r = trial(t, &ms);
+    if (r == LBM_OK && ms < chosen_ms) {
+      chosen_ms = ms;
+      chosen = t;
+    }
+    return r;
+  };
+  for (int sh = 0; sh < kNumBulkShapes && st == LBM_OK; ++sh) {
+    if (kBulkShapes[sh].npt > h->ops.max_npt) continue;
+    cand.bulk_shape = sh;
+    st = consider(cand);
+  }
+  const int link_opts[] = {64, 128};
+  for (int k = 0; k < 2 && st == LBM_OK; ++k) {
+    cand = chosen;
+    cand.link_threads = link_opts[k];
+    st = consider(cand);
+  }
+  const int graph_opts[] = {2, 32};
+  for (int k = 0; k < 2 && st == LBM_OK; ++k) {
+    cand = chosen;
+    cand.graph_steps = graph_opts[k];
+    st = consider(cand);
+  }
+  // put the state back and keep the fastest shapes
+  if (st == LBM_OK) {
+    e = restore(step0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) st = fail(LBM_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
+  } else {
+    char keep[sizeof g_msg];
+    memcpy(keep, g_msg, sizeof keep);
+    restore(step0);
+    cudaStreamSynchronize(h->stream);
+    memcpy(g_msg, keep, sizeof keep);
+  }
+  const lbm_status st2 = lbm_set_tuning(h, st == LBM_OK ? &chosen : &tune0);
+  if (st == LBM_OK) st = st2;
+  if (st == LBM_OK) {
+    if (best) *best = chosen;
+    if (ms_per_step) *ms_per_step = chosen_ms;
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  cleanup();
+  return st;
 }
 
 lbm_status lbm_set_profiling(lbm_handle h, int32_t on) {

@@ -338,6 +338,20 @@ def cylinder_channel(nx=2000, ny_fluid=400, center=(400.37, 200.61), radius=20.3
     return g
 
 
+def cylinders_channel(nx, ny_fluid, cylinders, u_max=0.1, bc=-1) -> Geometry:
+    """The channel of ``cylinder_channel`` holding several cylinders:
+    ``cylinders`` lists (c_x, c_y, R) in fluid-row coordinates; cylinder k
+    gets force id k.  Bodies: the two walls, then the cylinders in order."""
+    ny = ny_fluid + 2
+    bodies = [halfspace((0, -1, 0), -0.5, force_id=-1, bc=0),
+              halfspace((0, 1, 0), ny_fluid + 0.5, force_id=-1, bc=0)]
+    for k, (cx, cy, r) in enumerate(cylinders):
+        bodies.append(ball((cx, cy + 1.0, 0.0), r, force_id=k, bc=bc))
+    return build(D2Q9, (nx, ny, 1), (False, False, True), bodies, open_x=(True, True),
+                 info=dict(kind="cylinders", y_lo=0.5, y_hi=ny_fluid + 0.5, u_max=u_max,
+                           cylinders=[tuple(map(float, c)) for c in cylinders]))
+
+
 def couette(L, omega1, offset=(0.13, 0.27), bc=-1) -> Geometry:
     """Cylindrical Couette cell of Sec. 4.2: inner cylinder of radius L/4.8
     rotating at omega1 inside a fixed outer cylinder of radius L/2.4.  Only

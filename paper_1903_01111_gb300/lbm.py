@@ -29,7 +29,7 @@ LBM_BGK, LBM_MRT = 0, 1
 LBM_BC_DEFAULT, LBM_BC_HALFWAY, LBM_BC_BOUZIDI, LBM_BC_VIBB = -1, 0, 1, 2
 LBM_FP64, LBM_FP32_SHIFTED = 0, 1
 LBM_VIBB_RHO_PRINTED, LBM_VIBB_RHO_LOCAL = 0, 1
-LBM_MAX_BODIES = 64
+LBM_MAX_BODIES = 32768
 STATUS_NAMES = {0: "LBM_OK", 1: "LBM_ERR_INVALID_ARG", 2: "LBM_ERR_STATE", 3: "LBM_ERR_CUDA", 4: "LBM_ERR_OOM",
                 5: "LBM_ERR_DIVERGED", 6: "LBM_ERR_TIMEOUT", 7: "LBM_ERR_UNSUPPORTED"}
 
@@ -83,7 +83,41 @@ class lbm_info(ctypes.Structure):
         ("real_bytes", ctypes.c_int32),
         ("n_stored", ctypes.c_int64),
         ("n_runs", ctypes.c_int64),
+        ("n_bodies", ctypes.c_int32),
+        ("n_domains", ctypes.c_int32),
     ]
+
+
+class lbm_domain(ctypes.Structure):
+    _fields_ = [
+        ("lo", ctypes.c_int32),
+        ("n", ctypes.c_int32),
+        ("nx", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("tau", ctypes.c_double),
+        ("g", ctypes.c_double * 3),
+        ("inlet_umax", ctypes.c_double),
+        ("inlet_y0", ctypes.c_double),
+        ("inlet_y1", ctypes.c_double),
+    ]
+
+
+class lbm_tuning(ctypes.Structure):
+    _fields_ = [
+        ("bulk_shape", ctypes.c_int32),
+        ("link_threads", ctypes.c_int32),
+        ("graph_steps", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+    def as_dict(self):
+        return {"bulk_shape": self.bulk_shape, "bulk_threads": BULK_SHAPES[self.bulk_shape][0],
+                "bulk_nodes_per_thread": BULK_SHAPES[self.bulk_shape][1], "link_threads": self.link_threads,
+                "graph_steps": self.graph_steps}
+
+
+# (threads per block, nodes per thread) of bulk_shape 0..5
+BULK_SHAPES = ((256, 1), (128, 1), (512, 1), (256, 2), (128, 2), (512, 2))
 
 
 _H = ctypes.c_void_p
@@ -106,6 +140,13 @@ _sig = {
     "lbm_set_profiling": [_H, ctypes.c_int32],
     "lbm_kernel_times": [_H, _P(ctypes.c_int64), _P(ctypes.c_double)],
     "lbm_force_noalloc": [_P(lbm_config), _vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32, _vp],
+    "lbm_adjoint_step": [_H, ctypes.c_int32, _vp, ctypes.c_int64, ctypes.c_int64,
+                         _P(ctypes.c_double), _vp, _vp, _P(ctypes.c_double)],
+    "lbm_set_domains": [_H, _vp, ctypes.c_int32],
+    "lbm_forces": [_H, ctypes.c_int32, _vp],
+    "lbm_set_tuning": [_H, _P(lbm_tuning)],
+    "lbm_get_tuning": [_H, _P(lbm_tuning)],
+    "lbm_autotune": [_H, ctypes.c_int32, _P(lbm_tuning), _P(ctypes.c_double)],
 }
 for _name, _args in _sig.items():
     _fn = getattr(_lib, _name)
@@ -221,6 +262,74 @@ def lbm_gather(h, nodes) -> np.ndarray:
     return out
 
 
+def lbm_adjoint_step(h, body: int, dJ_dF, n_steps: int, checkpoint_every: int):
+    """Run n_steps forward with checkpoints and the adjoint sweep back.
+    body >= 0: dJ_dF has 3 entries; body = -1: dJ_dF is (n_bodies, 3).
+    Returns (J, dJ_dq (n_links, caller's link order), dJ_dtau, seconds[3]);
+    dJ_dtau is a float for a lattice of one domain, else an array per domain."""
+    info = lbm_query(h)
+    w = np.ascontiguousarray(dJ_dF, np.float64).reshape(-1)
+    need = 3 if body >= 0 else 3 * info.n_bodies
+    if w.size != need:
+        raise ValueError(f"dJ_dF needs {need} entries")
+    J = ctypes.c_double(0.0)
+    dtau = np.zeros(info.n_domains)
+    sec = (ctypes.c_double * 3)()
+    dq = np.zeros(max(info.n_links, 1))
+    _check(_lib.lbm_adjoint_step(h, int(body), w.ctypes.data, int(n_steps), int(checkpoint_every), ctypes.byref(J),
+                                 dq.ctypes.data, dtau.ctypes.data, sec))
+    return J.value, dq[: info.n_links], (float(dtau[0]) if info.n_domains == 1 else dtau), list(sec)
+
+
+def make_domains(rows):
+    """ctypes array of lbm_domain from dicts with keys lo, n, nx, tau and
+    optionally g, inlet_umax, inlet_y0, inlet_y1."""
+    arr = (lbm_domain * len(rows))()
+    for k, r in enumerate(rows):
+        d = arr[k]
+        d.lo, d.n, d.nx = int(r["lo"]), int(r["n"]), int(r["nx"])
+        d.tau = float(r["tau"])
+        g = r.get("g", (0.0, 0.0, 0.0))
+        for a in range(3):
+            d.g[a] = float(g[a]) if a < len(g) else 0.0
+        d.inlet_umax = float(r.get("inlet_umax", 0.0))
+        d.inlet_y0 = float(r.get("inlet_y0", 0.0))
+        d.inlet_y1 = float(r.get("inlet_y1", 0.0))
+    return arr
+
+
+def lbm_set_domains(h, rows) -> None:
+    arr = make_domains(rows)
+    _check(_lib.lbm_set_domains(h, arr if len(rows) else None, len(rows)))
+
+
+def lbm_forces(h, n: int) -> np.ndarray:
+    """Forces (n, 3) on bodies 0..n-1 of the last step."""
+    out = np.zeros((max(n, 1), 3))
+    _check(_lib.lbm_forces(h, int(n), out.ctypes.data))
+    return out[:n]
+
+
+def lbm_set_tuning(h, bulk_shape=-1, link_threads=256, graph_steps=2) -> None:
+    t = lbm_tuning(int(bulk_shape), int(link_threads), int(graph_steps), 0)
+    _check(_lib.lbm_set_tuning(h, ctypes.byref(t)))
+
+
+def lbm_get_tuning(h) -> lbm_tuning:
+    t = lbm_tuning()
+    _check(_lib.lbm_get_tuning(h, ctypes.byref(t)))
+    return t
+
+
+def lbm_autotune(h, steps_per_trial: int = 20):
+    """Time the launch shapes on the current state (restored afterwards);
+    returns (lbm_tuning chosen, ms per step)."""
+    t = lbm_tuning()
+    ms = ctypes.c_double(0.0)
+    _check(_lib.lbm_autotune(h, int(steps_per_trial), ctypes.byref(t), ctypes.byref(ms)))
+    return t, ms.value
+
+
 def lbm_check(h) -> None:
     _check(_lib.lbm_check(h))
 
@@ -261,7 +370,7 @@ KERNEL_NAMES = ("k_links", "k_open", "k_bulk")
 class Lattice:
     """Owner of one lattice handle; mirrors the C entry points."""
 
-    def __init__(self, geometry=None, **cfg):
+    def __init__(self, geometry=None, domains=None, **cfg):
         if geometry is not None:
             cfg.setdefault("stencil", geometry.stencil)
             cfg.setdefault("nx", geometry.nx)
@@ -272,6 +381,8 @@ class Lattice:
             cfg.setdefault("outlet", int(geometry.open_x[1]))
         self.cfg = make_config(**cfg)
         self.h = lbm_create_lattice(self.cfg)
+        if domains is not None:
+            lbm_set_domains(self.h, domains)
         if geometry is not None:
             self.set_geometry(geometry.solid, geometry.links)
 
@@ -312,6 +423,18 @@ class Lattice:
     def force(self, body=0):
         return lbm_force(self.h, body)
 
+    def forces(self, n=None):
+        return lbm_forces(self.h, self.info().n_bodies if n is None else n)
+
+    def autotune(self, steps_per_trial=20):
+        return lbm_autotune(self.h, steps_per_trial)
+
+    def set_tuning(self, **kw):
+        lbm_set_tuning(self.h, **kw)
+
+    def tuning(self):
+        return lbm_get_tuning(self.h)
+
     def distributions(self):
         return lbm_get_distributions(self.h)
 
@@ -326,3 +449,13 @@ class Lattice:
 
     def info(self):
         return lbm_query(self.h)
+
+
+def batch_lattice(batch, **cfg) -> Lattice:
+    """Lattice over a stacked batch (``batch.Batch``): its domain table and
+    geometry.  cfg's tau and inlet profile are placeholders (each domain has
+    its own)."""
+    cfg.setdefault("tau", 1.0)
+    cfg.setdefault("inlet_y0", 0.0)
+    cfg.setdefault("inlet_y1", 1.0)
+    return Lattice(batch.geometry, domains=batch.domains, **cfg)

@@ -1,0 +1,223 @@
+"""Batches (lbm_set_domains): several channel flows of different sizes,
+cylinder layouts and relaxation times stacked in one lattice.
+
+* FP64 batch against the FP64 oracle run on each domain alone (1e-11 after
+  150 steps), and the FP32-shifted batch within the FP32 bound of the parity
+  tests;
+* the batch against each domain run as its own GPU lattice: the same bits
+  (the kernels do the same arithmetic; only the domain table differs);
+* forces per body and the batched adjoint (J = sum over bodies of w_b . F_b,
+  dJ/dtau per domain) against single-domain runs;
+* launch shapes (lbm_set_tuning) change no bits, and lbm_autotune leaves the
+  state as it found it.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1903_01111_gb300 import batch as B
+from paper_1903_01111_gb300 import geometry as G
+
+pytestmark = pytest.mark.gpu
+
+EPS32 = float(np.finfo(np.float32).eps)
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1903_01111_gb300 import lbm
+
+    return lbm
+
+
+def _small_specs(n=5, seed=3):
+    return B.draw_channels(n, seed, nx_range=(28, 61), ny_range=(10, 23), n_cyl=(1, 3), r_range=(2.2, 4.6),
+                           re_range=(5.0, 40.0), u_max=0.05, gap=2.0)
+
+
+def _batch_lattice(L, b, precision, bc=2, **kw):
+    lat = L.batch_lattice(b, precision=precision, bc=bc, **kw)
+    lat.init_equilibrium(u=b.initial_velocity())
+    return lat
+
+
+def _single_cfg(s, geo, bc=2):
+    return dict(stencil=0, nx=geo.nx, ny=geo.ny, nz=1, periodic=geo.periodic, inlet=1, outlet=1, tau=s.tau, bc=bc,
+                **s.inlet())
+
+
+def _fluid_mask(geo):
+    m = (geo.solid == 0).reshape(geo.ny, geo.nx).copy()
+    m[:, 0] = False
+    m[:, -1] = False
+    return m.reshape(-1)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32s"])
+def test_batch_matches_oracle_per_domain(L, prec):
+    specs = _small_specs()
+    b = B.stack(specs)
+    steps = 150
+    precision = L.LBM_FP64 if prec == "fp64" else L.LBM_FP32_SHIFTED
+    lat = _batch_lattice(L, b, precision)
+    lat.step(steps)
+    f = lat.distributions()
+    F = lat.forces()
+    lat.close()
+    _, w = O.velocity_set(0)
+    for d, (s, geo) in enumerate(zip(specs, b.parts)):
+        cfg = O.make_config(**_single_cfg(s, geo))
+        u0 = s.initial_velocity(geo)
+        st = O.init(cfg, geo.solid, u=u0)
+        Fo = O.run(cfg, geo.solid, geo.links, st, steps, nbody=len(s.cylinders))
+        fl = _fluid_mask(geo)
+        fd = f[:, b.domain_nodes(d)]
+        if precision == L.LBM_FP64:
+            tol = 1e-11
+        else:
+            tol = 4 * steps * EPS32 * max(np.abs(st.fp[:, fl] - w[:, None]).max(), 1e-6)
+        err = np.abs(fd[:, fl] - st.fp[:, fl]).max()
+        assert err <= tol, (d, err, tol)
+        Fd = F[b.body0[d]:b.body0[d] + len(s.cylinders)]
+        scale = np.abs(Fo).max()
+        ftol = 1e-10 * scale if precision == L.LBM_FP64 else 1e-4 * scale + len(geo.links) * tol
+        assert np.abs(Fd - Fo[:len(s.cylinders)]).max() <= ftol, (d, Fd, Fo)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32s"])
+def test_batch_equals_domains_run_alone(L, prec):
+    specs = _small_specs(4, seed=11)
+    b = B.stack(specs)
+    precision = L.LBM_FP64 if prec == "fp64" else L.LBM_FP32_SHIFTED
+    lat = _batch_lattice(L, b, precision)
+    lat.step(101)
+    f = lat.distributions()
+    F = lat.forces()
+    lat.close()
+    for d, (s, geo) in enumerate(zip(specs, b.parts)):
+        with L.Lattice(geo, precision=precision, bc=2, tau=s.tau, **s.inlet()) as one:
+            one.init_equilibrium(u=s.initial_velocity(geo))
+            one.step(101)
+            f1 = one.distributions()
+            F1 = one.forces(len(s.cylinders))
+        assert np.array_equal(f[:, b.domain_nodes(d)], f1), d
+        Fd = F[b.body0[d]:b.body0[d] + len(s.cylinders)]
+        # force sums run in another order (FP32 lane sums in shifted storage)
+        rtol = 1e-12 if precision == L.LBM_FP64 else 1e-5
+        assert np.allclose(Fd, F1, rtol=rtol, atol=rtol * 1e-3 * np.abs(F1).max()), (d, Fd, F1)
+
+
+def test_batch_adjoint_equals_domains_alone(L):
+    specs = _small_specs(3, seed=5)
+    b = B.stack(specs)
+    rng = np.random.default_rng(0)
+    wts = rng.normal(size=(b.n_bodies, 3))
+    wts[:, 2] = 0.0
+    lat = _batch_lattice(L, b, L.LBM_FP64)
+    J, dq, dtau, _ = L.lbm_adjoint_step(lat.h, -1, wts, 60, 25)
+    lat.close()
+    assert dtau.shape == (3,)
+    Jsum = 0.0
+    for d, (s, geo) in enumerate(zip(specs, b.parts)):
+        wd = wts[b.body0[d]:b.body0[d] + len(s.cylinders)]
+        with L.Lattice(geo, precision=L.LBM_FP64, bc=2, tau=s.tau, **s.inlet()) as one:
+            one.init_equilibrium(u=s.initial_velocity(geo))
+            Jd, dqd, dtd, _ = L.lbm_adjoint_step(one.h, -1, wd, 60, 25)
+        Jsum += Jd
+        dqb = dq[b.domain_links(d)]
+        assert np.allclose(dqb, dqd, rtol=1e-9, atol=1e-12 * np.abs(dqd).max()), d
+        assert abs(dtau[d] - dtd) <= 1e-9 * abs(dtd), (d, dtau[d], dtd)
+    assert abs(J - Jsum) <= 1e-12 * abs(Jsum) + 1e-15
+
+
+def _shapes(L, stencil):
+    return [k for k, (_, npt) in enumerate(L.BULK_SHAPES) if npt == 1 or stencil == 0]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32s"])
+@pytest.mark.parametrize("stencil", [0, 1])
+def test_launch_shapes(L, prec, stencil):
+    """Block sizes, link block sizes and graph lengths change no bits; one
+    and two nodes per thread are separate compilations of the same
+    arithmetic and agree to rounding (the parity bound of 37 steps)."""
+    precision = L.LBM_FP64 if prec == "fp64" else L.LBM_FP32_SHIFTED
+    if stencil == 0:
+        geo = G.build(0, (83, 41, 1), (1, 1, 1), [G.ball((30.37, 20.61, 0), 7.3, force_id=0)])
+    else:
+        geo = G.sphere_pack(24, porosity=0.5, rmin=2.5, rmax=4.5, seed=3)
+    ref = {}
+    for shape in _shapes(L, stencil):
+        npt = L.BULK_SHAPES[shape][1]
+        for lt, gs in ((256, 2), (64, 8), (128, 32)):
+            with L.Lattice(geo, precision=precision, bc=2, tau=0.7, g=(1e-5, 0, 0)) as lat:
+                lat.set_tuning(bulk_shape=shape, link_threads=lt, graph_steps=gs)
+                lat.init_equilibrium()
+                lat.step(37)
+                f = lat.distributions()
+            ref.setdefault(npt, f)
+            assert np.array_equal(f, ref[npt]), (shape, lt, gs)
+    if len(ref) == 2:
+        _, w = O.velocity_set(stencil)
+        h = np.abs(ref[1] - (w[:, None] if precision == L.LBM_FP32_SHIFTED else 0.0)).max()
+        tol = 1e-12 if precision == L.LBM_FP64 else 4 * 37 * EPS32 * h
+        assert np.abs(ref[1] - ref[2]).max() <= tol
+
+
+def test_autotune_restores_state_and_picks_a_valid_shape(L):
+    specs = _small_specs(6, seed=2)
+    b = B.stack(specs)
+    lat = _batch_lattice(L, b, L.LBM_FP32_SHIFTED)
+    lat.step(9)
+    F0 = lat.forces()
+    f0 = lat.distributions()
+    t, ms = lat.autotune(10)
+    assert ms > 0 and 0 <= t.bulk_shape < 6 and t.link_threads in (64, 128, 256) and t.graph_steps % 2 == 0
+    assert lat.tuning().bulk_shape == t.bulk_shape
+    assert lat.info().step == 9
+    assert np.array_equal(lat.distributions(), f0)
+    assert np.array_equal(lat.forces(), F0)
+    lat.step(20)
+    f1 = lat.distributions()
+    lat.close()
+    lat2 = _batch_lattice(L, b, L.LBM_FP32_SHIFTED)
+    lat2.set_tuning(bulk_shape=t.bulk_shape, link_threads=256, graph_steps=2)
+    lat2.step(29)
+    assert np.array_equal(lat2.distributions(), f1)
+    lat2.close()
+
+
+def test_set_domains_rejects_bad_tables(L):
+    specs = _small_specs(2, seed=1)
+    b = B.stack(specs)
+    geo = b.geometry
+    base = dict(stencil=0, nx=geo.nx, ny=geo.ny, nz=1, periodic=geo.periodic, inlet=1, outlet=1, tau=0.8,
+                inlet_y0=0.0, inlet_y1=1.0)
+    bad = [dict(b.domains[0], lo=1), dict(b.domains[0], n=2), dict(b.domains[0], nx=geo.nx + 1),
+           dict(b.domains[0], tau=0.5)]
+    for row in bad:
+        h = L.lbm_create_lattice(L.make_config(**base))
+        with pytest.raises(L.LBMError) as e:
+            L.lbm_set_domains(h, [row, b.domains[1]])
+        assert e.value.status == L.LBM_ERR_INVALID_ARG
+        L.lbm_destroy(h)
+    # rows do not cover the lattice
+    h = L.lbm_create_lattice(L.make_config(**base))
+    with pytest.raises(L.LBMError):
+        L.lbm_set_domains(h, b.domains[:1])
+    # a fluid node in a domain's boundary row
+    L.lbm_set_domains(h, b.domains)
+    solid = geo.solid.copy()
+    solid[geo.nx * (b.domains[1]["lo"]) + 5] = 0
+    with pytest.raises(L.LBMError) as e:
+        L.lbm_set_geometry(h, solid, geo.links)
+    assert e.value.status == L.LBM_ERR_INVALID_ARG
+    # domains after the geometry
+    L.lbm_set_geometry(h, geo.solid, geo.links)
+    with pytest.raises(L.LBMError) as e:
+        L.lbm_set_domains(h, b.domains)
+    assert e.value.status == L.LBM_ERR_STATE
+    L.lbm_destroy(h)

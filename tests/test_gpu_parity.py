@@ -388,3 +388,28 @@ def test_mrt_open_channel_cylinder(L, prec):
     u0[:, 0] = np.where(geo.solid == 0, 4 * 0.05 * (y - 0.5) * (30.5 - y) / 30 ** 2, 0.0)
     _compare(L, geo, 200, _p(L, prec), nbody=1, init_u=u0, tau=0.56, bc=2, collision=1, inlet_umax=0.05,
              inlet_y0=0.5, inlet_y1=30.5)
+
+
+@pytest.mark.parametrize("bc", [0, 1, 2])
+def test_poiseuille_l2_error_fp32_no_worse_than_fp64(L, bc):
+    """Analytic case: L2 error of the velocity against the parabolic profile
+    of body-force-driven Poiseuille flow (Sec. 4.1) after 12000 steps (about
+    two diffusion times), walls at q = 0.3.  The FP32-shifted run's error is
+    the FP64 run's to within 1e-3 of itself."""
+    geo = G.channel(0, 32, 24, q_lo=0.3, q_hi=0.3)
+    tau, g = 0.8, 1e-6
+    nu = (tau - 0.5) / 3
+    y = np.arange(geo.ny)
+    exact = G.poiseuille_profile(y, geo.info["y_lo"], geo.info["y_hi"], g, nu)
+    rows = slice(1, geo.ny - 1)
+    errs = {}
+    for prec in (L.LBM_FP64, L.LBM_FP32_SHIFTED):
+        with L.Lattice(geo, precision=prec, tau=tau, g=(g, 0, 0), bc=bc) as lat:
+            lat.init_equilibrium()
+            lat.step(12000)
+            _, u = lat.moments()
+        ux = u[0].reshape(geo.ny, geo.nx)[rows].mean(axis=1)
+        errs[prec] = np.sqrt(np.sum((ux - exact[rows]) ** 2) / np.sum(exact[rows] ** 2))
+    assert errs[L.LBM_FP32_SHIFTED] <= errs[L.LBM_FP64] * (1 + 1e-3), errs
+    if bc != 0:
+        assert errs[L.LBM_FP64] < 2e-3, errs
