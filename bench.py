@@ -149,6 +149,7 @@ def run_precision(lbm, torch, geo, precision, steps, warmup, dist, peak):
                       stream=stream.cuda_stream, vibb_density=lbm.LBM_VIBB_RHO_LOCAL)
     info = lat.info()
     lat.init_equilibrium()
+    tuning, _ = lat.autotune(10)
     lat.step(warmup)
     _barrier(dist, torch)
     lbm.lbm_set_profiling(lat.h, True)
@@ -178,9 +179,13 @@ def run_precision(lbm, torch, geo, precision, steps, warmup, dist, peak):
     link_gbs = link_bytes / (link_ms * 1e-3) / 1e9
     return {
         "mlups": mlups, "ms_per_step": ms / steps, "n_fluid": nf, "n_links": nl, "n_nodes": N,
+        "tuning": tuning.as_dict(),
         "launches": int(sum(n_launch)), "force": F.tolist(),
         "roofline": dict(roofline_entry(bulk_bytes, nf * FLOPS_PER_NODE[Q3], bulk_ms, s, peak), kernel="k_bulk",
-                         bytes_per_launch=bulk_bytes, avg_launch_ms=bulk_ms),
+                         bytes_per_launch=bulk_bytes, avg_launch_ms=bulk_ms,
+                         traffic=(TRAFFIC_PER_FLUID_NODE_PACK_FP32 * nf if s == 4 else None),
+                         traffic_source=("ncu dram__bytes_read+write on a 192^3 pack, per fluid node, scaled"
+                                         if s == 4 else None)),
         "kernels": {
             "k_bulk": {"launches": n_launch[2], "avg_ms": bulk_ms, "share": kms[2] / max(sum(kms), 1e-30),
                        "gbs": bulk_gbs, "bytes_per_launch": bulk_bytes},
@@ -191,13 +196,22 @@ def run_precision(lbm, torch, geo, precision, steps, warmup, dist, peak):
     }
 
 
+# DRAM bytes (read + write) per fluid node of k_bulk<D3Q19, F32S> on the
+# sphere-pack recipe, from an ncu capture of a 192^3 pack of the same recipe
+# (593 MB per launch for 2.83M fluid nodes); traffic grows with the fluid
+# node count, so a full launch moves this figure times its fluid nodes.
+TRAFFIC_PER_FLUID_NODE_PACK_FP32 = 209.7
+
+
 # FP64 arithmetic peak of GB300, from unit counts and clock: 152 SMs x 2 FP64
 # FMA per clock per SM x 2 flops x 2.07 GHz = 1.26 TFLOP/s (nominal 1.25).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# Algorithmic FP64 flops of one BGK + Guo node update (FMA = 2): moments
-# (Q-1 adds for rho, 3 x (Q_nonzero - 1) for j, 7 for u), 11 for |u|^2 and
-# u.g, and per direction 16 (e.u, polynomial, equilibrium, relaxation, Guo).
-FLOPS_PER_NODE = {9: 8 + 3 * 5 + 7 + 11 + 9 * 16, 19: 18 + 3 * 9 + 7 + 11 + 19 * 16}
+# Algorithmic FP64 flops of one BGK + Guo node update (FMA = 2) in the form
+# the kernel evaluates, per pair of opposite directions (e.u, 4.5 (e.u)^2 -
+# 1.5 u.u, A, B, omega A and omega B, the two source terms, two outputs: 20
+# plus the adds of e.u) and once per node (moments, velocity, u.u, u.g, the
+# rest direction, weight products): D2Q9 4 pairs -> 125, D3Q19 9 pairs -> 263.
+FLOPS_PER_NODE = {9: 125, 19: 263}
 
 
 def roofline_entry(bytes_per_launch, flops_per_launch, avg_ms, s, peak_gbs):
@@ -211,19 +225,22 @@ def roofline_entry(bytes_per_launch, flops_per_launch, avg_ms, s, peak_gbs):
             "traffic": None}
 
 
-def run_sweep(lbm, torch, steps, peak):
-    """No-solid periodic lattices: D2Q9 16384 x 8192 and D3Q19 384^3, FP32
-    shifted and FP64; the bulk kernel's roofline on each."""
+def run_sweep(lbm, torch, steps, peak, scale=1):
+    """No-solid periodic lattices: D2Q9 16384 x 8192 and D3Q19 384^3 (each
+    side divided by `scale`), FP32 shifted and FP64; the bulk kernel's
+    roofline on each."""
     from paper_1903_01111_gb300 import geometry as G
 
     out = {}
-    for name, stencil, shape in (("d2q9_16384x8192", 0, (16384, 8192, 1)), ("d3q19_384^3", 1, (384, 384, 384))):
+    for name, stencil, shape in ((f"d2q9_{16384 // scale}x{8192 // scale}", 0, (16384 // scale, 8192 // scale, 1)),
+                                 (f"d3q19_{384 // scale}^3", 1, (384 // scale,) * 3)):
         geo = G.build(stencil, shape, (1, 1, 1), [])
         Q = 9 if stencil == 0 else 19
         for prec, s in ((lbm.LBM_FP32_SHIFTED, 4), (lbm.LBM_FP64, 8)):
             stream = torch.cuda.Stream()
             lat = lbm.Lattice(geo, precision=prec, tau=0.7, g=(1e-6, 0.0, 0.0), bc=0, stream=stream.cuda_stream)
             lat.init_equilibrium()
+            tuning, _ = lat.autotune(10)
             n = steps if s == 4 else max(10, steps // 5)
             lat.step(3)
             torch.cuda.synchronize()
@@ -243,7 +260,7 @@ def run_sweep(lbm, torch, steps, peak):
             r = roofline_entry(nf * (2 * Q * s + 1), nf * FLOPS_PER_NODE[Q], bulk_ms, s, peak)
             out[f"{name}_{'fp32s' if s == 4 else 'fp64'}"] = {
                 "mlups": nf * n / (ms * 1e-3) / 1e6, "ms_per_step": ms / n, "steps": n,
-                "bytes_per_node": 2 * Q * s + 1, "bulk_avg_ms": bulk_ms, "roofline": r}
+                "bytes_per_node": 2 * Q * s + 1, "bulk_avg_ms": bulk_ms, "roofline": r, "tuning": tuning.as_dict()}
     return out
 
 
@@ -327,7 +344,12 @@ def run_batch(lbm, torch, peak, n_domains=256, seed=0, steps=2000, warmup=10, ad
     torch.cuda.synchronize()
     ms32 = e0.elapsed_time(e1)
     F32 = lat.forces()
-    lat.check()
+    diverged = []
+    try:
+        lat.check()
+    except lbm.LBMError:
+        bad = ~np.isfinite(F32).all(axis=1)
+        diverged = sorted({int(np.searchsorted(b.body0, k, side="right") - 1) for k in np.flatnonzero(bad)})
     # kernel times of a few more steps (direct launches between events)
     lbm.lbm_set_profiling(lat.h, True)
     lat.step(50)
@@ -359,6 +381,7 @@ def run_batch(lbm, torch, peak, n_domains=256, seed=0, steps=2000, warmup=10, ad
         one.close()
     mlups64 = nf * (steps - warmup) / s64 / 1e6
     rel = np.abs(F32[:, 0] - F64[:, 0]) / np.abs(F64[:, 0])
+    rel = rel[np.isfinite(rel)]
     # batched adjoint of the summed drag
     lat = lbm.batch_lattice(b, precision=lbm.LBM_FP32_SHIFTED, bc=lbm.LBM_BC_VIBB, stream=stream.cuda_stream)
     lat.set_tuning(bulk_shape=tuning.bulk_shape, link_threads=tuning.link_threads, graph_steps=tuning.graph_steps)
@@ -372,7 +395,7 @@ def run_batch(lbm, torch, peak, n_domains=256, seed=0, steps=2000, warmup=10, ad
                     "r U[4,20], Re U[10,100] on the channel height, u_max 0.1; stacked in one lattice",
         "lattice": [b.geometry.nx, b.geometry.ny], "fluid_nodes": nf, "links": int(info.n_links),
         "bodies": int(b.n_bodies), "stored_nodes": int(info.n_stored), "build_s": t_build,
-        "tuning": tuning.as_dict(), "autotune_best_ms_per_step": tune_ms,
+        "tuning": tuning.as_dict(), "autotune_best_ms_per_step": tune_ms, "diverged_domains": diverged,
         "fp32_batched": {"value": mlups32, "unit": "MLUPS", "ms_per_step": ms32 / (steps - warmup),
                          "steps_timed": steps - warmup,
                          "roofline": dict(roofline_entry(bulk_bytes, nf * FLOPS_PER_NODE[9], bulk_ms, s, peak),
@@ -488,11 +511,33 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--sweep-steps", type=int, default=100)
+    ap.add_argument("--part", default="all", choices=["all", "batch", "adjoint", "sweep"],
+                    help="run one section alone (for profiling) and print its JSON")
+    ap.add_argument("--batch-domains", type=int, default=256)
+    ap.add_argument("--batch-steps", type=int, default=2000)
+    ap.add_argument("--adjoint-steps", type=int, default=20000)
+    ap.add_argument("--sweep-scale", type=int, default=1, help="divide the sweep lattices' sides by this")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return reference_arm(args)
+    if args.part != "all":
+        import torch
+
+        from paper_1903_01111_gb300 import lbm
+
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        if args.part == "sweep":
+            out = run_sweep(lbm, torch, args.sweep_steps, _peaks()[0], scale=args.sweep_scale)
+        elif args.part == "batch":
+            out = run_batch(lbm, torch, _peaks()[0], n_domains=args.batch_domains, steps=args.batch_steps,
+                            warmup=args.warmup, adjoint_steps=min(64, args.batch_steps), K=8)
+        else:
+            out = run_adjoint(lbm, n_steps=args.adjoint_steps, checkpoint_every=max(2, int(args.adjoint_steps ** 0.5)),
+                              fd=False)
+        print(json.dumps(out), flush=True)
+        return 0
 
     import torch
 
@@ -537,7 +582,7 @@ def main():
                    "geometry_build_s": t_geo},
         "roofline": dict(r32["roofline"], peak_source=peak_src),
         "hbm_peak_source": peak_src,
-        "kernels": r32["kernels"], "step_gbs": r32["step_gbs"],
+        "kernels": r32["kernels"], "step_gbs": r32["step_gbs"], "tuning": r32["tuning"],
         "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": r32["launches"],
         "clocks": ck,

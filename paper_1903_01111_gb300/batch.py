@@ -61,36 +61,56 @@ class DomainSpec:
 
 
 def draw_channels(n_domains=256, seed=0, nx_range=(64, 512), ny_range=(64, 256), n_cyl=(1, 8), r_range=(4.0, 20.0),
-                  re_range=(10.0, 100.0), u_max=0.1, gap=3.0, max_tries=400) -> list:
+                  re_range=(10.0, 100.0), u_max=0.1, gap=3.0, max_blockage=0.4, max_tries=400) -> list:
     """Seeded channel workload: sizes uniform in nx_range x ny_range (fluid
     rows), 1..8 non-overlapping cylinders per channel with radii uniform in
-    r_range (capped to fit the channel) and off-grid centres at least ``gap``
+    r_range (capped at ny/6 and nx/4) and off-grid centres at least ``gap``
     apart and from the walls, kept clear of the inlet and outlet, Re uniform
-    in re_range."""
+    in re_range.  The cylinders whose x-extents overlap block at most
+    ``max_blockage`` of the channel height (the flow through the remaining
+    gaps speeds up by 1/(1 - blockage); a nearly closed channel would push
+    the lattice Mach number past what BGK tolerates)."""
     rng = np.random.default_rng(seed)
     out = []
     for _ in range(n_domains):
         nx = int(rng.integers(nx_range[0], nx_range[1] + 1))
         ny = int(rng.integers(ny_range[0], ny_range[1] + 1))
         want = int(rng.integers(n_cyl[0], n_cyl[1] + 1))
-        rmax = min(r_range[1], ny / 2.0 - gap - 1.0, nx / 4.0)
+        rmax = min(r_range[1], ny / 6.0, nx / 4.0)
         cyl = []
         tries = 0
         while len(cyl) < want and tries < max_tries:
             tries += 1
-            r = float(rng.uniform(r_range[0], max(r_range[0], rmax)))
-            r = min(r, rmax)
+            r = min(float(rng.uniform(r_range[0], max(r_range[0], rmax))), rmax)
             x_lo, x_hi = r + 8.0, nx - r - 16.0
             y_lo, y_hi = r + gap, ny - 1 - r - gap
             if x_hi <= x_lo or y_hi <= y_lo:
                 continue
             c = (float(rng.uniform(x_lo, x_hi)), float(rng.uniform(y_lo, y_hi)))
-            if all((c[0] - a) ** 2 + (c[1] - b) ** 2 >= (r + rr + gap) ** 2 for a, b, rr in cyl):
-                cyl.append((c[0], c[1], r))
+            if any((c[0] - a) ** 2 + (c[1] - b) ** 2 < (r + rr + gap) ** 2 for a, b, rr in cyl):
+                continue
+            if _max_chord(cyl + [(c[0], c[1], r)]) > max_blockage * ny:
+                continue
+            cyl.append((c[0], c[1], r))
         if not cyl:
             raise RuntimeError("could not place a cylinder")
         out.append(DomainSpec(nx, ny, cyl, float(rng.uniform(*re_range)), u_max))
     return out
+
+
+def _max_chord(cylinders) -> float:
+    """Largest total height that the cylinders cover on one vertical line."""
+    xs = np.concatenate([np.linspace(a - r, a + r, 65) for a, _, r in cylinders])
+    h = np.zeros_like(xs)
+    for a, _, r in cylinders:
+        h += 2.0 * np.sqrt(np.clip(r * r - (xs - a) ** 2, 0.0, None))
+    return float(h.max())
+
+
+def blockage(spec: DomainSpec) -> float:
+    """Largest fraction of the channel height that the cylinders cover on
+    one vertical line."""
+    return _max_chord(spec.cylinders) / spec.ny_fluid
 
 
 @dataclass

@@ -39,7 +39,7 @@ __device__ __forceinline__ void atomic_add_real(T* p, T v) {
 // form); lam: lambda(s+1) of this node; mu: output.  Returns the node's
 // sum_i lam_i dC_i/dtau.
 template <class L, class P>
-__device__ __forceinline__ double collide_adjoint(const typename P::T (&f)[L::Q], const typename P::T (&lam)[L::Q],
+__device__ __forceinline__ typename P::T collide_adjoint(const typename P::T (&f)[L::Q], const typename P::T (&lam)[L::Q],
                                                   typename P::T (&mu)[L::Q], const Params& p, const Relax& rx) {
   using T = typename P::T;
   T r = 0, jx = 0, jy = 0, jz = 0;
@@ -56,8 +56,7 @@ __device__ __forceinline__ double collide_adjoint(const typename P::T (&f)[L::Q]
   const T omega = (T)rx.omega;
   const T uu15 = (T)1.5 * (ux * ux + uy * uy + uz * uz);
   const T ug = ux * gx + uy * gy + uz * gz;
-  T A = 0, B0 = 0, B1 = 0, B2 = 0;
-  double dtau = 0.0;
+  T A = 0, B0 = 0, B1 = 0, B2 = 0, dtau = 0;
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
     const T ex = (T)L::cx(i), ey = (T)L::cy(i), ez = (T)L::cz(i);
@@ -74,7 +73,7 @@ __device__ __forceinline__ double collide_adjoint(const typename P::T (&f)[L::Q]
     B1 += lam[i] * (c1 * ((T)3 * ey + (T)9 * eu * ey - (T)3 * uy) + c2 * ((T)-3 * gy + (T)9 * ey * eg));
     B2 += lam[i] * (c1 * ((T)3 * ez + (T)9 * eu * ez - (T)3 * uz) + c2 * ((T)-3 * gz + (T)9 * ez * eg));
     // dC_i/dtau = (f_i - feq_i + src_i / 2) / tau^2
-    dtau += (double)lam[i] * (double)(f[i] - feq + (T)0.5 * src);
+    dtau += lam[i] * (f[i] - feq + (T)0.5 * src);
   }
   const T ir = (T)1 / rho;
 #pragma unroll
@@ -82,29 +81,33 @@ __device__ __forceinline__ double collide_adjoint(const typename P::T (&f)[L::Q]
     const T ex = (T)L::cx(j), ey = (T)L::cy(j), ez = (T)L::cz(j);
     mu[j] = ((T)1 - omega) * lam[j] + omega * A + (B0 * (ex - ux) + B1 * (ey - uy) + B2 * (ez - uz)) * ir;
   }
-  return dtau * (rx.omega * rx.omega);
+  return dtau * (T)(rx.omega * rx.omega);
 }
 
-// Adds v to target[key] over the block (key < 0: nothing to add): one atomic
-// when every contributing thread has the same key, else one per thread.
-__device__ __forceinline__ void block_add_keyed(double v, int key, double* target) {
+// Adds v to target[key] over the block (key < 0: nothing to add): when
+// every contributing thread has the same key, warp sums in the value's own
+// precision, the block sum and one atomic in FP64; else one FP64 atomic per
+// thread.
+template <class T>
+__device__ __forceinline__ void block_add_keyed(T v, int key, double* target) {
   __shared__ double red[32];
   __shared__ int kref;
   if (threadIdx.x == 0) kref = -1;
   __syncthreads();
-  if (key >= 0) atomicMax(&kref, key);
+  const int wmax = __reduce_max_sync(0xffffffffu, key);
+  if ((threadIdx.x & 31) == 0 && wmax >= 0) atomicMax(&kref, wmax);
   __syncthreads();
   const int k0 = kref;
   if (!__syncthreads_and(key < 0 || key == k0)) {
-    if (key >= 0 && v != 0.0) atomicAdd(target + key, v);
+    if (key >= 0 && v != (T)0) atomicAdd(target + key, (double)v);
     return;
   }
   if (k0 < 0) return;
-  if (key < 0) v = 0.0;
+  if (key < 0) v = (T)0;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) red[warp] = v;
+  if (lane == 0) red[warp] = (double)v;
   __syncthreads();
   if (threadIdx.x == 0) {
     double acc = 0.0;
@@ -121,7 +124,7 @@ __global__ void __launch_bounds__(256) k_adj_bulk(const typename P::T* __restric
   using T = typename P::T;
   const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   const size_t S = (size_t)lay.S;
-  double dt = 0.0;
+  T dt = 0;
   int key = -1;
   if (k < (uint64_t)lay.S) {
     const uint32_t w = lay.word[k];
@@ -136,7 +139,6 @@ __global__ void __launch_bounds__(256) k_adj_bulk(const typename P::T* __restric
       for (int i = 0; i < L::Q; ++i) {
         f[i] = fin[(size_t)i * S + src[i]];
         lam[i] = lam_next[(size_t)i * S + k];
-        lam_next[(size_t)i * S + k] = (T)0;
       }
       if (w & W_CACHE) {
         // moments of f+(s) at this node (the k_refresh formula)
@@ -156,9 +158,13 @@ __global__ void __launch_bounds__(256) k_adj_bulk(const typename P::T* __restric
       dt = collide_adjoint<L, P>(f, lam, mu, p, rx);
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) lam_out[(size_t)i * S + src[i]] = mu[i];
+      // consumed: clear after the compute (a store right behind the load of
+      // the same address would hold up the warp's following loads)
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) lam_next[(size_t)i * S + k] = (T)0;
     }
   }
-  block_add_keyed(dt, key, dtau);
+  block_add_keyed<T>(dt, key, dtau);
 }
 
 // Adds (a_r, a_u) -- adjoints of a node's moments rho and u -- to all
@@ -216,7 +222,6 @@ __global__ void __launch_bounds__(256) k_adj_links(const typename P::T* __restri
     if (L::D == 3) uw2 = uwv[2 * nl + k];
   }
   T om = lam[(size_t)i * S + ks];  // weight of this link's value (consumed here)
-  lam[(size_t)i * S + ks] = (T)0;
   if (final_step && body >= 0) {
     // J = w_b . sum (f+_i'(x_f) + L) e_i'
     const double* wb = wbody + 3 * body;
@@ -315,6 +320,7 @@ __global__ void __launch_bounds__(256) k_adj_links(const typename P::T* __restri
            (double)aud2 * (double)(dcf * mf.uz + dcff * mff.uz + dcw * uw2);
   }
   dq_acc[k] += (double)om * dLdq;
+  lam[(size_t)i * S + ks] = (T)0;
 }
 
 // Open columns (D2Q9): inlet f+(0) = feq(rho1, u_in) + f+(1) - feq(rho1, u1)
@@ -347,21 +353,29 @@ __global__ void k_adj_open(typename P::T* __restrict__ lam, const Mom4<typename 
         B0 += l0[i] * w * ((T)3 * ex + (T)9 * e1 * ex - (T)3 * m1.ux);
         B1 += l0[i] * w * ((T)3 * ey + (T)9 * e1 * ey - (T)3 * m1.uy);
       }
+      T l1[L::Q];
 #pragma unroll
-      for (int j = 0; j < L::Q; ++j) {
-        lam[(size_t)j * S + k1] += l0[j] + sp - (B0 * ((T)L::cx(j) - m1.ux) + B1 * ((T)L::cy(j) - m1.uy));
-        lam[(size_t)j * S + k0] = (T)0;
-      }
+      for (int j = 0; j < L::Q; ++j) l1[j] = lam[(size_t)j * S + k1];
+#pragma unroll
+      for (int j = 0; j < L::Q; ++j)
+        lam[(size_t)j * S + k1] = l1[j] + l0[j] + sp - (B0 * ((T)L::cx(j) - m1.ux) + B1 * ((T)L::cy(j) - m1.uy));
+#pragma unroll
+      for (int j = 0; j < L::Q; ++j) lam[(size_t)j * S + k0] = (T)0;
     }
   }
   if (p.outlet) {
     const int32_t kl = lay.row_last[y];
     if (kl >= 0 && (lay.word[kl] & W_OPEN)) {
+      T a[L::Q], b[L::Q];
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) {
-        lam[(size_t)i * S + kl - 1] += lam[(size_t)i * S + kl];
-        lam[(size_t)i * S + kl] = (T)0;
+        a[i] = lam[(size_t)i * S + kl];
+        b[i] = lam[(size_t)i * S + kl - 1];
       }
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) lam[(size_t)i * S + kl - 1] = a[i] + b[i];
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) lam[(size_t)i * S + kl] = (T)0;
     }
   }
 }
@@ -408,7 +422,7 @@ __global__ void __launch_bounds__(256) k_adj_init(const typename P::T* __restric
     }
     dt *= rx.omega * rx.omega;
   }
-  block_add_keyed(dt, key, dtau);
+  block_add_keyed<double>(dt, key, dtau);
 }
 
 struct AdjointOps {

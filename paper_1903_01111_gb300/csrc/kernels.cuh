@@ -216,22 +216,42 @@ __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Pa
       return;
     }
   }
-  // Guo source (1 - 1/(2 tau)) w_i [3 (e_i - u).g + 9 (e_i.u)(e_i.g)]
-  //   = 3 (1 - 1/(2 tau)) w_i [(e_i.g)(1 + 3 e_i.u) - u.g]
+  // BGK with the Guo source (1 - 1/(2 tau)) w_i [3 (e_i - u).g + 9 (e_i.u)(e_i.g)]
+  //   = 3 (1 - 1/(2 tau)) w_i [(e_i.g)(1 + 3 e_i.u) - u.g],
+  // evaluated per pair of opposite directions (i, j = opp(i)): e_j = -e_i
+  // turns the equilibria into A +- B and the sources into Sc +- So with
+  //   A  = w (r + rho (4.5 (e_i.u)^2 - 1.5 u.u))   (FP64: w rho (1 + ...))
+  //   B  = 3 w rho (e_i.u)
+  //   Sc = fpre3 w (3 (e_i.g)(e_i.u) - u.g),   So = fpre3 w (e_i.g)
+  // so that f+_i,j = (1 - omega) f_i,j + (omega A + Sc) +- (omega B + So).
   const T fpre3 = (T)rx.fpre3;
   const T ug = ux * gx + uy * gy + uz * gz;
+  const T om1 = (T)1 - omega;
+  {
+    const T w = (T)L::w(0);
+    const T A = P::shifted ? w * (r - rho * uu15) : (w * rho) * ((T)1 - uu15);
+    T out = om1 * f[0] + omega * A;
+    if (rx.has_force) out -= fpre3 * w * ug;
+    fout[n_] = out;
+  }
 #pragma unroll
-  for (int i = 0; i < L::Q; ++i) {
+  for (int i = 1; i < L::Q; ++i) {
+    const int j = L::opp(i);
+    if (j < i) continue;
     const T eu = (T)L::cx(i) * ux + (T)L::cy(i) * uy + (T)L::cz(i) * uz;
     const T w = (T)L::w(i);
-    const T poly = (T)3 * eu + (T)4.5 * eu * eu - uu15;
-    const T feq = P::shifted ? w * (r + rho * poly) : (w * rho) * ((T)1 + poly);
-    T out = f[i] + omega * (feq - f[i]);
+    const T sym = (T)4.5 * eu * eu - uu15;
+    const T A = P::shifted ? w * (r + rho * sym) : (w * rho) * ((T)1 + sym);
+    const T B = ((T)3 * w * rho) * eu;
+    T Pv = omega * A, Mv = omega * B;
     if (rx.has_force) {
       const T eg = (T)L::cx(i) * gx + (T)L::cy(i) * gy + (T)L::cz(i) * gz;
-      out += fpre3 * w * (eg * ((T)1 + (T)3 * eu) - ug);
+      const T fw = fpre3 * w;
+      Pv += fw * ((T)3 * eg * eu - ug);
+      Mv += fw * eg;
     }
-    fout[(size_t)i * S + n_] = out;
+    fout[(size_t)i * S + n_] = om1 * f[i] + (Pv + Mv);
+    fout[(size_t)j * S + n_] = om1 * f[j] + (Pv - Mv);
   }
 }
 
@@ -569,17 +589,23 @@ __global__ void k_open(typename P::T* __restrict__ f, const Mom4<typename P::T>*
       const T uin = (T)inlet_velocity(p, lay, y);
       const Mom4<T> m1 = mom[k1];
       const T rho1 = P::shifted ? (T)p.rho0 + m1.r : m1.r;
+      T v[L::Q];
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) v[i] = f[i * S + k1];
 #pragma unroll
       for (int i = 0; i < L::Q; ++i)
         f[i * S + k0] = equilibrium<L, P>(i, m1.r, rho1, uin, (T)0, (T)0) +
-                        (f[i * S + k1] - equilibrium<L, P>(i, m1.r, rho1, m1.ux, m1.uy, (T)0));
+                        (v[i] - equilibrium<L, P>(i, m1.r, rho1, m1.ux, m1.uy, (T)0));
     }
   }
   if (p.outlet) {
     const int32_t kl = lay.row_last[y];
     if (kl >= 0 && (lay.word[kl] & W_OPEN)) {
+      T v[L::Q];
 #pragma unroll
-      for (int i = 0; i < L::Q; ++i) f[i * S + kl] = f[i * S + kl - 1];
+      for (int i = 0; i < L::Q; ++i) v[i] = f[i * S + kl - 1];
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) f[i * S + kl] = v[i];
     }
   }
 }

@@ -13,8 +13,9 @@ def test_draw_is_seeded_and_within_ranges():
         assert 64 <= s.nx <= 512 and 64 <= s.ny_fluid <= 256 and 10 <= s.re <= 100
         assert 1 <= len(s.cylinders) <= 8
         assert s.tau > 0.5
+        assert B.blockage(s) <= 0.4 + 1e-12
         for i, (x, y, r) in enumerate(s.cylinders):
-            assert 4.0 <= r <= 20.0 + 1e-12
+            assert 4.0 <= r <= min(20.0, s.ny_fluid / 6) + 1e-12
             assert r + 8 <= x <= s.nx - r - 16
             assert y - r >= 3.0 - 1e-9 and y + r <= s.ny_fluid - 1 - 3.0 + 1e-9
             for (x2, y2, r2) in s.cylinders[i + 1:]:
