@@ -128,6 +128,23 @@ def _max_over_ranks(dist, torch, v):
     return float(t.item())
 
 
+def _sum_over_ranks(dist, torch, v):
+    """Sum of a per-rank count over all ranks."""
+    if dist is None:
+        return v
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def sharded_mlups(dist, torch, units_local, steps, ms_local):
+    """Whole-job throughput when the ranks split one workload (no exchange):
+    the units of all ranks over the slowest rank's time."""
+    units = _sum_over_ranks(dist, torch, units_local)
+    return units * steps / (_max_over_ranks(dist, torch, ms_local) * 1e-3) / 1e6
+
+
 def replica_mlups(world, units_per_rank, steps, max_ms):
     """Whole-job throughput of `world` replicas: all units they processed
     divided by the slowest rank's time."""
@@ -312,7 +329,7 @@ def run_adjoint(lbm, n_steps=20000, checkpoint_every=500, fd=True):
     return out
 
 
-def run_batch(lbm, torch, peak, n_domains=256, seed=0, steps=2000, warmup=10, adjoint_steps=1024, K=32):
+def run_batch(lbm, torch, peak, n_domains=256, seed=0, steps=2000, warmup=10, adjoint_steps=1024, K=32, dist=None):
     """Batched channels: n_domains D2Q9 channels (sizes U[64,512] x U[64,256]
     fluid rows, 1-8 non-overlapping cylinders with radii U[4,20], Re U[10,100]
     on the channel height, u_max 0.1, VIBB cylinders, half-way walls,
@@ -322,11 +339,16 @@ def run_batch(lbm, torch, peak, n_domains=256, seed=0, steps=2000, warmup=10, ad
     stream).  Both arms run `steps` steps from the Poiseuille initial state
     and are timed over the last steps - warmup; the drag of every cylinder
     after the last step is compared.  Then the batched adjoint of the summed
-    drag (every cylinder, FP32 with FP64 accumulation)."""
+    drag (every cylinder, FP32 with FP64 accumulation).  Under several ranks
+    the channels are split between them (every world-th channel; no
+    exchange) and the throughputs count all ranks' nodes over the slowest
+    rank's time."""
     from paper_1903_01111_gb300 import batch as B
 
     t0 = time.perf_counter()
     specs = B.draw_channels(n_domains, seed)
+    if dist is not None:
+        specs = B.shard(specs, dist.get_rank(), dist.get_world_size())
     b = B.stack(specs)
     t_build = time.perf_counter() - t0
     u0 = b.initial_velocity()
@@ -360,7 +382,7 @@ def run_batch(lbm, torch, peak, n_domains=256, seed=0, steps=2000, warmup=10, ad
     s = 4
     bulk_ms = kms[2] / max(nlaunch[2], 1)
     bulk_bytes = nf * (2 * 9 * s + 1)
-    mlups32 = nf * (steps - warmup) / (ms32 * 1e-3) / 1e6
+    mlups32 = sharded_mlups(dist, torch, nf, steps - warmup, ms32)
     # per-domain FP64 lattices on one stream
     lats = []
     for spec, geo in zip(specs, b.parts):
@@ -379,7 +401,7 @@ def run_batch(lbm, torch, peak, n_domains=256, seed=0, steps=2000, warmup=10, ad
     F64 = np.concatenate([one.forces(len(spec.cylinders)) for one, spec in zip(lats, specs)])
     for one in lats:
         one.close()
-    mlups64 = nf * (steps - warmup) / s64 / 1e6
+    mlups64 = sharded_mlups(dist, torch, nf, steps - warmup, s64 * 1e3)
     rel = np.abs(F32[:, 0] - F64[:, 0]) / np.abs(F64[:, 0])
     rel = rel[np.isfinite(rel)]
     # batched adjoint of the summed drag
@@ -564,7 +586,7 @@ def main():
     e2e = None if args.no_e2e else run_e2e(lbm, torch, geo, args.steps)
     sweep = None if args.no_sweep else run_sweep(lbm, torch, args.sweep_steps, peak)
     adjoint = None if args.no_adjoint else run_adjoint(lbm)
-    batched = None if args.no_batch else run_batch(lbm, torch, peak)
+    batched = None if args.no_batch else run_batch(lbm, torch, peak, dist=dist)
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = run_oracle(96, 16)
