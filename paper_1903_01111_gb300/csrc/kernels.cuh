@@ -289,6 +289,28 @@ __device__ __forceinline__ void pull_sources(uint32_t k, const RunRec& run, cons
   }
 }
 
+// Offsets src_i - k of the pull sources of fluid node k (run `run`): away
+// from the periodic x seam every offset is a per-run constant (dx in the
+// node's own row, base - k0 + dx in a neighbour row); at the seam (x = 0 or
+// nx - 1 of a periodic row) they come from pull_sources.
+template <class L>
+__device__ __forceinline__ void pull_offsets(uint32_t k, const RunRec& run, const Layout& lay, const Params& p,
+                                             int (&d)[L::Q]) {
+  const int x = run.x0 + (int)(k - (uint32_t)run.k0);
+  if (x > 0 && x < p.nx - 1) {
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      const int dx = -L::cx(i), dy = -L::cy(i), dz = -L::cz(i);
+      d[i] = (dy == 0 && dz == 0) ? dx : run.base[row_slot(dy, dz)] - run.k0 + dx;
+    }
+    return;
+  }
+  uint32_t src[L::Q];
+  pull_sources<L>(k, run, lay, p, src);
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) d[i] = (int)(src[i] - k);
+}
+
 // ------------------------------------------------------------------ bulk --
 
 // Shapes of the bulk kernel the autotuner chooses from: threads per block
@@ -348,10 +370,11 @@ __global__ void __launch_bounds__(BT, (bulk_blocks_per_sm<P, BT, NPT>())) k_bulk
     if (live[j] && !(w[j] & (W_GHOST | W_OPEN))) {
       const RunRec run = lay.runs[w[j] & W_RUN];
       if (MULTI) dom[j] = run.dom;
-      uint32_t src[L::Q];
-      pull_sources<L>(k[j], run, lay, p, src);
+      int d[L::Q];
+      pull_offsets<L>(k[j], run, lay, p, d);
+      const T* __restrict__ fk = fin + k[j];
 #pragma unroll
-      for (int i = 0; i < L::Q; ++i) f[j][i] = __ldg(fin + (size_t)i * S + src[i]);
+      for (int i = 0; i < L::Q; ++i) f[j][i] = __ldg(fk + ((ptrdiff_t)i * (ptrdiff_t)S + d[i]));
     }
   }
 #pragma unroll
