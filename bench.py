@@ -128,6 +128,16 @@ def _max_over_ranks(dist, torch, v):
     return float(t.item())
 
 
+AUTOTUNE = True  # --tuning default: the stencil's default shapes (reproducible ncu launch lists)
+
+
+def _tune(lat, steps_per_trial):
+    """The lattice's launch shapes: autotuned on its live state, or the defaults."""
+    if AUTOTUNE:
+        return lat.autotune(steps_per_trial)[0]
+    return lat.tuning()
+
+
 def _sum_over_ranks(dist, torch, v):
     """Sum of a per-rank count over all ranks."""
     if dist is None:
@@ -166,7 +176,7 @@ def run_precision(lbm, torch, geo, precision, steps, warmup, dist, peak):
                       stream=stream.cuda_stream, vibb_density=lbm.LBM_VIBB_RHO_LOCAL)
     info = lat.info()
     lat.init_equilibrium()
-    tuning, _ = lat.autotune(10)
+    tuning = _tune(lat, 10)
     lat.step(warmup)
     _barrier(dist, torch)
     lbm.lbm_set_profiling(lat.h, True)
@@ -257,7 +267,7 @@ def run_sweep(lbm, torch, steps, peak, scale=1):
             stream = torch.cuda.Stream()
             lat = lbm.Lattice(geo, precision=prec, tau=0.7, g=(1e-6, 0.0, 0.0), bc=0, stream=stream.cuda_stream)
             lat.init_equilibrium()
-            tuning, _ = lat.autotune(10)
+            tuning = _tune(lat, 10)
             n = steps if s == 4 else max(10, steps // 5)
             lat.step(3)
             torch.cuda.synchronize()
@@ -356,7 +366,7 @@ def run_batch(lbm, torch, peak, n_domains=256, seed=0, steps=2000, warmup=10, ad
     lat = lbm.batch_lattice(b, precision=lbm.LBM_FP32_SHIFTED, bc=lbm.LBM_BC_VIBB, stream=stream.cuda_stream)
     info = lat.info()
     lat.init_equilibrium(u=u0)
-    tuning, tune_ms = lat.autotune(20)
+    tuning = _tune(lat, 20)
     lat.step(warmup)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -417,7 +427,7 @@ def run_batch(lbm, torch, peak, n_domains=256, seed=0, steps=2000, warmup=10, ad
                     "r U[4,20], Re U[10,100] on the channel height, u_max 0.1; stacked in one lattice",
         "lattice": [b.geometry.nx, b.geometry.ny], "fluid_nodes": nf, "links": int(info.n_links),
         "bodies": int(b.n_bodies), "stored_nodes": int(info.n_stored), "build_s": t_build,
-        "tuning": tuning.as_dict(), "autotune_best_ms_per_step": tune_ms, "diverged_domains": diverged,
+        "tuning": tuning.as_dict(), "diverged_domains": diverged,
         "fp32_batched": {"value": mlups32, "unit": "MLUPS", "ms_per_step": ms32 / (steps - warmup),
                          "steps_timed": steps - warmup,
                          "roofline": dict(roofline_entry(bulk_bytes, nf * FLOPS_PER_NODE[9], bulk_ms, s, peak),
@@ -539,7 +549,11 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=2000)
     ap.add_argument("--adjoint-steps", type=int, default=20000)
     ap.add_argument("--sweep-scale", type=int, default=1, help="divide the sweep lattices' sides by this")
+    ap.add_argument("--tuning", default="auto", choices=["auto", "default"],
+                    help="autotune every timed lattice (default) or keep the default launch shapes")
     args = ap.parse_args()
+    global AUTOTUNE
+    AUTOTUNE = args.tuning == "auto"
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -153,16 +153,19 @@ typedef struct {
 } lbm_domain;
 
 /* Launch shapes of the step (lbm_set_tuning, lbm_autotune).
- *  bulk_shape     0..5: (threads per block, nodes per thread) of the bulk
- *                 kernel = (256,1) (128,1) (512,1) (256,2) (128,2) (512,2);
- *                 3..5 are D2Q9 only.  -1 on input: the stencil's default.
+ *  bulk_shape     0..7: (threads per block, nodes per thread) of the bulk
+ *                 kernel = (256,1) (128,1) (512,1) (256,2) (128,2) (512,2),
+ *                 then (128,1) and (256,1) with each thread walking 4 nodes
+ *                 in sequence over the grid, the next node's addressing
+ *                 loaded while the current node's pulls are in flight;
+ *                 3..7 are D2Q9 only.  -1 on input: the stencil's default.
  *  link_threads   64, 128 or 256 threads per block of the link kernel.
  *  graph_steps    time steps per CUDA graph replayed by lbm_step (even,
  *                 2..64).
- * Shapes with the same nodes per thread give the same bits (force sums may
- * differ in the last place, as FP64 atomics are unordered); one and two
- * nodes per thread are separate compilations of the same arithmetic and
- * agree to rounding. */
+ * Shapes of the same kernel (same nodes per thread in parallel and in
+ * sequence) give the same bits (force sums may differ in the last place, as
+ * FP64 atomics are unordered); the kernels are separate compilations of the
+ * same arithmetic and agree to rounding. */
 typedef struct {
   int32_t bulk_shape, link_threads, graph_steps, reserved;
 } lbm_tuning;

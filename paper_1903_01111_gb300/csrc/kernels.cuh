@@ -313,19 +313,29 @@ __device__ __forceinline__ void pull_offsets(uint32_t k, const RunRec& run, cons
 
 // ------------------------------------------------------------------ bulk --
 
-// Shapes of the bulk kernel the autotuner chooses from: threads per block
-// and nodes per thread (a thread with two nodes takes k and k + ceil(S/2),
-// both ranges coalesced, and has 2Q loads in flight).  Two nodes per thread
-// are built for D2Q9 only (D3Q19 threads already have 19 loads in flight).
+// Shapes of the bulk kernel the autotuner chooses from: threads per block,
+// nodes per thread in parallel (a thread with two nodes takes k and
+// k + ceil(S/2), both ranges coalesced, and has 2Q loads in flight) and nodes
+// per thread in sequence (a thread walks k, k + G, k + 2G, ... over the grid
+// G and loads the next node's word and run while the current node's pulls
+// are in flight).  Two nodes per thread and the sequential walk are built
+// for D2Q9 only (D3Q19 threads already have 19 loads in flight).
 struct BulkShape {
-  int threads, npt;
+  int threads, npt, seq;
 };
-constexpr BulkShape kBulkShapes[] = {{256, 1}, {128, 1}, {512, 1}, {256, 2}, {128, 2}, {512, 2}};
-constexpr int kNumBulkShapes = 6;
+constexpr BulkShape kBulkShapes[] = {{256, 1, 1}, {128, 1, 1}, {512, 1, 1}, {256, 2, 1},
+                                     {128, 2, 1}, {512, 2, 1}, {128, 1, 4}, {256, 1, 4}};
+constexpr int kNumBulkShapes = 8;
 
 template <class L>
 constexpr int bulk_max_npt() {
   return L::Q == 9 ? 2 : 1;
+}
+
+// Shapes built for a stencil, one bit per shape.
+template <class L>
+constexpr unsigned bulk_shape_mask() {
+  return L::Q == 9 ? 0xffu : 0x07u;
 }
 
 // Default shape: two nodes per thread for D2Q9, one for D3Q19, 256 threads.
@@ -334,12 +344,14 @@ constexpr int bulk_default_shape() {
   return L::Q == 9 ? 3 : 0;
 }
 
-// Resident blocks per SM a shape is compiled for: the register budget of
-// 256-thread blocks at the precision's count (one fewer for two nodes per
-// thread in FP32, whose registers would otherwise spill), scaled to BT.
-template <class P, int BT, int NPT>
+// Resident blocks per SM a shape is compiled for, from a register budget per
+// 256 threads: FP32 D2Q9 6 blocks with one node per thread (40 registers) and
+// 4 with two; FP32 D3Q19 5 (48 registers); FP64 2.  Measured: one block more
+// spills (D3Q19) or runs slower (D2Q9 two nodes); one fewer leaves too few
+// loads in flight.
+template <class L, class P, int BT, int NPT>
 constexpr int bulk_blocks_per_sm() {
-  constexpr int base = (NPT == 2 && P::bulk_min_blocks > 2) ? P::bulk_min_blocks - 1 : P::bulk_min_blocks;
+  constexpr int base = !P::shifted ? 2 : (L::Q == 9 ? (NPT == 1 ? 6 : 4) : 5);
   return base * 256 / BT < 1 ? 1 : base * 256 / BT;
 }
 
@@ -347,7 +359,7 @@ constexpr int bulk_blocks_per_sm() {
 // run's domain parameters.  Block (0) also clears the force slot of the
 // next step.
 template <class L, class P, bool MULTI, int BT, int NPT>
-__global__ void __launch_bounds__(BT, (bulk_blocks_per_sm<P, BT, NPT>())) k_bulk(const typename P::T* __restrict__ fin,
+__global__ void __launch_bounds__(BT, (bulk_blocks_per_sm<L, P, BT, NPT>())) k_bulk(const typename P::T* __restrict__ fin,
                                                                        typename P::T* __restrict__ fout, Layout lay,
                                                                        Mom4<typename P::T>* __restrict__ mom,
                                                                        double* __restrict__ force_next, Params p) {
@@ -387,6 +399,76 @@ __global__ void __launch_bounds__(BT, (bulk_blocks_per_sm<P, BT, NPT>())) k_bulk
     }
     const Relax rx = MULTI ? relax_domain(lay.dom, dom[j]) : relax_params(p);
     collide_store<L, P>(f[j], p, rx, fout, S, k[j], mom, (w[j] & W_CACHE) != 0);
+  }
+}
+
+// The fields of a run record that the pull offsets use away from the seam.
+template <class L>
+struct RunLite {
+  int32_t x0, k0, dom;
+  int32_t base[L::D == 2 ? 2 : 8];
+};
+
+template <class L, bool MULTI>
+__device__ __forceinline__ RunLite<L> load_run_lite(const RunRec* __restrict__ runs, uint32_t r) {
+  RunLite<L> v;
+  v.x0 = runs[r].x0;
+  v.k0 = runs[r].k0;
+  v.dom = MULTI ? runs[r].dom : 0;
+#pragma unroll
+  for (int sl = 0; sl < (L::D == 2 ? 2 : 8); ++sl) v.base[sl] = runs[r].base[sl];
+  return v;
+}
+
+// Sequential walk over the grid with the next node's word and run loaded
+// while the current node's pulls are in flight (D2Q9).
+template <class L, class P, bool MULTI, int BT, int SEQ>
+__global__ void __launch_bounds__(BT, (bulk_blocks_per_sm<L, P, BT, 1>())) k_bulk_seq(
+    const typename P::T* __restrict__ fin, typename P::T* __restrict__ fout, Layout lay,
+    Mom4<typename P::T>* __restrict__ mom, double* __restrict__ force_next, Params p) {
+  using T = typename P::T;
+  if (force_next && blockIdx.x == 0)
+    for (int t = threadIdx.x; t < 3 * p.nbody; t += BT) force_next[t] = 0.0;
+  const size_t S = (size_t)lay.S;
+  const uint32_t G = gridDim.x * BT;
+  uint32_t k = blockIdx.x * BT + threadIdx.x;
+  uint32_t w = k < S ? __ldg(lay.word + k) : W_GHOST;
+  RunLite<L> run{};
+  if (!(w & (W_GHOST | W_OPEN))) run = load_run_lite<L, MULTI>(lay.runs, w & W_RUN);
+  uint32_t w2 = ((uint64_t)k + G < S) ? __ldg(lay.word + k + G) : W_GHOST;
+#pragma unroll 1
+  for (int it = 0; it < SEQ && (uint64_t)k < S; ++it, k += G) {
+    T f[L::Q];
+    const bool fluid = !(w & (W_GHOST | W_OPEN));
+    if (fluid) {
+      int d[L::Q];
+      const int x = run.x0 + (int)(k - (uint32_t)run.k0);
+      if (x > 0 && x < p.nx - 1) {
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+          const int dx = -L::cx(i), dy = -L::cy(i), dz = -L::cz(i);
+          d[i] = (dy == 0 && dz == 0) ? dx : run.base[row_slot(dy, dz)] - run.k0 + dx;
+        }
+      } else {
+        pull_offsets<L>(k, lay.runs[w & W_RUN], lay, p, d);
+      }
+      const T* __restrict__ fk = fin + k;
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) f[i] = __ldg(fk + ((ptrdiff_t)i * (ptrdiff_t)S + d[i]));
+    }
+    RunLite<L> run2{};
+    if ((uint64_t)k + G < S && !(w2 & (W_GHOST | W_OPEN))) run2 = load_run_lite<L, MULTI>(lay.runs, w2 & W_RUN);
+    const uint32_t w3 = ((uint64_t)k + 2ull * G < S) ? __ldg(lay.word + k + 2 * G) : W_GHOST;
+    if (!fluid) {
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) fout[(size_t)i * S + k] = (T)0;
+    } else {
+      const Relax rx = MULTI ? relax_domain(lay.dom, run.dom) : relax_params(p);
+      collide_store<L, P>(f, p, rx, fout, S, k, mom, (w & W_CACHE) != 0);
+    }
+    w = w2;
+    run = run2;
+    w2 = w3;
   }
 }
 
@@ -784,7 +866,8 @@ __global__ void k_check(const typename P::T* __restrict__ f, Layout lay, int* __
 struct KernelOps {
   int Q, D;
   size_t real_bytes;
-  int default_shape, max_npt;
+  int default_shape;
+  unsigned shape_mask;  // bit b: kBulkShapes[b] is built for this stencil
   // shape: index into kBulkShapes; threads: link kernel block size (64, 128 or 256)
   void (*bulk)(const void* fin, void* fout, const Layout& lay, void* mom, double* force_next, const Params& p,
                int shape, cudaStream_t s);
@@ -813,6 +896,12 @@ struct Launch {
     k_bulk<L, P, M, BT, NPT><<<blocks_for((lay.S + NPT - 1) / NPT, BT), BT, 0, s>>>((const T*)fin, (T*)fout, lay,
                                                                                    (Mom4<T>*)mom, force_next, p);
   }
+  template <bool M, int BT, int SEQ>
+  static void bulk_seq(const void* fin, void* fout, const Layout& lay, void* mom, double* force_next,
+                       const Params& p, cudaStream_t s) {
+    k_bulk_seq<L, P, M, BT, SEQ><<<blocks_for((lay.S + SEQ - 1) / SEQ, BT), BT, 0, s>>>(
+        (const T*)fin, (T*)fout, lay, (Mom4<T>*)mom, force_next, p);
+  }
   template <bool M>
   static void bulk_m(const void* fin, void* fout, const Layout& lay, void* mom, double* fn, const Params& p,
                      int shape, cudaStream_t s) {
@@ -826,6 +915,8 @@ struct Launch {
         case 3: return bulk_shape<M, 256, 2>(fin, fout, lay, mom, fn, p, s);
         case 4: return bulk_shape<M, 128, 2>(fin, fout, lay, mom, fn, p, s);
         case 5: return bulk_shape<M, 512, 2>(fin, fout, lay, mom, fn, p, s);
+        case 6: return bulk_seq<M, 128, 4>(fin, fout, lay, mom, fn, p, s);
+        case 7: return bulk_seq<M, 256, 4>(fin, fout, lay, mom, fn, p, s);
         default: break;
       }
     }
@@ -880,7 +971,7 @@ struct Launch {
     k_gather<L, P><<<blocks_for(n, 256), 256, 0, s>>>((const T*)f, lay, sk, n, out, p);
   }
   static KernelOps ops() {
-    return KernelOps{L::Q,    L::D,    sizeof(T), bulk_default_shape<L>(), bulk_max_npt<L>(), bulk, links, open, init,
+    return KernelOps{L::Q,    L::D,    sizeof(T), bulk_default_shape<L>(), bulk_shape_mask<L>(), bulk, links, open, init,
                      moments, refresh, get_dir, set_dir, check,     gather};
   }
 };

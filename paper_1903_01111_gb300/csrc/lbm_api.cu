@@ -1247,7 +1247,7 @@ lbm_status lbm_set_tuning(lbm_handle h, const lbm_tuning* t) {
   if (!h || !t) return fail(LBM_ERR_INVALID_ARG, "null argument");
   lbm_tuning v = *t;
   if (v.bulk_shape == -1) v.bulk_shape = h->ops.default_shape;
-  if (v.bulk_shape < 0 || v.bulk_shape >= kNumBulkShapes || kBulkShapes[v.bulk_shape].npt > h->ops.max_npt)
+  if (v.bulk_shape < 0 || v.bulk_shape >= kNumBulkShapes || !((h->ops.shape_mask >> v.bulk_shape) & 1u))
     return fail(LBM_ERR_INVALID_ARG, "bulk_shape %d is not built for this stencil", t->bulk_shape);
   if (v.link_threads != 64 && v.link_threads != 128 && v.link_threads != 256)
     return fail(LBM_ERR_INVALID_ARG, "link_threads must be 64, 128 or 256");
@@ -1350,7 +1350,7 @@ lbm_status lbm_autotune(lbm_handle h, int32_t steps_per_trial, lbm_tuning* best,
     return r;
   };
   for (int sh = 0; sh < kNumBulkShapes && st == LBM_OK; ++sh) {
-    if (kBulkShapes[sh].npt > h->ops.max_npt) continue;
+    if (!((h->ops.shape_mask >> sh) & 1u)) continue;
     cand.bulk_shape = sh;
     st = consider(cand);
   }

@@ -111,13 +111,14 @@ class lbm_tuning(ctypes.Structure):
     ]
 
     def as_dict(self):
-        return {"bulk_shape": self.bulk_shape, "bulk_threads": BULK_SHAPES[self.bulk_shape][0],
-                "bulk_nodes_per_thread": BULK_SHAPES[self.bulk_shape][1], "link_threads": self.link_threads,
-                "graph_steps": self.graph_steps}
+        t, npt, seq = BULK_SHAPES[self.bulk_shape]
+        return {"bulk_shape": self.bulk_shape, "bulk_threads": t, "bulk_nodes_per_thread": npt,
+                "bulk_sequential_nodes": seq, "link_threads": self.link_threads, "graph_steps": self.graph_steps}
 
 
-# (threads per block, nodes per thread) of bulk_shape 0..5
-BULK_SHAPES = ((256, 1), (128, 1), (512, 1), (256, 2), (128, 2), (512, 2))
+# (threads per block, nodes per thread, nodes per thread in sequence) of
+# bulk_shape 0..7; 3..7 are built for D2Q9 only
+BULK_SHAPES = ((256, 1, 1), (128, 1, 1), (512, 1, 1), (256, 2, 1), (128, 2, 1), (512, 2, 1), (128, 1, 4), (256, 1, 4))
 
 
 _H = ctypes.c_void_p
