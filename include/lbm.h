@@ -155,9 +155,9 @@ typedef struct {
 /* Launch shapes of the step (lbm_set_tuning, lbm_autotune).
  *  bulk_shape     0..7: (threads per block, nodes per thread) of the bulk
  *                 kernel = (256,1) (128,1) (512,1) (256,2) (128,2) (512,2),
- *                 then (128,1) and (256,1) with each thread walking 4 nodes
- *                 in sequence over the grid, the next node's addressing
- *                 loaded while the current node's pulls are in flight;
+ *                 then (128,1) with each thread walking 4 or 8 nodes in
+ *                 sequence over the grid, the next node's addressing loaded
+ *                 while the current node's pulls are in flight;
  *                 3..7 are D2Q9 only.  -1 on input: the stencil's default.
  *  link_threads   64, 128 or 256 threads per block of the link kernel.
  *  graph_steps    time steps per CUDA graph replayed by lbm_step (even,

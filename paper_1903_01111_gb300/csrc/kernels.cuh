@@ -63,13 +63,14 @@ constexpr uint32_t W_CACHE = 1u << 29;
 constexpr uint32_t W_OPEN = 1u << 30;
 constexpr uint32_t W_GHOST = 1u << 31;
 
-// One fluid run: x0, its storage index k0, its row (y, z), for each
-// neighbour row (slot order below) the storage index of (x0, row'), and the
-// domain the row belongs to.
+// One fluid run starting at x0 with storage index k0: xk = x0 - k0 (so that
+// node k of the run sits at x = k + xk), its row (y, z), the domain the row
+// belongs to, and for each neighbour row (slot order below) dbase = the
+// storage index of (x0, row') minus k0 (so that the pull from (x + dx, row')
+// is k + dbase + dx).  48 B.
 struct __align__(16) RunRec {
-  int32_t x0, k0, y, z;
-  int32_t base[8];
-  int32_t dom, pad_[3];
+  int32_t xk, y, z, dom;
+  int32_t dbase[8];
 };
 
 // Run parameters of one domain of a batch (several independent flows
@@ -260,7 +261,7 @@ template <class L>
 __device__ __forceinline__ void pull_sources(uint32_t k, const RunRec& run, const Layout& lay, const Params& p,
                                              uint32_t (&src)[L::Q]) {
   const int nx = p.nx;
-  const int x = run.x0 + (int)(k - (uint32_t)run.k0);
+  const int x = (int)k + run.xk;
   const bool left = x == 0, right = x == nx - 1;
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
@@ -283,7 +284,7 @@ __device__ __forceinline__ void pull_sources(uint32_t k, const RunRec& run, cons
         const int row = yy + p.ny * zz;
         src[i] = (uint32_t)(dx < 0 ? lay.row_last[row] : lay.row_first[row]);
       } else {
-        src[i] = (uint32_t)(run.base[row_slot(dy, dz)] + (x + dx - run.x0));
+        src[i] = (uint32_t)((int)k + run.dbase[row_slot(dy, dz)] + dx);
       }
     }
   }
@@ -296,12 +297,12 @@ __device__ __forceinline__ void pull_sources(uint32_t k, const RunRec& run, cons
 template <class L>
 __device__ __forceinline__ void pull_offsets(uint32_t k, const RunRec& run, const Layout& lay, const Params& p,
                                              int (&d)[L::Q]) {
-  const int x = run.x0 + (int)(k - (uint32_t)run.k0);
+  const int x = (int)k + run.xk;
   if (x > 0 && x < p.nx - 1) {
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
       const int dx = -L::cx(i), dy = -L::cy(i), dz = -L::cz(i);
-      d[i] = (dy == 0 && dz == 0) ? dx : run.base[row_slot(dy, dz)] - run.k0 + dx;
+      d[i] = (dy == 0 && dz == 0) ? dx : run.dbase[row_slot(dy, dz)] + dx;
     }
     return;
   }
@@ -324,7 +325,7 @@ struct BulkShape {
   int threads, npt, seq;
 };
 constexpr BulkShape kBulkShapes[] = {{256, 1, 1}, {128, 1, 1}, {512, 1, 1}, {256, 2, 1},
-                                     {128, 2, 1}, {512, 2, 1}, {128, 1, 4}, {256, 1, 4}};
+                                     {128, 2, 1}, {512, 2, 1}, {128, 1, 4}, {128, 1, 8}};
 constexpr int kNumBulkShapes = 8;
 
 template <class L>
@@ -405,23 +406,23 @@ __global__ void __launch_bounds__(BT, (bulk_blocks_per_sm<L, P, BT, NPT>())) k_b
 // The fields of a run record that the pull offsets use away from the seam.
 template <class L>
 struct RunLite {
-  int32_t x0, k0, dom;
-  int32_t base[L::D == 2 ? 2 : 8];
+  int32_t xk, dom;
+  int32_t dbase[L::D == 2 ? 2 : 8];
 };
 
 template <class L, bool MULTI>
 __device__ __forceinline__ RunLite<L> load_run_lite(const RunRec* __restrict__ runs, uint32_t r) {
   RunLite<L> v;
-  v.x0 = runs[r].x0;
-  v.k0 = runs[r].k0;
+  v.xk = runs[r].xk;
   v.dom = MULTI ? runs[r].dom : 0;
 #pragma unroll
-  for (int sl = 0; sl < (L::D == 2 ? 2 : 8); ++sl) v.base[sl] = runs[r].base[sl];
+  for (int sl = 0; sl < (L::D == 2 ? 2 : 8); ++sl) v.dbase[sl] = runs[r].dbase[sl];
   return v;
 }
 
-// Sequential walk over the grid with the next node's word and run loaded
-// while the current node's pulls are in flight (D2Q9).
+// Sequential walk over the grid: the word of the node after next is loaded
+// while the current node's pulls are in flight, and the next node's run
+// record right after the current node's stores (D2Q9).
 template <class L, class P, bool MULTI, int BT, int SEQ>
 __global__ void __launch_bounds__(BT, (bulk_blocks_per_sm<L, P, BT, 1>())) k_bulk_seq(
     const typename P::T* __restrict__ fin, typename P::T* __restrict__ fout, Layout lay,
@@ -442,12 +443,12 @@ __global__ void __launch_bounds__(BT, (bulk_blocks_per_sm<L, P, BT, 1>())) k_bul
     const bool fluid = !(w & (W_GHOST | W_OPEN));
     if (fluid) {
       int d[L::Q];
-      const int x = run.x0 + (int)(k - (uint32_t)run.k0);
+      const int x = (int)k + run.xk;
       if (x > 0 && x < p.nx - 1) {
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
           const int dx = -L::cx(i), dy = -L::cy(i), dz = -L::cz(i);
-          d[i] = (dy == 0 && dz == 0) ? dx : run.base[row_slot(dy, dz)] - run.k0 + dx;
+          d[i] = (dy == 0 && dz == 0) ? dx : run.dbase[row_slot(dy, dz)] + dx;
         }
       } else {
         pull_offsets<L>(k, lay.runs[w & W_RUN], lay, p, d);
@@ -456,8 +457,6 @@ __global__ void __launch_bounds__(BT, (bulk_blocks_per_sm<L, P, BT, 1>())) k_bul
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) f[i] = __ldg(fk + ((ptrdiff_t)i * (ptrdiff_t)S + d[i]));
     }
-    RunLite<L> run2{};
-    if ((uint64_t)k + G < S && !(w2 & (W_GHOST | W_OPEN))) run2 = load_run_lite<L, MULTI>(lay.runs, w2 & W_RUN);
     const uint32_t w3 = ((uint64_t)k + 2ull * G < S) ? __ldg(lay.word + k + 2 * G) : W_GHOST;
     if (!fluid) {
 #pragma unroll
@@ -466,8 +465,9 @@ __global__ void __launch_bounds__(BT, (bulk_blocks_per_sm<L, P, BT, 1>())) k_bul
       const Relax rx = MULTI ? relax_domain(lay.dom, run.dom) : relax_params(p);
       collide_store<L, P>(f, p, rx, fout, S, k, mom, (w & W_CACHE) != 0);
     }
+    // the next node's run record, loaded before its pulls are needed
     w = w2;
-    run = run2;
+    if ((uint64_t)k + G < S && !(w & (W_GHOST | W_OPEN))) run = load_run_lite<L, MULTI>(lay.runs, w & W_RUN);
     w2 = w3;
   }
 }
@@ -916,7 +916,7 @@ struct Launch {
         case 4: return bulk_shape<M, 128, 2>(fin, fout, lay, mom, fn, p, s);
         case 5: return bulk_shape<M, 512, 2>(fin, fout, lay, mom, fn, p, s);
         case 6: return bulk_seq<M, 128, 4>(fin, fout, lay, mom, fn, p, s);
-        case 7: return bulk_seq<M, 256, 4>(fin, fout, lay, mom, fn, p, s);
+        case 7: return bulk_seq<M, 128, 8>(fin, fout, lay, mom, fn, p, s);
         default: break;
       }
     }

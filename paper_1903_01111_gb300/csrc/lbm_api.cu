@@ -607,8 +607,7 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
       int64_t xe = x;
       while (xe + 1 < nx && !(m[xe + 1 + nx * r] & (H_SOLID | H_OPEN))) ++xe;
       RunRec rec{};
-      rec.x0 = (int32_t)x;
-      rec.k0 = sidx[n];
+      rec.xk = (int32_t)(x - sidx[n]);
       rec.y = (int32_t)y;
       rec.z = (int32_t)z;
       rec.dom = rdom[r];
@@ -624,7 +623,7 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
             return fail(LBM_ERR_INVALID_ARG,
                         "layout: neighbour row of the fluid run at (%lld..%lld, %lld, %lld) is not fully stored",
                         (long long)x, (long long)xe, (long long)y, (long long)z);
-        rec.base[sl] = base;
+        rec.dbase[sl] = base - sidx[n];
       }
       const uint32_t rid = (uint32_t)runs.size();
       if (rid > W_RUN) return fail(LBM_ERR_UNSUPPORTED, "too many fluid runs");

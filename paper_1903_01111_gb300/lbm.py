@@ -118,7 +118,7 @@ class lbm_tuning(ctypes.Structure):
 
 # (threads per block, nodes per thread, nodes per thread in sequence) of
 # bulk_shape 0..7; 3..7 are built for D2Q9 only
-BULK_SHAPES = ((256, 1, 1), (128, 1, 1), (512, 1, 1), (256, 2, 1), (128, 2, 1), (512, 2, 1), (128, 1, 4), (256, 1, 4))
+BULK_SHAPES = ((256, 1, 1), (128, 1, 1), (512, 1, 1), (256, 2, 1), (128, 2, 1), (512, 2, 1), (128, 1, 4), (128, 1, 8))
 
 
 _H = ctypes.c_void_p
