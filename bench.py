@@ -131,8 +131,18 @@ def _max_over_ranks(dist, torch, v):
 AUTOTUNE = True  # --tuning default: the stencil's default shapes (reproducible ncu launch lists)
 
 
+BULK_SHAPE = -1  # --bulk-shape: force one bulk kernel shape (profiling a given kernel)
+
+
 def _tune(lat, steps_per_trial):
-    """The lattice's launch shapes: autotuned on its live state, or the defaults."""
+    """The lattice's launch shapes: autotuned on its live state, the
+    defaults, or the forced bulk shape (where the stencil has it)."""
+    if BULK_SHAPE >= 0:
+        try:
+            lat.set_tuning(bulk_shape=BULK_SHAPE)
+        except Exception:
+            pass
+        return lat.tuning()
     if AUTOTUNE:
         return lat.autotune(steps_per_trial)[0]
     return lat.tuning()
@@ -223,11 +233,11 @@ def run_precision(lbm, torch, geo, precision, steps, warmup, dist, peak):
     }
 
 
-# DRAM bytes (read + write) per fluid node of k_bulk<D3Q19, F32S> on the
-# sphere-pack recipe, from an ncu capture of a 192^3 pack of the same recipe
-# (593 MB per launch for 2.83M fluid nodes); traffic grows with the fluid
-# node count, so a full launch moves this figure times its fluid nodes.
-TRAFFIC_PER_FLUID_NODE_PACK_FP32 = 209.7
+# DRAM bytes (read + write) per fluid node of k_bulk<D3Q19, F32S, 0, 256, 1>
+# on the sphere-pack recipe, from an ncu capture of a 192^3 pack of the same
+# recipe (594.5 MB per launch for 2.83M fluid nodes); traffic grows with the
+# fluid node count, so a full launch moves this figure times its fluid nodes.
+TRAFFIC_PER_FLUID_NODE_PACK_FP32 = 210.2
 
 
 # FP64 arithmetic peak of GB300, from unit counts and clock: 152 SMs x 2 FP64
@@ -551,9 +561,12 @@ def main():
     ap.add_argument("--sweep-scale", type=int, default=1, help="divide the sweep lattices' sides by this")
     ap.add_argument("--tuning", default="auto", choices=["auto", "default"],
                     help="autotune every timed lattice (default) or keep the default launch shapes")
+    ap.add_argument("--bulk-shape", type=int, default=-1,
+                    help="force this bulk kernel shape where the stencil has it (profiling)")
     args = ap.parse_args()
-    global AUTOTUNE
+    global AUTOTUNE, BULK_SHAPE
     AUTOTUNE = args.tuning == "auto"
+    BULK_SHAPE = args.bulk_shape
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
