@@ -457,6 +457,62 @@ def run_batch(lbm, torch, peak, n_domains=256, seed=0, steps=2000, warmup=10, ad
     }
 
 
+def run_cylinder(lbm, torch, re, steps, sample_every=10, window=None):
+    """Flow past the off-grid cylinder in the 2000 x 400 channel (radius 20.3
+    at (400.37, 200.61), u_max 0.1, Re on the mean inflow 2/3 u_max and the
+    diameter, Poiseuille start), FP32 shifted and FP64, VIBB: drag and lift
+    coefficients C_D = 2 F_x / (rho0 U^2 D), C_L = 2 F_y / (rho0 U^2 D) sampled
+    every `sample_every` steps; mean C_D, the lift's amplitude and the
+    Strouhal number St = f D / U (FFT of C_L) over the last `window` steps."""
+    from paper_1903_01111_gb300 import geometry as G
+
+    R, u_max, H = 20.3, 0.1, 400
+    ubar, D = 2.0 / 3.0 * u_max, 2 * R
+    tau = 3 * ubar * D / re + 0.5
+    geo = G.cylinder_channel(nx=2000, ny_fluid=H, center=(400.37, 200.61), radius=R, u_max=u_max)
+    y = (np.arange(geo.N) // geo.nx) % geo.ny
+    u0 = np.zeros((geo.N, 3))
+    u0[:, 0] = np.where(geo.solid == 0, 4 * u_max * (y - 0.5) * (H + 0.5 - y) / H ** 2, 0.0)
+    window = window or steps // 2
+    m = window // sample_every
+    out = {"re": re, "tau": tau, "steps": steps, "window": window}
+    series = {}
+    for name, prec in (("fp32s", lbm.LBM_FP32_SHIFTED), ("fp64", lbm.LBM_FP64)):
+        with lbm.Lattice(geo, precision=prec, tau=tau, bc=lbm.LBM_BC_VIBB, inlet_umax=u_max, inlet_y0=0.5,
+                         inlet_y1=H + 0.5) as lat:
+            lat.init_equilibrium(u=u0)
+            _tune(lat, 10)
+            cd, cl = [], []
+            t0 = time.perf_counter()
+            for _ in range(steps // sample_every):
+                lat.step(sample_every)
+                F = lat.force(0)
+                cd.append(2 * F[0] / (ubar ** 2 * D))
+                cl.append(2 * F[1] / (ubar ** 2 * D))
+            wall = time.perf_counter() - t0
+            lat.check()
+            nf = lat.info().n_fluid
+        cd, cl = np.array(cd), np.array(cl)
+        clw = cl[-m:] - cl[-m:].mean()
+        spec = np.abs(np.fft.rfft(clw * np.hanning(m)))
+        freq = np.fft.rfftfreq(m, d=sample_every)
+        amp = 0.5 * (cl[-m:].max() - cl[-m:].min())
+        st = freq[int(np.argmax(spec[1:]) + 1)] * D / ubar if amp > 1e-3 else None  # steady wake: no shedding
+        series[name] = (cd, cl)
+        out[name] = {"C_D_mean": float(cd[-m:].mean()), "C_L_mean": float(cl[-m:].mean()),
+                     "C_L_amplitude": float(amp), "St": (float(st) if st is not None else None),
+                     "mlups_with_force_every_sample": nf * steps / wall / 1e6}
+    d32, d64 = out["fp32s"], out["fp64"]
+    out["fp32s_vs_fp64"] = {
+        "C_D_rel": abs(d32["C_D_mean"] - d64["C_D_mean"]) / abs(d64["C_D_mean"]),
+        "C_L_amplitude_rel": (abs(d32["C_L_amplitude"] - d64["C_L_amplitude"]) / d64["C_L_amplitude"]
+                              if d64["C_L_amplitude"] > 1e-3 else None),
+        "St_rel": (abs(d32["St"] - d64["St"]) / d64["St"] if d32["St"] and d64["St"] else None),
+        "max_abs_C_D_diff_over_run": float(np.abs(series["fp32s"][0] - series["fp64"][0]).max()),
+        "max_abs_C_L_diff_over_run": float(np.abs(series["fp32s"][1] - series["fp64"][1]).max())}
+    return out
+
+
 def run_e2e(lbm, torch, geo, steps):
     """Same workload through the C ABI with host buffers: geometry upload,
     initialisation, per step lbm_step(1) + lbm_force to a host array, and the
@@ -552,8 +608,10 @@ def main():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-cylinder", action="store_true")
+    ap.add_argument("--cylinder-steps", type=int, default=60000)
     ap.add_argument("--sweep-steps", type=int, default=100)
-    ap.add_argument("--part", default="all", choices=["all", "batch", "adjoint", "sweep"],
+    ap.add_argument("--part", default="all", choices=["all", "batch", "adjoint", "sweep", "cylinder"],
                     help="run one section alone (for profiling) and print its JSON")
     ap.add_argument("--batch-domains", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=2000)
@@ -577,7 +635,10 @@ def main():
         from paper_1903_01111_gb300 import lbm
 
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-        if args.part == "sweep":
+        if args.part == "cylinder":
+            out = [run_cylinder(lbm, torch, 20, args.cylinder_steps // 2),
+                   run_cylinder(lbm, torch, 100, args.cylinder_steps)]
+        elif args.part == "sweep":
             out = run_sweep(lbm, torch, args.sweep_steps, _peaks()[0], scale=args.sweep_scale)
         elif args.part == "batch":
             out = run_batch(lbm, torch, _peaks()[0], n_domains=args.batch_domains, steps=args.batch_steps,
@@ -614,6 +675,10 @@ def main():
     sweep = None if args.no_sweep else run_sweep(lbm, torch, args.sweep_steps, peak)
     adjoint = None if args.no_adjoint else run_adjoint(lbm)
     batched = None if args.no_batch else run_batch(lbm, torch, peak, dist=dist)
+    cylinder = None
+    if not args.no_cylinder:
+        cylinder = [run_cylinder(lbm, torch, 20, args.cylinder_steps // 2),
+                    run_cylinder(lbm, torch, 100, args.cylinder_steps)]
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = run_oracle(96, 16)
@@ -642,6 +707,8 @@ def main():
         line["adjoint"] = adjoint
     if batched is not None:
         line["batched"] = batched
+    if cylinder is not None:
+        line["cylinder"] = cylinder
     if r64 is not None:
         line["fp64"] = {"value": r64["mlups"], "unit": "MLUPS", "ms_per_step": r64["ms_per_step"],
                         "roofline": r64["roofline"], "kernels": r64["kernels"],

@@ -116,8 +116,16 @@ __device__ __forceinline__ void block_add_keyed(T v, int key, double* target) {
   }
 }
 
+// Resident 256-thread blocks per SM of the adjoint bulk kernel: 4 (64
+// registers, no spill) for FP32 D2Q9, 2 (up to 128 registers) for FP64 D2Q9
+// and FP32 D3Q19, 1 for FP64 D3Q19 (which spills at 128 registers).
 template <class L, class P>
-__global__ void __launch_bounds__(256) k_adj_bulk(const typename P::T* __restrict__ fin,
+constexpr int adj_bulk_blocks_per_sm() {
+  return L::Q == 9 ? (P::shifted ? 4 : 2) : (P::shifted ? 2 : 1);
+}
+
+template <class L, class P>
+__global__ void __launch_bounds__(256, (adj_bulk_blocks_per_sm<L, P>())) k_adj_bulk(const typename P::T* __restrict__ fin,
                                                   typename P::T* __restrict__ lam_next,
                                                   typename P::T* __restrict__ lam_out, Layout lay, Params p,
                                                   double* __restrict__ dtau, Mom4<typename P::T>* __restrict__ mom) {

@@ -223,3 +223,59 @@ def test_set_domains_rejects_bad_tables(L):
         L.lbm_set_domains(h, b.domains)
     assert e.value.status == L.LBM_ERR_STATE
     L.lbm_destroy(h)
+
+
+def _slab(nx, ny, nzf, q_lo, q_hi, sphere):
+    """D3Q19 slab channel: walls normal to z at q_lo below the first and q_hi
+    above the last of nzf fluid layers (one solid layer each side), periodic
+    in x and y, one sphere (force id 0)."""
+    bodies = [G.halfspace((0, 0, -1), -(1.0 - q_lo), force_id=-1),
+              G.halfspace((0, 0, 1), nzf + q_hi, force_id=-1),
+              G.ball(sphere[:3], sphere[3], force_id=0)]
+    return G.build(1, (nx, ny, nzf + 2), (True, True, False), bodies)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32s"])
+def test_d3q19_domains_stacked_along_z_equal_domains_alone(L, prec):
+    """D3Q19 domains stack along z (the last axis): two slab channels with
+    their own tau and body force, each equal bit for bit to the same slab run
+    as a lattice of its own."""
+    precision = L.LBM_FP64 if prec == "fp64" else L.LBM_FP32_SHIFTED
+    parts = [(_slab(14, 12, 9, 0.3, 0.6, (6.3, 5.7, 5.2, 2.6)), 0.7, (1e-5, 0.0, 0.0)),
+             (_slab(14, 12, 13, 0.45, 0.8, (8.1, 6.4, 7.3, 3.4)), 0.9, (0.0, 2e-5, 0.0))]
+    nx, ny = 14, 12
+    nz = sum(g.nz for g, _, _ in parts)
+    solid = np.ones(nx * ny * nz, np.uint8)
+    links, rows, z0, b0 = [], [], 0, 0
+    for g, tau, gv in parts:
+        solid[nx * ny * z0:nx * ny * (z0 + g.nz)] = g.solid
+        lk = g.links.copy()
+        lk["node"] += nx * ny * z0
+        lk["body"] = np.where(lk["body"] >= 0, lk["body"] + b0, -1)
+        links.append(lk)
+        rows.append(dict(lo=z0, n=g.nz, nx=nx, tau=tau, g=gv))
+        z0 += g.nz
+        b0 += 1
+    links = np.concatenate(links)
+    with L.Lattice(None, domains=rows, stencil=1, nx=nx, ny=ny, nz=nz, periodic=(1, 1, 0), tau=1.0, bc=2,
+                   precision=precision) as lat:
+        lat.set_geometry(solid, links)
+        lat.init_equilibrium()
+        lat.step(61)
+        f = lat.distributions()
+        F = lat.forces()
+        assert lat.info().n_domains == 2
+    z0 = 0
+    for d, (g, tau, gv) in enumerate(parts):
+        with L.Lattice(g, precision=precision, tau=tau, g=gv, bc=2) as one:
+            one.init_equilibrium()
+            one.step(61)
+            f1 = one.distributions()
+            F1 = one.force(0)
+        sl = slice(nx * ny * z0, nx * ny * (z0 + g.nz))
+        assert np.array_equal(f[:, sl], f1), d
+        # the sums run in another order; small components are differences of
+        # O(max |F|) link terms
+        rtol = 1e-12 if precision == L.LBM_FP64 else 1e-5
+        assert np.allclose(F[d], F1, rtol=rtol, atol=rtol * 10 * np.abs(F1).max()), (d, F[d], F1)
+        z0 += g.nz
