@@ -57,9 +57,19 @@ __device__ __forceinline__ typename P::T collide_adjoint(const typename P::T (&f
   const T uu15 = (T)1.5 * (ux * ux + uy * uy + uz * uz);
   const T ug = ux * gx + uy * gy + uz * gz;
   T A = 0, B0 = 0, B1 = 0, B2 = 0, dtau = 0;
+  // The u-derivatives of the equilibrium and of the source, and f - feq +
+  // src/2, sum to zero over the directions (mass is conserved and the source
+  // carries no mass), so the B and dtau sums may use lambda minus its mean:
+  // the same values in exact arithmetic, without the rounding of a large
+  // common part of lambda that cancels.
+  T lbar = 0;
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) lbar += lam[i];
+  lbar *= (T)(1.0 / L::Q);
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
     const T ex = (T)L::cx(i), ey = (T)L::cy(i), ez = (T)L::cz(i);
+    const T ld = lam[i] - lbar;
     const T w = (T)L::w(i);
     const T eu = ex * ux + ey * uy + ez * uz;
     const T poly = (T)3 * eu + (T)4.5 * eu * eu - uu15;
@@ -69,11 +79,11 @@ __device__ __forceinline__ typename P::T collide_adjoint(const typename P::T (&f
     // d feq_i / d rho at fixed u, and the u-derivatives of feq_i and of the source
     A += lam[i] * w * ((T)1 + poly);
     const T c1 = omega * w * rho, c2 = ((T)1 - (T)0.5 * omega) * w;
-    B0 += lam[i] * (c1 * ((T)3 * ex + (T)9 * eu * ex - (T)3 * ux) + c2 * ((T)-3 * gx + (T)9 * ex * eg));
-    B1 += lam[i] * (c1 * ((T)3 * ey + (T)9 * eu * ey - (T)3 * uy) + c2 * ((T)-3 * gy + (T)9 * ey * eg));
-    B2 += lam[i] * (c1 * ((T)3 * ez + (T)9 * eu * ez - (T)3 * uz) + c2 * ((T)-3 * gz + (T)9 * ez * eg));
+    B0 += ld * (c1 * ((T)3 * ex + (T)9 * eu * ex - (T)3 * ux) + c2 * ((T)-3 * gx + (T)9 * ex * eg));
+    B1 += ld * (c1 * ((T)3 * ey + (T)9 * eu * ey - (T)3 * uy) + c2 * ((T)-3 * gy + (T)9 * ey * eg));
+    B2 += ld * (c1 * ((T)3 * ez + (T)9 * eu * ez - (T)3 * uz) + c2 * ((T)-3 * gz + (T)9 * ez * eg));
     // dC_i/dtau = (f_i - feq_i + src_i / 2) / tau^2
-    dtau += lam[i] * (f[i] - feq + (T)0.5 * src);
+    dtau += ld * (f[i] - feq + (T)0.5 * src);
   }
   const T ir = (T)1 / rho;
 #pragma unroll

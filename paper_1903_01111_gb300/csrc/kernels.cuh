@@ -225,13 +225,18 @@ __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Pa
   //   B  = 3 w rho (e_i.u)
   //   Sc = fpre3 w (3 (e_i.g)(e_i.u) - u.g),   So = fpre3 w (e_i.g)
   // so that f+_i,j = (1 - omega) f_i,j + (omega A + Sc) +- (omega B + So).
+  // Shifted FP32 storage relaxes in the difference form
+  // f + omega ((A +- B) - f): the non-equilibrium part f - feq is small, and
+  // rounding it rather than the two large products keeps the error on the
+  // small quantity (the reason for shifted storage); FP64 uses the product
+  // form, which needs fewer operations.
   const T fpre3 = (T)rx.fpre3;
   const T ug = ux * gx + uy * gy + uz * gz;
   const T om1 = (T)1 - omega;
   {
     const T w = (T)L::w(0);
     const T A = P::shifted ? w * (r - rho * uu15) : (w * rho) * ((T)1 - uu15);
-    T out = om1 * f[0] + omega * A;
+    T out = P::shifted ? f[0] + omega * (A - f[0]) : om1 * f[0] + omega * A;
     if (rx.has_force) out -= fpre3 * w * ug;
     fout[n_] = out;
   }
@@ -244,15 +249,29 @@ __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Pa
     const T sym = (T)4.5 * eu * eu - uu15;
     const T A = P::shifted ? w * (r + rho * sym) : (w * rho) * ((T)1 + sym);
     const T B = ((T)3 * w * rho) * eu;
-    T Pv = omega * A, Mv = omega * B;
-    if (rx.has_force) {
-      const T eg = (T)L::cx(i) * gx + (T)L::cy(i) * gy + (T)L::cz(i) * gz;
-      const T fw = fpre3 * w;
-      Pv += fw * ((T)3 * eg * eu - ug);
-      Mv += fw * eg;
+    if constexpr (P::shifted) {
+      T oi = f[i] + omega * ((A + B) - f[i]);
+      T oj = f[j] + omega * ((A - B) - f[j]);
+      if (rx.has_force) {
+        const T eg = (T)L::cx(i) * gx + (T)L::cy(i) * gy + (T)L::cz(i) * gz;
+        const T fw = fpre3 * w;
+        const T Sc = fw * ((T)3 * eg * eu - ug), So = fw * eg;
+        oi += Sc + So;
+        oj += Sc - So;
+      }
+      fout[(size_t)i * S + n_] = oi;
+      fout[(size_t)j * S + n_] = oj;
+    } else {
+      T Pv = omega * A, Mv = omega * B;
+      if (rx.has_force) {
+        const T eg = (T)L::cx(i) * gx + (T)L::cy(i) * gy + (T)L::cz(i) * gz;
+        const T fw = fpre3 * w;
+        Pv += fw * ((T)3 * eg * eu - ug);
+        Mv += fw * eg;
+      }
+      fout[(size_t)i * S + n_] = om1 * f[i] + (Pv + Mv);
+      fout[(size_t)j * S + n_] = om1 * f[j] + (Pv - Mv);
     }
-    fout[(size_t)i * S + n_] = om1 * f[i] + (Pv + Mv);
-    fout[(size_t)j * S + n_] = om1 * f[j] + (Pv - Mv);
   }
 }
 
