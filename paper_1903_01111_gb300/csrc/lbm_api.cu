@@ -407,6 +407,7 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
   }
   // node classes
   std::vector<uint8_t> m(N);
+#pragma omp parallel for schedule(static)
   for (int64_t n = 0; n < N; ++n) m[n] = solid[n] ? H_SOLID : 0;
   if (ndom > 0) {
     for (int64_t r = 0; r < rows; ++r)
@@ -464,42 +465,70 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
     }
     return x[0] + nx * (x[1] + ny * x[2]);
   };
-  // links: checks, second fluid node, cache flags
+  // links: checks, second fluid node, cache flags.  The checks run in
+  // parallel; the first failing link is reported.
   std::vector<int64_t> lk_s(n_links), lk_ff(n_links);
   std::vector<int> lk_rule(n_links);
-  bool moving = false;
-  int nbody = 1;
-  for (int64_t k = 0; k < n_links; ++k) {
+  auto check_link = [&](int64_t k, int64_t& s, int64_t& ff, int& rule) -> int {
     const lbm_link& L = links[k];
-    if (L.node < 0 || L.node >= N) return fail(LBM_ERR_INVALID_ARG, "link %lld: node out of range", (long long)k);
-    if (m[L.node] & (H_SOLID | H_OPEN))
-      return fail(LBM_ERR_INVALID_ARG, "link %lld: node %lld is not a fluid node", (long long)k, (long long)L.node);
-    if (L.dir < 1 || L.dir >= Q) return fail(LBM_ERR_INVALID_ARG, "link %lld: dir %d out of range", (long long)k, L.dir);
-    if (!(L.q > 0.0 && L.q <= 1.0)) return fail(LBM_ERR_INVALID_ARG, "link %lld: q = %g not in (0,1]", (long long)k, L.q);
-    if (L.bc < LBM_BC_DEFAULT || L.bc > LBM_BC_VIBB)
-      return fail(LBM_ERR_INVALID_ARG, "link %lld: unknown rule %d", (long long)k, L.bc);
-    if (L.body < -1 || L.body >= MAX_BODIES)
-      return fail(LBM_ERR_INVALID_ARG, "link %lld: body %d out of range", (long long)k, L.body);
-    nbody = std::max(nbody, (int)L.body + 1);
+    if (L.node < 0 || L.node >= N) return 1;
+    if (m[L.node] & (H_SOLID | H_OPEN)) return 2;
+    if (L.dir < 1 || L.dir >= Q) return 3;
+    if (!(L.q > 0.0 && L.q <= 1.0)) return 4;
+    if (L.bc < LBM_BC_DEFAULT || L.bc > LBM_BC_VIBB) return 5;
+    if (L.body < -1 || L.body >= MAX_BODIES) return 6;
     for (int a = 0; a < 3; ++a)
-      if (!std::isfinite(L.uw[a])) return fail(LBM_ERR_INVALID_ARG, "link %lld: non-finite wall velocity", (long long)k);
-    const int64_t s = neighbour(L.node, L.dir, 1);
-    if (s < 0 || !(m[s] & H_SOLID))
-      return fail(LBM_ERR_INVALID_ARG, "link %lld: neighbour of node %lld in direction %d is not a solid node",
-                  (long long)k, (long long)L.node, L.dir);
-    int64_t ff = neighbour(L.node, L.dir, -1);
+      if (!std::isfinite(L.uw[a])) return 7;
+    s = neighbour(L.node, L.dir, 1);
+    if (s < 0 || !(m[s] & H_SOLID)) return 8;
+    ff = neighbour(L.node, L.dir, -1);
     if (ff < 0 || (m[ff] & (H_SOLID | H_OPEN))) ff = L.node;  // no second fluid node: use x_f
-    const int rule = L.bc >= 0 ? L.bc : c.bc;
-    if (rule == LBM_BC_VIBB) {
-      m[L.node] |= H_CACHE;
-      m[ff] |= H_CACHE;
+    rule = L.bc >= 0 ? L.bc : c.bc;
+    return 0;
+  };
+  int64_t first_bad = n_links;
+  int nbody = 1, moving_i = 0;
+#pragma omp parallel for schedule(static) reduction(min : first_bad) reduction(max : nbody) reduction(| : moving_i)
+  for (int64_t k = 0; k < n_links; ++k) {
+    int64_t s = 0, ff = 0;
+    int rule = 0;
+    if (check_link(k, s, ff, rule)) {
+      first_bad = std::min(first_bad, k);
+      continue;
     }
-    for (int a = 0; a < D; ++a) moving |= L.uw[a] != 0.0;
+    const lbm_link& L = links[k];
+    nbody = std::max(nbody, (int)L.body + 1);
+    for (int a = 0; a < D; ++a) moving_i |= L.uw[a] != 0.0 ? 1 : 0;
     lk_s[k] = s;
     lk_ff[k] = ff;
     lk_rule[k] = rule;
   }
-  for (int64_t k = 0; k < n_links; ++k) m[lk_s[k]] |= H_GHOST;
+  if (first_bad < n_links) {
+    const int64_t k = first_bad;
+    const lbm_link& L = links[k];
+    int64_t s = 0, ff = 0;
+    int rule = 0;
+    switch (check_link(k, s, ff, rule)) {
+      case 1: return fail(LBM_ERR_INVALID_ARG, "link %lld: node out of range", (long long)k);
+      case 2: return fail(LBM_ERR_INVALID_ARG, "link %lld: node %lld is not a fluid node", (long long)k, (long long)L.node);
+      case 3: return fail(LBM_ERR_INVALID_ARG, "link %lld: dir %d out of range", (long long)k, L.dir);
+      case 4: return fail(LBM_ERR_INVALID_ARG, "link %lld: q = %g not in (0,1]", (long long)k, L.q);
+      case 5: return fail(LBM_ERR_INVALID_ARG, "link %lld: unknown rule %d", (long long)k, L.bc);
+      case 6: return fail(LBM_ERR_INVALID_ARG, "link %lld: body %d out of range", (long long)k, L.body);
+      case 7: return fail(LBM_ERR_INVALID_ARG, "link %lld: non-finite wall velocity", (long long)k);
+      default:
+        return fail(LBM_ERR_INVALID_ARG, "link %lld: neighbour of node %lld in direction %d is not a solid node",
+                    (long long)k, (long long)L.node, L.dir);
+    }
+  }
+  const bool moving = moving_i != 0;
+  for (int64_t k = 0; k < n_links; ++k) {
+    if (lk_rule[k] == LBM_BC_VIBB) {
+      m[links[k].node] |= H_CACHE;
+      m[lk_ff[k]] |= H_CACHE;
+    }
+    m[lk_s[k]] |= H_GHOST;
+  }
   // open inlet reads the moments of the first fluid column
   if (c.inlet)
     for (int64_t y = 0; y < ny; ++y)
@@ -535,6 +564,7 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
   }
   // completeness: count (fluid node, dir) pairs with a solid neighbour
   int64_t expected = 0, n_fluid = 0;
+#pragma omp parallel for schedule(static) reduction(+ : expected, n_fluid)
   for (int64_t n = 0; n < N; ++n) {
     if (m[n] & (H_SOLID | H_OPEN)) continue;
     ++n_fluid;
@@ -567,6 +597,7 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
     }
   const int64_t S = (int64_t)node_of.size();
   std::vector<int32_t> row_first(rows, -1), row_last(rows, -1);
+#pragma omp parallel for schedule(static)
   for (int64_t r = 0; r < rows; ++r)
     for (int64_t x = 0; x < nx; ++x) {
       const int32_t k = sidx[x + nx * r];
@@ -592,12 +623,16 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
     slot_dxhi[sl] = std::max(slot_dxhi[sl], dx);
     nslots = std::max(nslots, sl + 1);
   }
-  // fluid runs and their neighbour-row bases
-  std::vector<RunRec> runs;
-  std::vector<uint32_t> word(S, 0);
-  for (int64_t r = 0; r < rows; ++r) {
+  // fluid runs and their neighbour-row bases, row by row in parallel: count
+  // the runs of every row and check that the pulled part of each neighbour
+  // row is stored and contiguous (x0 + min dx .. x_end + max dx, inside the
+  // row), then fill the records with their global run ids.
+  std::vector<int64_t> row_runs(rows + 1, 0);
+  // walks row r; out == nullptr: count and check (returns false and the run
+  // at fault on a contiguity error); else write records from run id rid0
+  auto walk_row = [&](int64_t r, RunRec* out, uint32_t rid0, uint32_t* word_out, int64_t* bad) -> bool {
     const int64_t y = r % ny, z = r / ny;
-    int64_t x = 0;
+    int64_t x = 0, count = 0;
     while (x < nx) {
       const int64_t n = x + nx * r;
       if (m[n] & (H_SOLID | H_OPEN)) {
@@ -615,27 +650,54 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
         const int64_t yy = (y + slot_dy[sl] + ny) % ny, zz = (z + slot_dz[sl] + nz) % nz;
         const int64_t rr = yy + ny * zz;
         const int32_t base = sidx[x + nx * rr];
-        // the pull addressing needs the pulled part of row' stored and
-        // contiguous: x0 + min dx .. x_end + max dx (inside the row)
-        for (int64_t xx = std::max<int64_t>(x + slot_dxlo[sl], 0); xx <= std::min<int64_t>(xe + slot_dxhi[sl], nx - 1);
-             ++xx)
-          if (base < 0 || sidx[xx + nx * rr] != base + (int32_t)(xx - x))
-            return fail(LBM_ERR_INVALID_ARG,
-                        "layout: neighbour row of the fluid run at (%lld..%lld, %lld, %lld) is not fully stored",
-                        (long long)x, (long long)xe, (long long)y, (long long)z);
+        if (!out)
+          for (int64_t xx = std::max<int64_t>(x + slot_dxlo[sl], 0);
+               xx <= std::min<int64_t>(xe + slot_dxhi[sl], nx - 1); ++xx)
+            if (base < 0 || sidx[xx + nx * rr] != base + (int32_t)(xx - x)) {
+              bad[0] = x;
+              bad[1] = xe;
+              return false;
+            }
         rec.dbase[sl] = base - sidx[n];
       }
-      const uint32_t rid = (uint32_t)runs.size();
-      if (rid > W_RUN) return fail(LBM_ERR_UNSUPPORTED, "too many fluid runs");
-      for (int64_t xx = x; xx <= xe; ++xx) {
-        const int64_t nn = xx + nx * r;
-        word[sidx[nn]] = rid | ((m[nn] & H_CACHE) ? W_CACHE : 0u);
+      if (out) {
+        const uint32_t rid = rid0 + (uint32_t)count;
+        for (int64_t xx = x; xx <= xe; ++xx) {
+          const int64_t nn = xx + nx * r;
+          word_out[sidx[nn]] = rid | ((m[nn] & H_CACHE) ? W_CACHE : 0u);
+        }
+        out[count] = rec;
       }
-      runs.push_back(rec);
+      ++count;
       x = xe + 1;
     }
+    if (!out) row_runs[r + 1] = count;
+    return true;
+  };
+  int64_t bad_row = rows;
+#pragma omp parallel for schedule(dynamic, 64) reduction(min : bad_row)
+  for (int64_t r = 0; r < rows; ++r) {
+    int64_t bad[2];
+    if (!walk_row(r, nullptr, 0, nullptr, bad)) bad_row = std::min(bad_row, r);
+  }
+  if (bad_row < rows) {
+    int64_t bad[2] = {0, 0};
+    walk_row(bad_row, nullptr, 0, nullptr, bad);
+    return fail(LBM_ERR_INVALID_ARG,
+                "layout: neighbour row of the fluid run at (%lld..%lld, %lld, %lld) is not fully stored",
+                (long long)bad[0], (long long)bad[1], (long long)(bad_row % ny), (long long)(bad_row / ny));
+  }
+  for (int64_t r = 0; r < rows; ++r) row_runs[r + 1] += row_runs[r];
+  if (row_runs[rows] > (int64_t)W_RUN + 1) return fail(LBM_ERR_UNSUPPORTED, "too many fluid runs");
+  std::vector<RunRec> runs((size_t)row_runs[rows]);
+  std::vector<uint32_t> word(S, 0);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t r = 0; r < rows; ++r) {
+    int64_t bad[2];
+    walk_row(r, runs.data() + row_runs[r], (uint32_t)row_runs[r], word.data(), bad);
   }
   int64_t n_cached = 0;
+#pragma omp parallel for schedule(static) reduction(+ : n_cached)
   for (int64_t n = 0; n < N; ++n) {
     if (sidx[n] < 0) continue;
     if (m[n] & H_OPEN)
@@ -661,6 +723,7 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
   std::vector<LinkRec> recs(n_links);
   std::vector<double> qs(n_links);
   std::vector<double> uws(moving ? (size_t)D * n_links : 0);
+#pragma omp parallel for schedule(static)
   for (int64_t j = 0; j < n_links; ++j) {
     const int64_t k = order[j];
     const lbm_link& L = links[k];
