@@ -522,11 +522,15 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
     }
   }
   const bool moving = moving_i != 0;
+#pragma omp parallel for schedule(static)
   for (int64_t k = 0; k < n_links; ++k) {
     if (lk_rule[k] == LBM_BC_VIBB) {
+#pragma omp atomic
       m[links[k].node] |= H_CACHE;
+#pragma omp atomic
       m[lk_ff[k]] |= H_CACHE;
     }
+#pragma omp atomic
     m[lk_s[k]] |= H_GHOST;
   }
   // open inlet reads the moments of the first fluid column
@@ -542,18 +546,23 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
   std::vector<int64_t> order(n_links);
   for (int64_t k = 0; k < n_links; ++k) order[k] = k;
   auto nodedir = [&](int64_t k) { return (uint64_t)links[k].node * 32 + (uint64_t)links[k].dir; };
-  bool sorted = true;
-  for (int64_t k = 1; k < n_links && sorted; ++k) sorted = nodedir(k - 1) < nodedir(k);
+  int64_t unsorted = 0;
+#pragma omp parallel for schedule(static) reduction(+ : unsorted)
+  for (int64_t k = 1; k < n_links; ++k) unsorted += nodedir(k - 1) < nodedir(k) ? 0 : 1;
+  const bool sorted = unsorted == 0;
   if (!sorted) {
     std::vector<std::pair<uint64_t, int64_t>> tmp(n_links);
     for (int64_t k = 0; k < n_links; ++k) tmp[k] = {nodedir(k), k};
     std::sort(tmp.begin(), tmp.end());
     for (int64_t k = 0; k < n_links; ++k) order[k] = tmp[k].second;
   }
+  int64_t first_dup = n_links;
+#pragma omp parallel for schedule(static) reduction(min : first_dup)
   for (int64_t k = 1; k < n_links; ++k)
-    if (nodedir(order[k]) == nodedir(order[k - 1]))
-      return fail(LBM_ERR_INVALID_ARG, "duplicate link at node %lld direction %d",
-                  (long long)(nodedir(order[k]) / 32), (int)(nodedir(order[k]) % 32));
+    if (nodedir(order[k]) == nodedir(order[k - 1])) first_dup = std::min(first_dup, k);
+  if (first_dup < n_links)
+    return fail(LBM_ERR_INVALID_ARG, "duplicate link at node %lld direction %d",
+                (long long)(nodedir(order[first_dup]) / 32), (int)(nodedir(order[first_dup]) % 32));
   {
     std::vector<int64_t> count(nbody + 2, 0);
     for (int64_t k = 0; k < n_links; ++k) count[links[k].body + 2]++;
@@ -587,15 +596,29 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
                 (long long)expected, (long long)n_links);
 
   // ---- compacted layout: stored = fluid, open and ghost nodes, in row order
+  // storage indices in node order: per-chunk counts, prefix sums, fill
+  auto stored = [&](int64_t n) { return !(m[n] & H_SOLID) || (m[n] & H_GHOST); };
+  const int64_t nchunk = std::max<int64_t>(1, std::min<int64_t>(1024, N / 65536));
+  std::vector<int64_t> chunk_start(nchunk + 1, 0);
+#pragma omp parallel for schedule(static)
+  for (int64_t ch = 0; ch < nchunk; ++ch) {
+    int64_t cnt = 0;
+    for (int64_t n = N * ch / nchunk; n < N * (ch + 1) / nchunk; ++n) cnt += stored(n) ? 1 : 0;
+    chunk_start[ch + 1] = cnt;
+  }
+  for (int64_t ch = 0; ch < nchunk; ++ch) chunk_start[ch + 1] += chunk_start[ch];
+  const int64_t S = chunk_start[nchunk];
   std::vector<int32_t> sidx(N, -1);
-  std::vector<int32_t> node_of;
-  node_of.reserve((size_t)n_fluid + (size_t)n_links + 64);
-  for (int64_t n = 0; n < N; ++n)
-    if (!(m[n] & H_SOLID) || (m[n] & H_GHOST)) {
-      sidx[n] = (int32_t)node_of.size();
-      node_of.push_back((int32_t)n);
-    }
-  const int64_t S = (int64_t)node_of.size();
+  std::vector<int32_t> node_of((size_t)S);
+#pragma omp parallel for schedule(static)
+  for (int64_t ch = 0; ch < nchunk; ++ch) {
+    int64_t k = chunk_start[ch];
+    for (int64_t n = N * ch / nchunk; n < N * (ch + 1) / nchunk; ++n)
+      if (stored(n)) {
+        sidx[n] = (int32_t)k;
+        node_of[k++] = (int32_t)n;
+      }
+  }
   std::vector<int32_t> row_first(rows, -1), row_last(rows, -1);
 #pragma omp parallel for schedule(static)
   for (int64_t r = 0; r < rows; ++r)
