@@ -405,6 +405,24 @@ def sphere_pack(n=384, porosity=0.40, rmin=6.0, rmax=14.0, seed=0, batch=4096) -
                     dict(kind="sphere_pack", porosity=1.0 - solid.value / N, spheres=len(radii), seed=seed))
 
 
+def translated(geo: Geometry, shift) -> Geometry:
+    """The same geometry moved by an integer shift (sx, sy, sz) along its
+    periodic axes: the mask is rolled and every link keeps its direction, q
+    and wall velocity at the moved node (no ray casting, so the link data are
+    bit for bit those of ``geo``)."""
+    sh = [int(v) for v in shift] + [0] * (3 - len(shift))
+    for a in range(3):
+        if sh[a] and not geo.periodic[a]:
+            raise ValueError(f"axis {a} is not periodic")
+    solid = np.roll(geo.solid.reshape(geo.nz, geo.ny, geo.nx), (sh[2], sh[1], sh[0]), axis=(0, 1, 2)).reshape(-1)
+    x, y, z = geo.coords(geo.links["node"])
+    links = geo.links.copy()
+    links["node"] = (x + sh[0]) % geo.nx + geo.nx * (((y + sh[1]) % geo.ny) + geo.ny * ((z + sh[2]) % geo.nz))
+    order = np.lexsort((links["dir"], links["node"]))
+    return Geometry(geo.stencil, geo.nx, geo.ny, geo.nz, geo.periodic, solid, links[order], geo.open_x, geo.bodies,
+                    dict(geo.info, shift=tuple(sh)))
+
+
 def ball_q_derivatives(geo: Geometry, body_index: int) -> np.ndarray:
     """Derivatives of q with respect to (c_x, c_y, c_z, R) of ball
     ``geo.bodies[body_index]`` for every link whose wall crossing lies on that

@@ -643,3 +643,40 @@ def test_dual_gradient_matches_finite_differences(bc, vd):
         fd[k] = (8 * (vals[1] - vals[2]) - (vals[0] - vals[3])) / (12 * h)
     err = np.abs(dF[0, 0] - fd)
     assert np.all(err <= 1e-5 * np.abs(fd) + 1e-9 * np.abs(fd).max()), (dF[0, 0], fd)
+
+
+def _node_map(geo, shift):
+    x, y, z = geo.coords(np.arange(geo.N))
+    sx, sy, sz = (list(shift) + [0, 0])[:3]
+    return (x + sx) % geo.nx + geo.nx * (((y + sy) % geo.ny) + geo.ny * ((z + sz) % geo.nz))
+
+
+def test_poiseuille_columns_are_identical():
+    """Translation invariance along the periodic x axis of the channel: after
+    200 steps every column holds the same populations, bit for bit."""
+    g = G.channel(0, 32, 24, q_lo=0.3, q_hi=0.3)
+    cfg = _cfg_for(g, tau=0.8, g=(1e-6, 0, 0), bc=2)
+    st = O.init(cfg, g.solid)
+    O.run(cfg, g.solid, g.links, st, 200)
+    f = st.fp.reshape(9, g.ny, g.nx)
+    assert np.array_equal(f, np.repeat(f[:, :, :1], g.nx, axis=2))
+
+
+@pytest.mark.parametrize("stencil", [0, 1])
+@pytest.mark.parametrize("bc", [0, 1, 2])
+def test_translated_geometry_gives_translated_state(stencil, bc):
+    """An integer shift of a periodic geometry (mask and links moved, q kept)
+    moves the state by the same shift, bit for bit."""
+    g = _small_cylinder(stencil=stencil)
+    shift = (5, 3, 0) if stencil == 0 else (5, 3, 2)
+    gs = G.translated(g, shift)
+    cfg = _cfg_for(g, tau=0.7, g=(1e-5, 2e-6, 0), bc=bc)
+    st = O.init(cfg, g.solid)
+    F = O.run(cfg, g.solid, g.links, st, 40)
+    sts = O.init(cfg, gs.solid)
+    Fs = O.run(cfg, gs.solid, gs.links, sts, 40)
+    mp = _node_map(g, shift)
+    assert np.array_equal(sts.fp[:, mp], st.fp)
+    # the force sums run over the links in another order: terms of O(0.1)
+    # (unshifted populations), so a few ulps of 0.1 per link
+    assert np.allclose(Fs, F, rtol=1e-13, atol=1e-14 * len(g.links))
