@@ -132,16 +132,18 @@ AUTOTUNE = True  # --tuning default: the stencil's default shapes (reproducible 
 
 
 BULK_SHAPE = -1  # --bulk-shape: force one bulk kernel shape (profiling a given kernel)
+LINK_SEQ = 0     # --link-seq: force the link kernel's links per thread
 
 
 def _tune(lat, steps_per_trial):
     """The lattice's launch shapes: autotuned on its live state, the
-    defaults, or the forced bulk shape (where the stencil has it)."""
-    if BULK_SHAPE >= 0:
+    defaults, or the forced bulk shape / links per thread (where the stencil
+    has them)."""
+    if BULK_SHAPE >= 0 or LINK_SEQ:
         try:
-            lat.set_tuning(bulk_shape=BULK_SHAPE)
+            lat.set_tuning(bulk_shape=BULK_SHAPE, link_seq=LINK_SEQ or 1)
         except Exception:
-            pass
+            lat.set_tuning(bulk_shape=-1, link_seq=LINK_SEQ or 1)
         return lat.tuning()
     if AUTOTUNE:
         return lat.autotune(steps_per_trial)[0]
@@ -622,10 +624,13 @@ def main():
                     help="autotune every timed lattice (default) or keep the default launch shapes")
     ap.add_argument("--bulk-shape", type=int, default=-1,
                     help="force this bulk kernel shape where the stencil has it (profiling)")
+    ap.add_argument("--link-seq", type=int, default=0, choices=[0, 1, 4],
+                    help="force the link kernel's links per thread (profiling)")
     args = ap.parse_args()
-    global AUTOTUNE, BULK_SHAPE
+    global AUTOTUNE, BULK_SHAPE, LINK_SEQ
     AUTOTUNE = args.tuning == "auto"
     BULK_SHAPE = args.bulk_shape
+    LINK_SEQ = args.link_seq
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

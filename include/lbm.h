@@ -162,12 +162,16 @@ typedef struct {
  *  link_threads   64, 128 or 256 threads per block of the link kernel.
  *  graph_steps    time steps per CUDA graph replayed by lbm_step (even,
  *                 2..64).
+ *  link_seq       links per thread of the link kernel, 1 or 4 (a block
+ *                 takes link_seq rounds of consecutive links, loading the
+ *                 next round's record while it evaluates the current one);
+ *                 0 on input means 1.
  * Shapes of the same kernel (same nodes per thread in parallel and in
  * sequence) give the same bits (force sums may differ in the last place, as
  * FP64 atomics are unordered); the kernels are separate compilations of the
  * same arithmetic and agree to rounding. */
 typedef struct {
-  int32_t bulk_shape, link_threads, graph_steps, reserved;
+  int32_t bulk_shape, link_threads, graph_steps, link_seq;
 } lbm_tuning;
 
 /* Create a lattice: validates cfg, allocates the device state (two
@@ -332,7 +336,7 @@ lbm_status lbm_set_tuning(lbm_handle h, const lbm_tuning* t);
 lbm_status lbm_get_tuning(lbm_handle h, lbm_tuning* t);
 
 /* Autotuner: times the bulk shapes (with 256-thread link blocks), then the
- * link block sizes, then the graph lengths, each over steps_per_trial steps
+ * link block sizes, then 4 links per thread, then the graph lengths, each over steps_per_trial steps
  * (>= 2) from the current state after one untimed warm-up replay, and keeps
  * the fastest.  The state, the step counter and the force of the last step
  * are restored afterwards (a scratch copy of one state is allocated for the

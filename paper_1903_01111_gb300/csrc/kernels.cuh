@@ -576,7 +576,7 @@ __device__ __forceinline__ typename P::T link_value(int rule, typename P::T q, t
 //             q >  1/2: (f+_i'(x_f) + wall)/(2q) + (2q-1)/(2q) f+_i(x_f)  (Eq. q_larger)
 //   VIBB      feq_i'(rho_d, u_d) + fneq_i'(x_d) + wall                 (Sec. 3.1)
 // with wall = 6 w rho0 (e_i . u_w).
-template <class L, class P>
+template <class L, class P, int SEQ>
 __global__ void __launch_bounds__(256) k_links(typename P::T* __restrict__ f, const Mom4<typename P::T>* __restrict__ mom,
                                                const LinkRec* __restrict__ recs, const typename P::T* __restrict__ qv,
                                                const typename P::T* __restrict__ uwv, int64_t nl,
@@ -593,70 +593,87 @@ __global__ void __launch_bounds__(256) k_links(typename P::T* __restrict__ f, co
     tab.e[d][2] = (T)L::cz(d);
   }
   __syncthreads();
-  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  // lane and warp partial sums in the storage precision (FP32 sums of the
-  // small shifted terms), block sums and the accumulator in FP64
+  // the block takes SEQ rounds of blockDim consecutive links; the next
+  // round's record and q are loaded while the current link is processed
+  const int64_t base = (int64_t)blockIdx.x * blockDim.x * SEQ;
+  // body of the block's first link: the block's links of that body are
+  // summed per lane (storage precision), per warp and per block (FP64);
+  // links of any other body (a body boundary inside the block) add their
+  // terms with FP64 atomics directly
+  const int b0 = (int)(__ldg(&recs[base].meta) >> 7) - 1;
+  const size_t N = (size_t)S_;
   T F0 = 0, F1 = 0, F2 = 0;
-  int body = -1;
-  if (k < nl) {
-    const LinkRec rec = recs[k];
-    const int ip = (int)(rec.meta & 31);
-    const int rule = (int)((rec.meta >> 5) & 3);
-    body = (int)(rec.meta >> 7) - 1;
-    const uint32_t node = rec.kf, ff = rec.kff, s = rec.ks;
-    const int i = tab.opp[ip];
-    const T ex = tab.e[ip][0], ey = tab.e[ip][1], ez = tab.e[ip][2];
-    const T w = tab.w[ip];
-    const size_t N = (size_t)S_;
-    const T q = qv[k];
-    T uw0 = 0, uw1 = 0, uw2 = 0;
-    if (uwv) {
-      uw0 = uwv[k];
-      uw1 = uwv[nl + k];
-      if (L::D == 3) uw2 = uwv[2 * nl + k];
-    }
-    const T fpf = f[(size_t)ip * N + node];
-    T fpff = 0, fpi = 0;
-    Mom4<T> mf{0, 0, 0, 0}, mff{0, 0, 0, 0};
-    if (rule == 1) {
-      if (q <= (T)0.5)
-        fpff = f[(size_t)ip * N + ff];
-      else
-        fpi = f[(size_t)i * N + node];
-    } else if (rule == 2) {
-      fpff = f[(size_t)ip * N + ff];
-      mf = mom[node];
-      mff = mom[ff];
-    }
-    const T val = link_value<P>(rule, q, w, ex, ey, ez, fpf, fpff, fpi, mf, mff, uw0, uw1, uw2, p.rho0,
-                                p.vibb_local_rho);
-    f[(size_t)i * N + s] = val;
-    if (body >= 0) {
-      // momentum exchange (f+_i'(x_f,t) + f_i(x_f,t+1)) e_i'.  In shifted
-      // storage this sums (h+_i' + h_i) e_i'; the rest part 2 w_i' rho0 e_i'
-      // of every link is a geometric constant that the host adds in FP64.
-      const T t = fpf + val;
-      F0 = t * ex;
-      F1 = t * ey;
-      F2 = t * ez;
-    }
+  int64_t k = base + threadIdx.x;
+  bool live = k < nl;
+  LinkRec rec{0, 0, 0, 0};
+  T q = 0;
+  if (live) {
+    rec = recs[k];
+    q = qv[k];
   }
-  // block reduction: one atomic per component when the block has one body
-  __shared__ double red[3][32];
-  __shared__ int b_first;
-  if (threadIdx.x == 0) b_first = body;
-  __syncthreads();
-  const int b0 = b_first;
-  const int uniform = __syncthreads_and(body == b0 || body < 0);
-  if (!uniform) {
-    if (body >= 0) {
-      atomicAdd(&force[3 * body + 0], (double)F0);
-      atomicAdd(&force[3 * body + 1], (double)F1);
-      atomicAdd(&force[3 * body + 2], (double)F2);
+#pragma unroll 1
+  for (int r = 0; r < SEQ; ++r) {
+    const int64_t kn = k + blockDim.x;
+    const bool liven = (r + 1 < SEQ) && kn < nl;
+    LinkRec recn{0, 0, 0, 0};
+    T qn = 0;
+    if (liven) {
+      recn = recs[kn];
+      qn = qv[kn];
     }
-    return;
+    if (live) {
+      const int ip = (int)(rec.meta & 31);
+      const int rule = (int)((rec.meta >> 5) & 3);
+      const int body = (int)(rec.meta >> 7) - 1;
+      const uint32_t node = rec.kf, ff = rec.kff, s = rec.ks;
+      const int i = tab.opp[ip];
+      const T ex = tab.e[ip][0], ey = tab.e[ip][1], ez = tab.e[ip][2];
+      const T w = tab.w[ip];
+      T uw0 = 0, uw1 = 0, uw2 = 0;
+      if (uwv) {
+        uw0 = uwv[k];
+        uw1 = uwv[nl + k];
+        if (L::D == 3) uw2 = uwv[2 * nl + k];
+      }
+      const T fpf = f[(size_t)ip * N + node];
+      T fpff = 0, fpi = 0;
+      Mom4<T> mf{0, 0, 0, 0}, mff{0, 0, 0, 0};
+      if (rule == 1) {
+        if (q <= (T)0.5)
+          fpff = f[(size_t)ip * N + ff];
+        else
+          fpi = f[(size_t)i * N + node];
+      } else if (rule == 2) {
+        fpff = f[(size_t)ip * N + ff];
+        mf = mom[node];
+        mff = mom[ff];
+      }
+      const T val = link_value<P>(rule, q, w, ex, ey, ez, fpf, fpff, fpi, mf, mff, uw0, uw1, uw2, p.rho0,
+                                  p.vibb_local_rho);
+      f[(size_t)i * N + s] = val;
+      if (body >= 0) {
+        // momentum exchange (f+_i'(x_f,t) + f_i(x_f,t+1)) e_i'.  In shifted
+        // storage this sums (h+_i' + h_i) e_i'; the rest part 2 w_i' rho0 e_i'
+        // of every link is a geometric constant that the host adds in FP64.
+        const T t = fpf + val;
+        if (body == b0) {
+          F0 += t * ex;
+          F1 += t * ey;
+          F2 += t * ez;
+        } else {
+          atomicAdd(&force[3 * body + 0], (double)(t * ex));
+          atomicAdd(&force[3 * body + 1], (double)(t * ey));
+          atomicAdd(&force[3 * body + 2], (double)(t * ez));
+        }
+      }
+    }
+    k = kn;
+    rec = recn;
+    q = qn;
+    live = liven;
   }
   if (b0 < 0) return;
+  __shared__ double red[3][32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     F0 += __shfl_down_sync(0xffffffffu, F0, o);
@@ -677,6 +694,7 @@ __global__ void __launch_bounds__(256) k_links(typename P::T* __restrict__ f, co
     atomicAdd(&force[3 * b0 + threadIdx.x], acc);
   }
 }
+
 
 // ------------------------------------------------------------ open sides --
 
@@ -887,11 +905,12 @@ struct KernelOps {
   size_t real_bytes;
   int default_shape;
   unsigned shape_mask;  // bit b: kBulkShapes[b] is built for this stencil
-  // shape: index into kBulkShapes; threads: link kernel block size (64, 128 or 256)
+  // shape: index into kBulkShapes; threads: link kernel block size (64, 128 or
+  // 256); seq: links per thread of the link kernel (1 or 4)
   void (*bulk)(const void* fin, void* fout, const Layout& lay, void* mom, double* force_next, const Params& p,
                int shape, cudaStream_t s);
   void (*links)(void* f, const void* mom, const LinkRec* recs, const void* q, const void* uw, int64_t nl,
-                double* force, const Params& p, int64_t S, int threads, cudaStream_t s);
+                double* force, const Params& p, int64_t S, int threads, int seq, cudaStream_t s);
   void (*open)(void* f, const void* mom, const Layout& lay, const Params& p, cudaStream_t s);
   void (*init)(void* f, void* mom, const Layout& lay, const double* rho, const double* u, const Params& p,
                cudaStream_t s);
@@ -950,11 +969,15 @@ struct Launch {
       bulk_m<false>(fin, fout, lay, mom, force_next, p, shape, s);
   }
   static void links(void* f, const void* mom, const LinkRec* recs, const void* q, const void* uw, int64_t nl,
-                    double* force, const Params& p, int64_t S, int threads, cudaStream_t s) {
+                    double* force, const Params& p, int64_t S, int threads, int seq, cudaStream_t s) {
     if (nl == 0) return;
     const int bt = (threads == 64 || threads == 128) ? threads : 256;
-    k_links<L, P><<<blocks_for(nl, bt), bt, 0, s>>>((T*)f, (const Mom4<T>*)mom, recs, (const T*)q, (const T*)uw, nl,
-                                                   force, p, S);
+    if (seq == 4)
+      k_links<L, P, 4><<<blocks_for(nl, 4 * bt), bt, 0, s>>>((T*)f, (const Mom4<T>*)mom, recs, (const T*)q,
+                                                             (const T*)uw, nl, force, p, S);
+    else
+      k_links<L, P, 1><<<blocks_for(nl, bt), bt, 0, s>>>((T*)f, (const Mom4<T>*)mom, recs, (const T*)q,
+                                                         (const T*)uw, nl, force, p, S);
   }
   static void open(void* f, const void* mom, const Layout& lay, const Params& p, cudaStream_t s) {
     k_open<L, P><<<blocks_for(p.ny, 128), 128, 0, s>>>((T*)f, (const Mom4<T>*)mom, lay, p);

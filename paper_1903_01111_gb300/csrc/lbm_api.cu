@@ -75,7 +75,7 @@ struct lbm_lattice_s {
   std::vector<lbm_domain> domains;
   DeviceBuf dom, row_dom;
   int nbody = 1;  // force accumulators per slot
-  lbm_tuning tune{-1, 256, 2, 0};
+  lbm_tuning tune{-1, 256, 2, 1};
   std::vector<int32_t> sidx;  // dense -> storage index (-1: not stored), host
   // links
   DeviceBuf recs, q, uw;
@@ -194,7 +194,7 @@ lbm_status enqueue_step_buf(lbm_handle h, void* fc, void* fn, double* slot, doub
   lbm_status st;
   st = timed_launch(0, [&] {
     h->ops.links(fc, h->mom.p, (const LinkRec*)h->recs.p, h->q.p, h->uw.p, h->n_links, slot, h->p, h->lay.S,
-                 h->tune.link_threads, h->stream);
+                 h->tune.link_threads, h->tune.link_seq, h->stream);
   });
   if (st != LBM_OK) return st;
   if (h->p.inlet || h->p.outlet) {
@@ -1213,7 +1213,7 @@ lbm_status lbm_adjoint_step(lbm_handle h, int32_t body, const double dJ_dF[3], i
         // the last state of the segment has no link values yet
         h->ops.refresh(state, h->lay, h->mom.p, h->p, h->stream);
         h->ops.links(state, h->mom.p, (const LinkRec*)h->recs.p, h->q.p, h->uw.p, nl, fslot, h->p, S,
-                     h->tune.link_threads, h->stream);
+                     h->tune.link_threads, h->tune.link_seq, h->stream);
         if (open) h->ops.open(state, h->mom.p, h->lay, h->p, h->stream);
       }
       h->adj.bulk(state, lam[l].p, lam[l ^ 1].p, h->lay, h->p, dtau, h->mom.p, h->stream);
@@ -1338,9 +1338,10 @@ lbm_status lbm_set_tuning(lbm_handle h, const lbm_tuning* t) {
     return fail(LBM_ERR_INVALID_ARG, "link_threads must be 64, 128 or 256");
   if (v.graph_steps < 2 || v.graph_steps > 64 || (v.graph_steps & 1))
     return fail(LBM_ERR_INVALID_ARG, "graph_steps must be even and in 2..64");
-  v.reserved = 0;
+  if (v.link_seq == 0) v.link_seq = 1;
+  if (v.link_seq != 1 && v.link_seq != 4) return fail(LBM_ERR_INVALID_ARG, "link_seq must be 1 or 4");
   if (v.bulk_shape != h->tune.bulk_shape || v.link_threads != h->tune.link_threads ||
-      v.graph_steps != h->tune.graph_steps) {
+      v.graph_steps != h->tune.graph_steps || v.link_seq != h->tune.link_seq) {
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     drop_graphs(h);
   }
@@ -1423,7 +1424,7 @@ lbm_status lbm_autotune(lbm_handle h, int32_t steps_per_trial, lbm_tuning* best,
     *ms = bestms;
     return LBM_OK;
   };
-  lbm_tuning cand{h->ops.default_shape, 256, 8, 0}, chosen = cand;
+  lbm_tuning cand{h->ops.default_shape, 256, 8, 1}, chosen = cand;
   double chosen_ms = 1e300;
   auto consider = [&](const lbm_tuning& t) -> lbm_status {
     double ms = 0.0;
@@ -1443,6 +1444,11 @@ lbm_status lbm_autotune(lbm_handle h, int32_t steps_per_trial, lbm_tuning* best,
   for (int k = 0; k < 2 && st == LBM_OK; ++k) {
     cand = chosen;
     cand.link_threads = link_opts[k];
+    st = consider(cand);
+  }
+  if (st == LBM_OK) {
+    cand = chosen;
+    cand.link_seq = 4;
     st = consider(cand);
   }
   const int graph_opts[] = {2, 32};

@@ -153,14 +153,14 @@ def test_launch_shapes(L, prec, stencil):
     ref = {}
     for shape in _shapes(L, stencil):
         npt = L.BULK_SHAPES[shape][1:]
-        for lt, gs in ((256, 2), (64, 8), (128, 32)):
+        for lt, gs, ls in ((256, 2, 1), (64, 8, 4), (128, 32, 4)):
             with L.Lattice(geo, precision=precision, bc=2, tau=0.7, g=(1e-5, 0, 0)) as lat:
-                lat.set_tuning(bulk_shape=shape, link_threads=lt, graph_steps=gs)
+                lat.set_tuning(bulk_shape=shape, link_threads=lt, graph_steps=gs, link_seq=ls)
                 lat.init_equilibrium()
                 lat.step(37)
                 f = lat.distributions()
             ref.setdefault(npt, f)
-            assert np.array_equal(f, ref[npt]), (shape, lt, gs)
+            assert np.array_equal(f, ref[npt]), (shape, lt, gs, ls)
     _, w = O.velocity_set(stencil)
     base = ref[(1, 1)]
     h = np.abs(base - (w[:, None] if precision == L.LBM_FP32_SHIFTED else 0.0)).max()
@@ -178,6 +178,7 @@ def test_autotune_restores_state_and_picks_a_valid_shape(L):
     f0 = lat.distributions()
     t, ms = lat.autotune(10)
     assert ms > 0 and 0 <= t.bulk_shape < 8 and t.link_threads in (64, 128, 256) and t.graph_steps % 2 == 0
+    assert t.link_seq in (1, 4)
     assert lat.tuning().bulk_shape == t.bulk_shape
     assert lat.info().step == 9
     assert np.array_equal(lat.distributions(), f0)
@@ -186,7 +187,7 @@ def test_autotune_restores_state_and_picks_a_valid_shape(L):
     f1 = lat.distributions()
     lat.close()
     lat2 = _batch_lattice(L, b, L.LBM_FP32_SHIFTED)
-    lat2.set_tuning(bulk_shape=t.bulk_shape, link_threads=256, graph_steps=2)
+    lat2.set_tuning(bulk_shape=t.bulk_shape, link_threads=256, graph_steps=2, link_seq=1)
     lat2.step(29)
     assert np.array_equal(lat2.distributions(), f1)
     lat2.close()
