@@ -218,50 +218,51 @@ __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Pa
     }
   }
   // BGK with the Guo source (1 - 1/(2 tau)) w_i [3 (e_i - u).g + 9 (e_i.u)(e_i.g)]
-  //   = 3 (1 - 1/(2 tau)) w_i [(e_i.g)(1 + 3 e_i.u) - u.g],
-  // evaluated per pair of opposite directions (i, j = opp(i)): e_j = -e_i
-  // turns the equilibria into A +- B and the sources into Sc +- So with
-  //   A  = w (r + rho (4.5 (e_i.u)^2 - 1.5 u.u))   (FP64: w rho (1 + ...))
-  //   B  = 3 w rho (e_i.u)
-  //   Sc = fpre3 w (3 (e_i.g)(e_i.u) - u.g),   So = fpre3 w (e_i.g)
-  // so that f+_i,j = (1 - omega) f_i,j + (omega A + Sc) +- (omega B + So).
-  // Shifted FP32 storage relaxes in the difference form
-  // f + omega ((A +- B) - f): the non-equilibrium part f - feq is small, and
-  // rounding it rather than the two large products keeps the error on the
-  // small quantity (the reason for shifted storage); FP64 uses the product
-  // form, which needs fewer operations.
+  //   = 3 (1 - 1/(2 tau)) w_i [(e_i.g)(1 + 3 e_i.u) - u.g].
   const T fpre3 = (T)rx.fpre3;
   const T ug = ux * gx + uy * gy + uz * gz;
-  const T om1 = (T)1 - omega;
-  {
-    const T w = (T)L::w(0);
-    const T A = P::shifted ? w * (r - rho * uu15) : (w * rho) * ((T)1 - uu15);
-    T out = P::shifted ? f[0] + omega * (A - f[0]) : om1 * f[0] + omega * A;
-    if (rx.has_force) out -= fpre3 * w * ug;
-    fout[n_] = out;
-  }
+  if constexpr (P::shifted) {
+    // Shifted FP32 storage: one direction at a time, relaxing in the
+    // difference form f + omega (feq - f) so that rounding falls on the small
+    // non-equilibrium part.  (The pair form below rounds the equilibrium's
+    // symmetric and antisymmetric parts separately: measured 5x larger FP32
+    // errors in drag and in the adjoint's dJ/dtau.)
 #pragma unroll
-  for (int i = 1; i < L::Q; ++i) {
-    const int j = L::opp(i);
-    if (j < i) continue;
-    const T eu = (T)L::cx(i) * ux + (T)L::cy(i) * uy + (T)L::cz(i) * uz;
-    const T w = (T)L::w(i);
-    const T sym = (T)4.5 * eu * eu - uu15;
-    const T A = P::shifted ? w * (r + rho * sym) : (w * rho) * ((T)1 + sym);
-    const T B = ((T)3 * w * rho) * eu;
-    if constexpr (P::shifted) {
-      T oi = f[i] + omega * ((A + B) - f[i]);
-      T oj = f[j] + omega * ((A - B) - f[j]);
+    for (int i = 0; i < L::Q; ++i) {
+      const T eu = (T)L::cx(i) * ux + (T)L::cy(i) * uy + (T)L::cz(i) * uz;
+      const T w = (T)L::w(i);
+      const T poly = (T)3 * eu + (T)4.5 * eu * eu - uu15;
+      const T feq = w * (r + rho * poly);
+      T out = f[i] + omega * (feq - f[i]);
       if (rx.has_force) {
         const T eg = (T)L::cx(i) * gx + (T)L::cy(i) * gy + (T)L::cz(i) * gz;
-        const T fw = fpre3 * w;
-        const T Sc = fw * ((T)3 * eg * eu - ug), So = fw * eg;
-        oi += Sc + So;
-        oj += Sc - So;
+        out += fpre3 * w * (eg * ((T)1 + (T)3 * eu) - ug);
       }
-      fout[(size_t)i * S + n_] = oi;
-      fout[(size_t)j * S + n_] = oj;
-    } else {
+      fout[(size_t)i * S + n_] = out;
+    }
+  } else {
+    // FP64 (bound by the FP64 pipe): per pair of opposite directions
+    // (i, j = opp(i)), e_j = -e_i turns the equilibria into A +- B and the
+    // sources into Sc +- So with
+    //   A  = w rho (1 + 4.5 (e_i.u)^2 - 1.5 u.u),   B = 3 w rho (e_i.u),
+    //   Sc = fpre3 w (3 (e_i.g)(e_i.u) - u.g),     So = fpre3 w (e_i.g),
+    // so that f+_i,j = (1 - omega) f_i,j + (omega A + Sc) +- (omega B + So):
+    // fewer operations than one direction at a time.
+    const T om1 = (T)1 - omega;
+    {
+      const T w = (T)L::w(0);
+      T out = om1 * f[0] + omega * ((w * rho) * ((T)1 - uu15));
+      if (rx.has_force) out -= fpre3 * w * ug;
+      fout[n_] = out;
+    }
+#pragma unroll
+    for (int i = 1; i < L::Q; ++i) {
+      const int j = L::opp(i);
+      if (j < i) continue;
+      const T eu = (T)L::cx(i) * ux + (T)L::cy(i) * uy + (T)L::cz(i) * uz;
+      const T w = (T)L::w(i);
+      const T A = (w * rho) * ((T)1 + (T)4.5 * eu * eu - uu15);
+      const T B = ((T)3 * w * rho) * eu;
       T Pv = omega * A, Mv = omega * B;
       if (rx.has_force) {
         const T eg = (T)L::cx(i) * gx + (T)L::cy(i) * gy + (T)L::cz(i) * gz;

@@ -106,9 +106,10 @@ def test_batch_equals_domains_run_alone(L, prec):
             F1 = one.forces(len(s.cylinders))
         assert np.array_equal(f[:, b.domain_nodes(d)], f1), d
         Fd = F[b.body0[d]:b.body0[d] + len(s.cylinders)]
-        # force sums run in another order (FP32 lane sums in shifted storage)
+        # force sums run in another order (FP32 lane sums in shifted storage);
+        # small components are differences of O(max |F|) link terms
         rtol = 1e-12 if precision == L.LBM_FP64 else 1e-5
-        assert np.allclose(Fd, F1, rtol=rtol, atol=rtol * 1e-3 * np.abs(F1).max()), (d, Fd, F1)
+        assert np.allclose(Fd, F1, rtol=rtol, atol=rtol * 10 * np.abs(F1).max()), (d, Fd, F1)
 
 
 def test_batch_adjoint_equals_domains_alone(L):
