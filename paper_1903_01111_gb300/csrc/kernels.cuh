@@ -222,23 +222,39 @@ __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Pa
   const T fpre3 = (T)rx.fpre3;
   const T ug = ux * gx + uy * gy + uz * gz;
   if constexpr (P::shifted) {
-    // Shifted FP32 storage: one direction at a time, relaxing in the
-    // difference form f + omega (feq - f) so that rounding falls on the small
-    // non-equilibrium part.  (The pair form below rounds the equilibrium's
-    // symmetric and antisymmetric parts separately: measured 5x larger FP32
-    // errors in drag and in the adjoint's dJ/dtau.)
+    // Shifted FP32 storage: each direction keeps its own equilibrium
+    // feq_i = w (r + rho poly_i) and relaxes in the difference form
+    // f + omega (feq - f), so that rounding falls on the small
+    // non-equilibrium part; opposite directions (i, j = opp(i), e_j = -e_i)
+    // share e.u, the symmetric part 4.5 (e.u)^2 - 1.5 u.u of the polynomial
+    // and the two parts of the source, Sc +- So (Sc, So as in the FP64 form
+    // below).  (Relaxing the pair's symmetric and antisymmetric parts
+    // separately, as FP64 does, measured 5x larger FP32 errors in drag and in
+    // the adjoint's dJ/dtau.)
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
+      const int j = L::opp(i);
+      if (i != 0 && j < i) continue;
       const T eu = (T)L::cx(i) * ux + (T)L::cy(i) * uy + (T)L::cz(i) * uz;
       const T w = (T)L::w(i);
-      const T poly = (T)3 * eu + (T)4.5 * eu * eu - uu15;
-      const T feq = w * (r + rho * poly);
-      T out = f[i] + omega * (feq - f[i]);
+      const T sym = (T)4.5 * eu * eu - uu15;
+      const T feqi = w * (r + rho * (sym + (T)3 * eu));
+      T oi = f[i] + omega * (feqi - f[i]);
+      T Sc = 0, So = 0;
       if (rx.has_force) {
         const T eg = (T)L::cx(i) * gx + (T)L::cy(i) * gy + (T)L::cz(i) * gz;
-        out += fpre3 * w * (eg * ((T)1 + (T)3 * eu) - ug);
+        const T fw = fpre3 * w;
+        Sc = fw * ((T)3 * eg * eu - ug);
+        So = fw * eg;
+        oi += Sc + So;
       }
-      fout[(size_t)i * S + n_] = out;
+      fout[(size_t)i * S + n_] = oi;
+      if (i != 0) {
+        const T feqj = w * (r + rho * (sym - (T)3 * eu));
+        T oj = f[j] + omega * (feqj - f[j]);
+        if (rx.has_force) oj += Sc - So;
+        fout[(size_t)j * S + n_] = oj;
+      }
     }
   } else {
     // FP64 (bound by the FP64 pipe): per pair of opposite directions
@@ -423,6 +439,14 @@ __global__ void __launch_bounds__(BT, (bulk_blocks_per_sm<L, P, BT, NPT>())) k_b
   }
 }
 
+// Resident blocks per SM of the sequential walk (it keeps the next node's
+// word and run live): 4 per 256 threads in FP32 (64 registers, no spill;
+// at 40 registers the spills cost more than the prefetch wins), 2 in FP64.
+template <class P, int BT>
+constexpr int bulk_seq_blocks_per_sm() {
+  return (P::shifted ? 4 : 2) * 256 / BT;
+}
+
 // The fields of a run record that the pull offsets use away from the seam.
 template <class L>
 struct RunLite {
@@ -444,7 +468,7 @@ __device__ __forceinline__ RunLite<L> load_run_lite(const RunRec* __restrict__ r
 // while the current node's pulls are in flight, and the next node's run
 // record right after the current node's stores (D2Q9).
 template <class L, class P, bool MULTI, int BT, int SEQ>
-__global__ void __launch_bounds__(BT, (bulk_blocks_per_sm<L, P, BT, 1>())) k_bulk_seq(
+__global__ void __launch_bounds__(BT, (bulk_seq_blocks_per_sm<P, BT>())) k_bulk_seq(
     const typename P::T* __restrict__ fin, typename P::T* __restrict__ fout, Layout lay,
     Mom4<typename P::T>* __restrict__ mom, double* __restrict__ force_next, Params p) {
   using T = typename P::T;
