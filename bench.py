@@ -13,8 +13,12 @@ FP64 (``fp64``), each with the HBM roofline fraction of its dominant kernel
 (the bulk pull/collide kernel): algorithmic bytes 2*Q*s + 1 per fluid node
 divided by the kernel's average CUDA-event duration inside the timed region.
 
---impl reference times the FP64 CPU oracle (the reference implementation of
-this build) on a bounded sub-case of the same recipe.
+--impl reference times the FP64 CPU oracle (the plain restatement of the
+method that the tests check the kernels against) on a bounded sub-case of the
+same recipe.
+
+--part permeability runs the pack for --perm-steps steps (20,000 by default)
+in FP32 shifted and FP64 and reports the Darcy permeability of each.
 """
 from __future__ import annotations
 
@@ -484,14 +488,23 @@ def run_cylinder(lbm, torch, re, steps, sample_every=10, window=None):
                          inlet_y1=H + 0.5) as lat:
             lat.init_equilibrium(u=u0)
             _tune(lat, 10)
-            cd, cl = [], []
+            cd, cl, rho_trace = [], [], []
+            n_samples = steps // sample_every
+            rho_every = max(1, n_samples // 10)
+            wall = 0.0
             t0 = time.perf_counter()
-            for _ in range(steps // sample_every):
+            for j in range(n_samples):
                 lat.step(sample_every)
                 F = lat.force(0)
                 cd.append(2 * F[0] / (ubar ** 2 * D))
                 cl.append(2 * F[1] / (ubar ** 2 * D))
-            wall = time.perf_counter() - t0
+                if (j + 1) % rho_every == 0:
+                    # mean fluid density: the inlet/outlet pair fixes no density level
+                    wall += time.perf_counter() - t0
+                    rho, _ = lat.moments()
+                    rho_trace.append([(j + 1) * sample_every, float(rho[rho > 0].mean())])
+                    t0 = time.perf_counter()
+            wall += time.perf_counter() - t0
             lat.check()
             nf = lat.info().n_fluid
         cd, cl = np.array(cd), np.array(cl)
@@ -503,7 +516,7 @@ def run_cylinder(lbm, torch, re, steps, sample_every=10, window=None):
         series[name] = (cd, cl)
         out[name] = {"C_D_mean": float(cd[-m:].mean()), "C_L_mean": float(cl[-m:].mean()),
                      "C_L_amplitude": float(amp), "St": (float(st) if st is not None else None),
-                     "mlups_with_force_every_sample": nf * steps / wall / 1e6}
+                     "mlups_with_force_every_sample": nf * steps / wall / 1e6, "rho_mean_trace": rho_trace}
     d32, d64 = out["fp32s"], out["fp64"]
     out["fp32s_vs_fp64"] = {
         "C_D_rel": abs(d32["C_D_mean"] - d64["C_D_mean"]) / abs(d64["C_D_mean"]),
@@ -512,6 +525,48 @@ def run_cylinder(lbm, torch, re, steps, sample_every=10, window=None):
         "St_rel": (abs(d32["St"] - d64["St"]) / d64["St"] if d32["St"] and d64["St"] else None),
         "max_abs_C_D_diff_over_run": float(np.abs(series["fp32s"][0] - series["fp64"][0]).max()),
         "max_abs_C_L_diff_over_run": float(np.abs(series["fp32s"][1] - series["fp64"][1]).max())}
+    return out
+
+
+def darcy_permeability(geo, u, nu, g):
+    """Permeability of a periodic medium driven by the body-force density g
+    along x, from Darcy's law: k = nu q_D / g with the superficial velocity
+    q_D = (sum of u_x over the fluid nodes) / (all lattice nodes), rho0 = 1.
+    u: the (D, N) velocity of lbm_moments (zero at solid nodes)."""
+    return nu * float(np.sum(u[0])) / geo.N / g
+
+
+def run_permeability(lbm, torch, geo, steps, tau=0.7, g=1e-6, samples=4):
+    """Sphere-pack permeability after `steps` steps from rest, FP32 shifted
+    and FP64 (the same VIBB step as the headline), sampled `samples` times
+    along the run to show its convergence; the FP32-vs-FP64 difference is the
+    precision error of the quantity the pack workload is run for."""
+    nu = (tau - 0.5) / 3
+    out = {"steps": steps, "tau": tau, "g": g, "nu": nu, "porosity": geo.info.get("porosity")}
+    for name, prec in (("fp32s", lbm.LBM_FP32_SHIFTED), ("fp64", lbm.LBM_FP64)):
+        stream = torch.cuda.Stream()
+        with lbm.Lattice(geo, precision=prec, tau=tau, g=(g, 0.0, 0.0), bc=lbm.LBM_BC_VIBB,
+                         stream=stream.cuda_stream, vibb_density=lbm.LBM_VIBB_RHO_LOCAL) as lat:
+            lat.init_equilibrium()
+            _tune(lat, 10)
+            trace, wall, done = [], 0.0, 0
+            for j in range(1, samples + 1):
+                n = steps * j // samples - done
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                lat.step(n)
+                torch.cuda.synchronize()
+                wall += time.perf_counter() - t0
+                done += n
+                rho, u = lat.moments()
+                trace.append({"step": done, "k": darcy_permeability(geo, u, nu, g),
+                              "rho_mean": float(rho[rho > 0].mean())})
+            lat.check()
+            nf = lat.info().n_fluid
+        out[name] = {"k": trace[-1]["k"], "trace": trace, "mlups": nf * steps / wall / 1e6,
+                     "k_change_last_quarter": abs(trace[-1]["k"] - trace[-2]["k"]) / abs(trace[-1]["k"])
+                     if samples > 1 else None}
+    out["k_rel_fp32s_vs_fp64"] = abs(out["fp32s"]["k"] - out["fp64"]["k"]) / abs(out["fp64"]["k"])
     return out
 
 
@@ -613,13 +668,15 @@ def main():
     ap.add_argument("--no-cylinder", action="store_true")
     ap.add_argument("--cylinder-steps", type=int, default=60000)
     ap.add_argument("--sweep-steps", type=int, default=100)
-    ap.add_argument("--part", default="all", choices=["all", "batch", "adjoint", "sweep", "cylinder"],
+    ap.add_argument("--part", default="all", choices=["all", "batch", "adjoint", "sweep", "cylinder", "permeability"],
                     help="run one section alone (for profiling) and print its JSON")
     ap.add_argument("--batch-domains", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=2000)
     ap.add_argument("--adjoint-steps", type=int, default=20000)
     ap.add_argument("--adjoint-fd", action="store_true", help="with --part adjoint: also the FD check")
     ap.add_argument("--sweep-scale", type=int, default=1, help="divide the sweep lattices' sides by this")
+    ap.add_argument("--perm-steps", type=int, default=20000,
+                    help="with --part permeability: steps of the sphere-pack run (FP32 shifted and FP64)")
     ap.add_argument("--tuning", default="auto", choices=["auto", "default"],
                     help="autotune every timed lattice (default) or keep the default launch shapes")
     ap.add_argument("--bulk-shape", type=int, default=-1,
@@ -644,6 +701,8 @@ def main():
         if args.part == "cylinder":
             out = [run_cylinder(lbm, torch, 20, args.cylinder_steps // 2),
                    run_cylinder(lbm, torch, 100, args.cylinder_steps)]
+        elif args.part == "permeability":
+            out = run_permeability(lbm, torch, geometry(args.n), args.perm_steps)
         elif args.part == "sweep":
             out = run_sweep(lbm, torch, args.sweep_steps, _peaks()[0], scale=args.sweep_scale)
         elif args.part == "batch":

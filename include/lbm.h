@@ -43,7 +43,7 @@ typedef enum {
   LBM_ERR_OOM = 4,          /* device or host allocation failed */
   LBM_ERR_DIVERGED = 5,     /* non-finite population or non-positive density */
   LBM_ERR_TIMEOUT = 6,      /* reserved for bounded device waits */
-  LBM_ERR_UNSUPPORTED = 7   /* valid request this build does not implement */
+  LBM_ERR_UNSUPPORTED = 7   /* valid request the library does not implement */
 } lbm_status;
 
 enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 };
