@@ -307,14 +307,15 @@ def run_sweep(lbm, torch, steps, peak, scale=1):
     return out
 
 
-def run_adjoint(lbm, n_steps=20000, checkpoint_every=500, fd=True):
+def run_adjoint(lbm, n_steps=20000, checkpoint_every=500, fd=True, fd_all=False):
     """Drag gradient on the 1024 x 256 channel cylinder (radius 16.494, centre
     (256.343, 128.626), u_max 0.1, Re 40 on the mean inflow and the diameter):
     FP32-shifted forward and adjoint with FP64 sensitivity accumulation, cost
     per step of the backward sweep (recompute + adjoint) over a forward step,
     and an FP64 fourth-order central-difference check (steps 1e-3, 2e-3) of
     dJ/dR and dJ/dtau; the centre and radius keep every cut link at least
-    4e-3 (in theta) away from the q = 1/2 branch switch."""
+    4e-3 (in theta) away from the q = 1/2 branch switch.  fd_all: the same
+    check of dJ/dc_x and dJ/dc_y (the margin holds for the centre too)."""
     from paper_1903_01111_gb300.autograd import CylinderSpec, branch_margin, force_only, run
 
     ubar = 2.0 / 3.0 * 0.1
@@ -326,6 +327,7 @@ def run_adjoint(lbm, n_steps=20000, checkpoint_every=500, fd=True):
                         checkpoint_every=checkpoint_every, precision=lbm.LBM_FP32_SHIFTED)
     J32, g32 = run(spec, theta)
     sec = spec.last["seconds"]
+    cancel = spec.last["cancellation"]
     out = {"workload": "D2Q9 1024x256 channel, cylinder R 16.494 at (256.343, 128.626), u_max 0.1, Re 40, "
                        f"tau {tau:.4f}, {n_steps} steps, checkpoints every {checkpoint_every}",
            "J_drag": J32, "grad_fp32": {"cx": g32[0], "cy": g32[1], "R": g32[2], "tau": g32[3]},
@@ -333,7 +335,8 @@ def run_adjoint(lbm, n_steps=20000, checkpoint_every=500, fd=True):
            "backward_ms_per_step": (sec[1] + sec[2]) / n_steps * 1e3,
            "recompute_ms_per_step": sec[1] / n_steps * 1e3, "adjoint_ms_per_step": sec[2] / n_steps * 1e3,
            "ratio_backward_to_forward": (sec[1] + sec[2]) / sec[0],
-           "ratio_adjoint_kernels_to_forward": sec[2] / sec[0]}
+           "ratio_adjoint_kernels_to_forward": sec[2] / sec[0],
+           "link_sum_cancellation": {"cx": cancel[0], "cy": cancel[1], "R": cancel[2]}}
     if fd:
         spec64 = CylinderSpec(kind="channel", nx=1024, ny_fluid=256, u_max=0.1, n_steps=n_steps,
                               checkpoint_every=checkpoint_every, precision=lbm.LBM_FP64)
@@ -347,10 +350,12 @@ def run_adjoint(lbm, n_steps=20000, checkpoint_every=500, fd=True):
             tm[k] -= step
             return (force_only(spec64, tp) - force_only(spec64, tm)) / (2 * step)
 
-        for k, name in ((2, "R"), (3, "tau")):
+        scale = float(np.abs(g64).max())
+        for k, name in (((0, "cx"), (1, "cy"), (2, "R"), (3, "tau")) if fd_all else ((2, "R"), (3, "tau"))):
             fd_k = (4 * diff(k, h) - diff(k, 2 * h)) / 3
             checks[name] = {"adjoint_fp64": g64[k], "fd_fp64": fd_k, "rel_err_fp64": abs(g64[k] - fd_k) / abs(fd_k),
-                            "adjoint_fp32": g32[k], "rel_err_fp32_vs_fd": abs(g32[k] - fd_k) / abs(fd_k)}
+                            "adjoint_fp32": g32[k], "rel_err_fp32_vs_fd": abs(g32[k] - fd_k) / abs(fd_k),
+                            "err_fp32_over_max_grad": abs(g32[k] - fd_k) / scale}
         out["fd_check"] = checks
     return out
 
@@ -709,8 +714,8 @@ def main():
             out = run_batch(lbm, torch, _peaks()[0], n_domains=args.batch_domains, steps=args.batch_steps,
                             warmup=args.warmup, adjoint_steps=min(64, args.batch_steps), K=8)
         else:
-            out = run_adjoint(lbm, n_steps=args.adjoint_steps, checkpoint_every=max(2, int(args.adjoint_steps ** 0.5)),
-                              fd=args.adjoint_fd)
+            out = run_adjoint(lbm, n_steps=args.adjoint_steps, checkpoint_every=max(2, min(500, args.adjoint_steps)),
+                              fd=args.adjoint_fd, fd_all=args.adjoint_fd)
         print(json.dumps(out), flush=True)
         return 0
 
@@ -738,7 +743,7 @@ def main():
         r64["clocks"] = clocks64.stop()
     e2e = None if args.no_e2e else run_e2e(lbm, torch, geo, args.steps)
     sweep = None if args.no_sweep else run_sweep(lbm, torch, args.sweep_steps, peak)
-    adjoint = None if args.no_adjoint else run_adjoint(lbm)
+    adjoint = None if args.no_adjoint else run_adjoint(lbm, fd_all=True)
     batched = None if args.no_batch else run_batch(lbm, torch, peak, dist=dist)
     cylinder = None
     if not args.no_cylinder:

@@ -94,7 +94,12 @@ def run(spec: CylinderSpec, theta):
         J, dJdq, dJdtau, sec = lbm.lbm_adjoint_step(lat.h, 0, spec.direction, spec.n_steps, spec.checkpoint_every)
     dq = G.ball_q_derivatives(geo, bi)
     grad = np.array([dJdq @ dq[:, 0], dJdq @ dq[:, 1], dJdq @ dq[:, 3], dJdtau])
-    spec.last = dict(J=J, grad=grad, seconds=sec, n_links=len(geo.links), n_fluid=geo.fluid_count())
+    # sum over links of |term| / |sum of terms| for c_x, c_y, R: how much a
+    # relative error of the per-link sensitivities grows in each component
+    terms = dJdq[:, None] * dq[:, [0, 1, 3]]
+    cancel = np.abs(terms).sum(axis=0) / np.maximum(np.abs(terms.sum(axis=0)), 1e-300)
+    spec.last = dict(J=J, grad=grad, seconds=sec, n_links=len(geo.links), n_fluid=geo.fluid_count(),
+                     cancellation=cancel)
     return J, grad
 
 

@@ -15,6 +15,8 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "adjoint.cuh"
@@ -44,6 +46,41 @@ lbm_status fail(lbm_status st, const char* fmt, ...) {
   } while (0)
 
 constexpr int kMaxTimedKernels = 3;
+
+// Host arrays of the layout build: elements are not value-initialised on
+// construction (a serial zero fill of a few GB took a large part of
+// lbm_set_geometry); each array is filled or written in full by parallel
+// loops, which also spread the first-touch page faults over the threads.
+template <class T>
+struct RawAlloc {
+  using value_type = T;
+  RawAlloc() = default;
+  template <class U>
+  RawAlloc(const RawAlloc<U>&) {}
+  T* allocate(size_t n) { return std::allocator<T>().allocate(n); }
+  void deallocate(T* p, size_t n) { std::allocator<T>().deallocate(p, n); }
+  template <class U>
+  void construct(U* p) noexcept(std::is_nothrow_default_constructible<U>::value) {
+    ::new ((void*)p) U;
+  }
+  template <class U, class... A>
+  void construct(U* p, A&&... a) {
+    ::new ((void*)p) U(std::forward<A>(a)...);
+  }
+  template <class U>
+  bool operator==(const RawAlloc<U>&) const { return true; }
+  template <class U>
+  bool operator!=(const RawAlloc<U>&) const { return false; }
+};
+template <class T>
+using raw_vec = std::vector<T, RawAlloc<T>>;
+
+template <class V, class T>
+void par_fill(V& v, const T& x) {
+  const int64_t n = (int64_t)v.size();
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) v[i] = x;
+}
 
 // host mask bits used while building the layout
 enum : uint8_t { H_SOLID = 1, H_CACHE = 2, H_OPEN = 4, H_GHOST = 8 };
@@ -76,7 +113,7 @@ struct lbm_lattice_s {
   DeviceBuf dom, row_dom;
   int nbody = 1;  // force accumulators per slot
   lbm_tuning tune{-1, 256, 2, 1};
-  std::vector<int32_t> sidx;  // dense -> storage index (-1: not stored), host
+  raw_vec<int32_t> sidx;  // dense -> storage index (-1: not stored), host
   // links
   DeviceBuf recs, q, uw;
   int64_t n_links = 0, n_fluid = 0, n_cached = 0, n_runs = 0;
@@ -84,7 +121,7 @@ struct lbm_lattice_s {
   // shifted storage: sum over each body's links of 2 w_i' rho0 e_i' (FP64),
   // the rest part of the momentum exchange that the link kernel leaves out
   std::vector<double> force_rest = std::vector<double>(3, 0.0);
-  std::vector<int64_t> link_order;  // device link j = caller's link link_order[j]
+  raw_vec<int64_t> link_order;  // device link j = caller's link link_order[j]
   bool from_init = false;           // state is the one lbm_init_equilibrium made
   int cur = 0;      // buffer holding f+(t)
   int64_t step = 0;
@@ -406,7 +443,7 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
     }
   }
   // node classes
-  std::vector<uint8_t> m(N);
+  raw_vec<uint8_t> m(N);
 #pragma omp parallel for schedule(static)
   for (int64_t n = 0; n < N; ++n) m[n] = solid[n] ? H_SOLID : 0;
   if (ndom > 0) {
@@ -467,8 +504,8 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
   };
   // links: checks, second fluid node, cache flags.  The checks run in
   // parallel; the first failing link is reported.
-  std::vector<int64_t> lk_s(n_links), lk_ff(n_links);
-  std::vector<int> lk_rule(n_links);
+  raw_vec<int64_t> lk_s(n_links), lk_ff(n_links);  // written for every link that passes
+  raw_vec<int> lk_rule(n_links);
   auto check_link = [&](int64_t k, int64_t& s, int64_t& ff, int& rule) -> int {
     const lbm_link& L = links[k];
     if (L.node < 0 || L.node >= N) return 1;
@@ -487,8 +524,9 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
     return 0;
   };
   int64_t first_bad = n_links;
-  int nbody = 1, moving_i = 0;
-#pragma omp parallel for schedule(static) reduction(min : first_bad) reduction(max : nbody) reduction(| : moving_i)
+  int nbody = 1, moving_i = 0, min_body = MAX_BODIES, max_body = -1;
+#pragma omp parallel for schedule(static) reduction(min : first_bad, min_body) reduction(max : nbody, max_body) \
+    reduction(| : moving_i)
   for (int64_t k = 0; k < n_links; ++k) {
     int64_t s = 0, ff = 0;
     int rule = 0;
@@ -498,6 +536,8 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
     }
     const lbm_link& L = links[k];
     nbody = std::max(nbody, (int)L.body + 1);
+    min_body = std::min(min_body, (int)L.body);
+    max_body = std::max(max_body, (int)L.body);
     for (int a = 0; a < D; ++a) moving_i |= L.uw[a] != 0.0 ? 1 : 0;
     lk_s[k] = s;
     lk_ff[k] = ff;
@@ -522,16 +562,27 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
     }
   }
   const bool moving = moving_i != 0;
+  // moment-cache nodes (x_f, x_ff of VIBB links: fluid) and ghost nodes
+  // (x_s: solid) are disjoint, so one mark per node records both: every
+  // writer stores the same byte (an atomic write, no read-modify-write), and
+  // the class of the node tells which flag the mark stands for
+  {
+    raw_vec<uint8_t> mark(N);
+    par_fill(mark, (uint8_t)0);
 #pragma omp parallel for schedule(static)
-  for (int64_t k = 0; k < n_links; ++k) {
-    if (lk_rule[k] == LBM_BC_VIBB) {
-#pragma omp atomic
-      m[links[k].node] |= H_CACHE;
-#pragma omp atomic
-      m[lk_ff[k]] |= H_CACHE;
+    for (int64_t k = 0; k < n_links; ++k) {
+      if (lk_rule[k] == LBM_BC_VIBB) {
+#pragma omp atomic write
+        mark[links[k].node] = 1;
+#pragma omp atomic write
+        mark[lk_ff[k]] = 1;
+      }
+#pragma omp atomic write
+      mark[lk_s[k]] = 1;
     }
-#pragma omp atomic
-    m[lk_s[k]] |= H_GHOST;
+#pragma omp parallel for schedule(static)
+    for (int64_t n = 0; n < N; ++n)
+      if (mark[n]) m[n] |= (m[n] & H_SOLID) ? H_GHOST : H_CACHE;
   }
   // open inlet reads the moments of the first fluid column
   if (c.inlet)
@@ -543,7 +594,8 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
       }
   // link order: (node, dir) -- usually the input order already -- then
   // stably by body; reject duplicate (node, dir)
-  std::vector<int64_t> order(n_links);
+  raw_vec<int64_t> order(n_links);
+#pragma omp parallel for schedule(static)
   for (int64_t k = 0; k < n_links; ++k) order[k] = k;
   auto nodedir = [&](int64_t k) { return (uint64_t)links[k].node * 32 + (uint64_t)links[k].dir; };
   int64_t unsorted = 0;
@@ -563,32 +615,49 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
   if (first_dup < n_links)
     return fail(LBM_ERR_INVALID_ARG, "duplicate link at node %lld direction %d",
                 (long long)(nodedir(order[first_dup]) / 32), (int)(nodedir(order[first_dup]) % 32));
-  {
+  if (min_body < max_body) {  // (one body for every link: the order stands)
     std::vector<int64_t> count(nbody + 2, 0);
     for (int64_t k = 0; k < n_links; ++k) count[links[k].body + 2]++;
     for (int b = 1; b < nbody + 2; ++b) count[b] += count[b - 1];
-    std::vector<int64_t> byb(n_links);
+    raw_vec<int64_t> byb(n_links);
     for (int64_t k = 0; k < n_links; ++k) byb[count[links[order[k]].body + 1]++] = order[k];
     order.swap(byb);
   }
-  // completeness: count (fluid node, dir) pairs with a solid neighbour
+  // completeness: count (fluid node, dir) pairs with a solid neighbour, row
+  // by row (each direction's neighbour row is found once per row).  A
+  // neighbour outside a non-periodic face is skipped: only open columns can
+  // sit there (faces are solid otherwise).
   int64_t expected = 0, n_fluid = 0;
 #pragma omp parallel for schedule(static) reduction(+ : expected, n_fluid)
-  for (int64_t n = 0; n < N; ++n) {
-    if (m[n] & (H_SOLID | H_OPEN)) continue;
-    ++n_fluid;
-    int64_t x[3];
-    coords(n, x);
+  for (int64_t r = 0; r < rows; ++r) {
+    const int64_t y = r % ny, z = r / ny;
+    int64_t nrow[32];  // first node of the neighbour row of each direction, -1: outside
     for (int d = 1; d < Q; ++d) {
-      int64_t y[3] = {x[0] + cx_of(h, d), x[1] + cy_of(h, d), x[2] + cz_of(h, d)};
+      int64_t yy = y + cy_of(h, d), zz = z + cz_of(h, d);
       bool out = false;
-      for (int a = 0; a < 3; ++a)
-        if (y[a] < 0 || y[a] >= len[a]) {
-          if (!c.periodic[a]) out = true;
-          y[a] = (y[a] + len[a]) % len[a];
+      if (yy < 0 || yy >= ny) {
+        if (!c.periodic[1]) out = true;
+        yy = (yy + ny) % ny;
+      }
+      if (zz < 0 || zz >= nz) {
+        if (!c.periodic[2]) out = true;
+        zz = (zz + nz) % nz;
+      }
+      nrow[d] = out ? -1 : nx * (yy + ny * zz);
+    }
+    const uint8_t* mr = m.data() + nx * r;
+    for (int64_t x = 0; x < nx; ++x) {
+      if (mr[x] & (H_SOLID | H_OPEN)) continue;
+      ++n_fluid;
+      for (int d = 1; d < Q; ++d) {
+        if (nrow[d] < 0) continue;
+        int64_t xx = x + cx_of(h, d);
+        if (xx < 0 || xx >= nx) {
+          if (!c.periodic[0]) continue;
+          xx = (xx + nx) % nx;
         }
-      if (out) continue;  // only open columns can sit there (faces are solid otherwise)
-      if (m[y[0] + nx * (y[1] + ny * y[2])] & H_SOLID) ++expected;
+        if (m[nrow[d] + xx] & H_SOLID) ++expected;
+      }
     }
   }
   if (expected != n_links)
@@ -608,8 +677,9 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
   }
   for (int64_t ch = 0; ch < nchunk; ++ch) chunk_start[ch + 1] += chunk_start[ch];
   const int64_t S = chunk_start[nchunk];
-  std::vector<int32_t> sidx(N, -1);
-  std::vector<int32_t> node_of((size_t)S);
+  raw_vec<int32_t> sidx(N);
+  par_fill(sidx, (int32_t)-1);
+  raw_vec<int32_t> node_of((size_t)S);  // written for every stored node
 #pragma omp parallel for schedule(static)
   for (int64_t ch = 0; ch < nchunk; ++ch) {
     int64_t k = chunk_start[ch];
@@ -712,8 +782,10 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
   }
   for (int64_t r = 0; r < rows; ++r) row_runs[r + 1] += row_runs[r];
   if (row_runs[rows] > (int64_t)W_RUN + 1) return fail(LBM_ERR_UNSUPPORTED, "too many fluid runs");
-  std::vector<RunRec> runs((size_t)row_runs[rows]);
-  std::vector<uint32_t> word(S, 0);
+  raw_vec<RunRec> runs((size_t)row_runs[rows]);
+  par_fill(runs, RunRec{});
+  raw_vec<uint32_t> word(S);
+  par_fill(word, 0u);
 #pragma omp parallel for schedule(dynamic, 64)
   for (int64_t r = 0; r < rows; ++r) {
     int64_t bad[2];
@@ -730,22 +802,36 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
     else
       n_cached += (m[n] & H_CACHE) ? 1 : 0;
   }
-  // rest part of the momentum exchange per body (shifted storage)
+  // rest part of the momentum exchange per body (shifted storage):
+  // sum over the body's links of 2 w_i' rho0 e_i', from the exact count of
+  // its links per direction (counted in parallel, summed in a fixed order)
   std::vector<double> rest(3 * (size_t)nbody, 0.0);
-  if (c.precision == LBM_FP32_SHIFTED)
-    for (int64_t k = 0; k < n_links; ++k) {
-      const lbm_link& L = links[k];
-      if (L.body < 0) continue;
-      const double w = h->Q == 9 ? D2Q9::w(L.dir) : D3Q19::w(L.dir);
-      const double t = 2.0 * w * c.rho0;
-      rest[3 * L.body + 0] += t * cx_of(h, L.dir);
-      rest[3 * L.body + 1] += t * cy_of(h, L.dir);
-      rest[3 * L.body + 2] += t * cz_of(h, L.dir);
+  if (c.precision == LBM_FP32_SHIFTED && n_links > 0 && max_body >= 0) {
+    const size_t nc = (size_t)(max_body + 1) * Q;
+    std::vector<int64_t> cnt(nc, 0);
+#pragma omp parallel
+    {
+      std::vector<int64_t> mine(nc, 0);
+#pragma omp for schedule(static) nowait
+      for (int64_t k = 0; k < n_links; ++k)
+        if (links[k].body >= 0) ++mine[(size_t)links[k].body * Q + links[k].dir];
+#pragma omp critical
+      for (size_t j = 0; j < nc; ++j) cnt[j] += mine[j];
     }
+    for (int b = 0; b <= max_body; ++b)
+      for (int d = 1; d < Q; ++d) {
+        const int64_t n = cnt[(size_t)b * Q + d];
+        if (n == 0) continue;
+        const double t = (double)n * 2.0 * (Q == 9 ? D2Q9::w(d) : D3Q19::w(d)) * c.rho0;
+        rest[3 * b + 0] += t * cx_of(h, d);
+        rest[3 * b + 1] += t * cy_of(h, d);
+        rest[3 * b + 2] += t * cz_of(h, d);
+      }
+  }
   // link records in the chosen order
-  std::vector<LinkRec> recs(n_links);
-  std::vector<double> qs(n_links);
-  std::vector<double> uws(moving ? (size_t)D * n_links : 0);
+  raw_vec<LinkRec> recs(n_links);  // these three: written in full below
+  raw_vec<double> qs(n_links);
+  raw_vec<double> uws(moving ? (size_t)D * n_links : 0);
 #pragma omp parallel for schedule(static)
   for (int64_t j = 0; j < n_links; ++j) {
     const int64_t k = order[j];
@@ -802,7 +888,11 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
       st = upload(h->q, qs.data(), 8 * n_links);
       if (st == LBM_OK && moving) st = upload(h->uw, uws.data(), 8 * uws.size());
     } else {
-      std::vector<float> tq(qs.begin(), qs.end()), tw(uws.begin(), uws.end());
+      raw_vec<float> tq(qs.size()), tw(uws.size());
+#pragma omp parallel for schedule(static)
+      for (int64_t j = 0; j < (int64_t)qs.size(); ++j) tq[j] = (float)qs[j];
+#pragma omp parallel for schedule(static)
+      for (int64_t j = 0; j < (int64_t)uws.size(); ++j) tw[j] = (float)uws[j];
       st = upload(h->q, tq.data(), 4 * n_links);
       if (st == LBM_OK && moving) st = upload(h->uw, tw.data(), 4 * tw.size());
     }

@@ -295,9 +295,10 @@ def test_divergence_is_reported(L):
     lat.close()
 
 
-def _oracle_one_node_step(geo, e, w, opp, links_at, fp_of, x, tau, g):
-    """f+(x, t+1) from gathered f+(., t): pull, link rules, collision."""
-    cfg = O.make_config(stencil=geo.stencil, tau=tau, g=g, bc=2)
+def _oracle_one_node_step(geo, e, w, opp, links_at, fp_of, x, tau, g, bc=2, vibb_density=0):
+    """f+(x, t+1) from gathered f+(., t): pull, link rules (each link's own
+    rule, else bc), collision."""
+    cfg = O.make_config(stencil=geo.stencil, tau=tau, g=g, bc=bc, vibb_density=vibb_density)
     Q = len(w)
     f = np.empty(Q)
     nx, ny, nz = geo.shape
@@ -319,33 +320,26 @@ def _oracle_one_node_step(geo, e, w, opp, links_at, fp_of, x, tau, g):
         rf, rff = vf.sum(), vff.sum()
         uf = (vf @ e - 0.5 * np.asarray(g)) / rf
         uff = (vff @ e - 0.5 * np.asarray(g)) / rff
-        f[i] = O.link_value(cfg, 2, ip, lk["q"], lk["uw"], vf, vff, rf, uf, rff, uff)
+        rule = int(lk["bc"]) if int(lk["bc"]) >= 0 else bc
+        f[i] = O.link_value(cfg, rule, ip, lk["q"], lk["uw"], vf, vff, rf, uf, rff, uff)
     fp, _, _ = O.collide(cfg, f)
     return fp
 
 
-def test_full_size_sphere_pack_sampled_nodes(L):
-    """The 384^3 workload in the bench's launch configuration: after one step
-    from a non-uniform state, f+(t+1) at sampled fluid nodes equals the
-    oracle's pull + link rules + collision computed node by node from the
-    gathered f+(t)."""
-    geo = G.sphere_pack(384, seed=0)
-    e, w = O.velocity_set(1)
-    opp = [int(np.flatnonzero((e == -e[i]).all(1))[0]) for i in range(19)]
-    tau, g = 0.7, (1e-6, 0.0, 0.0)
-    lat = L.Lattice(geo, tau=tau, g=g, bc=2)
-    lat.init_equilibrium()
-    lat.step(3)  # non-uniform state near the walls
-    rng = np.random.default_rng(0)
-    fluid = np.flatnonzero(geo.solid == 0)
-    boundary = np.unique(geo.links["node"])
-    sample = np.concatenate([rng.choice(boundary, 150, replace=False), rng.choice(fluid, 50, replace=False)])
+def _sampled_step_check(L, lat, geo, sample, tau, g, bc, vibb_density, shifted):
+    """One step of `lat` against the one-node oracle step at `sample`, from
+    the gathered state; FP64: 1e-13 absolute; FP32 shifted: 16 eps32 of the
+    largest deviation |f - w rho0| (one step's roundings on the stored h)."""
+    stencil = geo.stencil
+    e, w = O.velocity_set(stencil)
+    Q = len(w)
+    opp = [int(np.flatnonzero((e == -e[i]).all(1))[0]) for i in range(Q)]
     nx, ny, _ = geo.shape
     need = set()
     for x in sample:
         c = np.array([x % nx, (x // nx) % ny, x // (nx * ny)])
-        for d1 in range(19):
-            for d2 in range(19):
+        for d1 in range(Q):
+            for d2 in range(Q):
                 cc = (c - e[d1] + e[d2]) % np.array(geo.shape)
                 need.add(int(cc[0] + nx * (cc[1] + ny * cc[2])))
     need = np.array(sorted(need))
@@ -357,9 +351,70 @@ def test_full_size_sphere_pack_sampled_nodes(L):
         links_at.setdefault(int(lk["node"]), []).append(lk)
     lat.step(1)
     got = L.lbm_gather(lat.h, sample)
-    for k, x in enumerate(sample):
-        want = _oracle_one_node_step(geo, e, w, opp, links_at, lambda n: table[n], int(x), tau, g)
-        assert np.abs(got[k] - want).max() < 1e-13, (x, got[k] - want)
+    want = np.array([_oracle_one_node_step(geo, e, w, opp, links_at, lambda n: table[n], int(x), tau, g, bc,
+                                           vibb_density) for x in sample])
+    tol = 16 * EPS32 * np.abs(want - w[None, :]).max() if shifted else 1e-13
+    err = np.abs(got - want).max(axis=1)
+    assert err.max() <= tol, (sample[int(np.argmax(err))], err.max(), tol)
+    return err.max(), tol
+
+
+@pytest.mark.parametrize("arm", ["fp64", "fp32s_bench"])
+def test_full_size_sphere_pack_sampled_nodes(L, arm):
+    """The 384^3 workload: after three steps from rest, f+(t+1) at sampled
+    fluid nodes (150 with links, 50 anywhere) equals the oracle's pull + link
+    rules + collision computed node by node from the gathered f+(t).  The
+    fp32s arm is the bench's configuration: FP32 shifted storage, VIBB with
+    rho_d = rho_f for q > 1/2, the autotuner's launch shapes (one node per
+    thread in 256-thread blocks, 128-thread link blocks with 4 links per
+    thread)."""
+    geo = G.sphere_pack(384, seed=0)
+    tau, g = 0.7, (1e-6, 0.0, 0.0)
+    if arm == "fp64":
+        lat = L.Lattice(geo, tau=tau, g=g, bc=2)
+        vd, shifted = 0, False
+    else:
+        lat = L.Lattice(geo, precision=L.LBM_FP32_SHIFTED, tau=tau, g=g, bc=2, vibb_density=L.LBM_VIBB_RHO_LOCAL)
+        lat.set_tuning(bulk_shape=0, link_threads=128, link_seq=4, graph_steps=8)
+        vd, shifted = 1, True
+    lat.init_equilibrium()
+    lat.step(3)  # non-uniform state near the walls
+    rng = np.random.default_rng(0)
+    fluid = np.flatnonzero(geo.solid == 0)
+    boundary = np.unique(geo.links["node"])
+    sample = np.concatenate([rng.choice(boundary, 150, replace=False), rng.choice(fluid, 50, replace=False)])
+    _sampled_step_check(L, lat, geo, sample, tau, g, 2, vd, shifted)
+    lat.close()
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_full_size_cylinder_channel_sampled_nodes(L, prec):
+    """The 2000 x 400 cylinder channel at Re 100 (tau 0.5812), the bench's
+    cylinder run: after 50 steps from the Poiseuille start, f+(t+1) at nodes
+    on the cylinder, on the walls and in the bulk (columns 2 .. nx - 3, whose
+    pulls do not reach the open columns) equals the one-node oracle step
+    from the gathered state."""
+    R, u_max, H = 20.3, 0.1, 400
+    ubar, D = 2.0 / 3.0 * u_max, 2 * R
+    tau = 3 * ubar * D / 100 + 0.5
+    geo = G.cylinder_channel(nx=2000, ny_fluid=H, center=(400.37, 200.61), radius=R, u_max=u_max)
+    y = (np.arange(geo.N) // geo.nx) % geo.ny
+    u0 = np.zeros((geo.N, 3))
+    u0[:, 0] = np.where(geo.solid == 0, 4 * u_max * (y - 0.5) * (H + 0.5 - y) / H ** 2, 0.0)
+    lat = L.Lattice(geo, precision=_p(L, prec), tau=tau, bc=2, inlet_umax=u_max, inlet_y0=0.5, inlet_y1=H + 0.5)
+    lat.init_equilibrium(u=u0)
+    lat.step(50)
+    rng = np.random.default_rng(1)
+    x = np.arange(geo.N) % geo.nx
+    inner = (x >= 2) & (x <= geo.nx - 3)
+    fluid = np.flatnonzero((geo.solid == 0) & inner)
+    lk_nodes = np.unique(geo.links["node"])
+    lk_nodes = lk_nodes[inner[lk_nodes]]
+    on_cyl = lk_nodes[np.abs(lk_nodes % geo.nx - 400) < 30]
+    on_wall = lk_nodes[np.abs(lk_nodes % geo.nx - 400) >= 30]
+    sample = np.concatenate([rng.choice(on_cyl, 80, replace=False), rng.choice(on_wall, 40, replace=False),
+                             rng.choice(fluid, 40, replace=False)])
+    _sampled_step_check(L, lat, geo, sample, tau, (0.0, 0.0, 0.0), 2, 0, prec == "fp32s")
     lat.close()
 
 
