@@ -18,7 +18,9 @@ method that the tests check the kernels against) on a bounded sub-case of the
 same recipe.
 
 --part permeability runs the pack for --perm-steps steps (20,000 by default)
-in FP32 shifted and FP64 and reports the Darcy permeability of each.
+in FP32 shifted and FP64 and reports the Darcy permeability of each;
+--part studies runs the link rules' accuracy studies (Poiseuille over q and
+tau, Couette convergence) on the FP64 path.
 """
 from __future__ import annotations
 
@@ -575,6 +577,70 @@ def run_permeability(lbm, torch, geo, steps, tau=0.7, g=1e-6, samples=4):
     return out
 
 
+def run_studies(lbm, torch):
+    """Accuracy studies of the link rules on the GPU FP64 path (the paper's
+    validation flows): plane Poiseuille flow (Sec. 4.1) between walls at
+    fraction q of the first and last links, swept over q and tau, and
+    cylindrical Couette flow (Sec. 4.2) over L = 20 .. 320 with the observed
+    order of convergence, at a fixed wall speed (acoustic scaling: the
+    Mach-number error stays) and at a wall speed falling as 1/L (diffusive
+    scaling: fixed Re).  Each run goes to steady state (about 3 diffusion
+    times) from rest; errors are relative L2 over the fluid nodes."""
+    from paper_1903_01111_gb300 import geometry as G
+
+    names = {0: "halfway", 1: "bouzidi", 2: "vibb", 3: "vibb_local_rho"}
+    rules = ((0, 0), (1, 0), (2, 0), (2, 1))  # (link rule, VIBB density reading)
+    out = {"poiseuille": [], "couette": []}
+    H, g0 = 24, 1e-6
+    for tau in (0.6, 0.8, 1.2):
+        nu = (tau - 0.5) / 3
+        for q in (0.1, 0.3, 0.5, 0.7, 0.9):
+            geo = G.channel(0, 4, H, q_lo=q, q_hi=q)
+            Hw = geo.info["y_hi"] - geo.info["y_lo"]
+            steps = 2 * int(16 * Hw * Hw / (nu * np.pi ** 2))
+            y = np.arange(geo.ny)
+            rows = slice(1, geo.ny - 1)
+            ex = G.poiseuille_profile(y, geo.info["y_lo"], geo.info["y_hi"], g0, nu)[rows]
+            row = {"tau": tau, "q": q, "steps": steps}
+            for k, (bc, vd) in enumerate(rules):
+                with lbm.Lattice(geo, precision=lbm.LBM_FP64, tau=tau, g=(g0, 0, 0), bc=bc, vibb_density=vd) as lat:
+                    lat.init_equilibrium()
+                    lat.step(steps)
+                    _, u = lat.moments()
+                ux = u[0].reshape(geo.ny, geo.nx)[rows].mean(axis=1)
+                row[names[k]] = float(np.sqrt(np.sum((ux - ex) ** 2) / np.sum(ex ** 2)))
+            out["poiseuille"].append(row)
+    tau = 0.8
+    nu = (tau - 0.5) / 3
+    for scaling, L in [("acoustic", L) for L in (20, 40, 80, 160, 320)] + \
+                      [("diffusive", L) for L in (20, 40, 80, 160, 320)]:
+        # acoustic: wall speed omega1 r1 = 0.01 at every L (Re grows with L);
+        # diffusive: wall speed 0.01 * 20 / L (Re fixed, Mach number -> 0)
+        r1 = L / 4.8
+        om = (0.01 if scaling == "acoustic" else 0.2 / L) / r1
+        geo = G.couette(L, om)
+        steps = 2 * int(11 * (geo.info["r2"] - r1) ** 2 / (nu * np.pi ** 2))
+        fl = np.flatnonzero(geo.solid == 0)
+        x, yy, _ = geo.coords(fl)
+        dx, dy = x - geo.info["center"][0], yy - geo.info["center"][1]
+        r = np.hypot(dx, dy)
+        ex = G.couette_profile(r, r1, geo.info["r2"], om)
+        row = {"scaling": scaling, "L": L, "steps": steps, "fluid_nodes": int(fl.size)}
+        for k, (bc, vd) in enumerate(rules):
+            with lbm.Lattice(geo, precision=lbm.LBM_FP64, tau=tau, bc=bc, vibb_density=vd) as lat:
+                lat.init_equilibrium()
+                lat.step(steps)
+                _, u = lat.moments()
+            ut = (-dy * u[0][fl] + dx * u[1][fl]) / r
+            row[names[k]] = float(np.sqrt(np.sum((ut - ex) ** 2) / np.sum(ex ** 2)))
+        out["couette"].append(row)
+    for scaling in ("acoustic", "diffusive"):
+        c = [row for row in out["couette"] if row["scaling"] == scaling]
+        out[f"couette_order_{scaling}"] = {n: [float(np.log2(c[k][n] / c[k + 1][n])) for k in range(len(c) - 1)]
+                                           for n in names.values()}
+    return out
+
+
 def run_e2e(lbm, torch, geo, steps):
     """Same workload through the C ABI with host buffers: geometry upload,
     initialisation, per step lbm_step(1) + lbm_force to a host array, and the
@@ -673,7 +739,8 @@ def main():
     ap.add_argument("--no-cylinder", action="store_true")
     ap.add_argument("--cylinder-steps", type=int, default=60000)
     ap.add_argument("--sweep-steps", type=int, default=100)
-    ap.add_argument("--part", default="all", choices=["all", "batch", "adjoint", "sweep", "cylinder", "permeability"],
+    ap.add_argument("--part", default="all",
+                    choices=["all", "batch", "adjoint", "sweep", "cylinder", "permeability", "studies"],
                     help="run one section alone (for profiling) and print its JSON")
     ap.add_argument("--batch-domains", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=2000)
@@ -706,6 +773,8 @@ def main():
         if args.part == "cylinder":
             out = [run_cylinder(lbm, torch, 20, args.cylinder_steps // 2),
                    run_cylinder(lbm, torch, 100, args.cylinder_steps)]
+        elif args.part == "studies":
+            out = run_studies(lbm, torch)
         elif args.part == "permeability":
             out = run_permeability(lbm, torch, geometry(args.n), args.perm_steps)
         elif args.part == "sweep":
