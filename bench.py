@@ -230,7 +230,11 @@ def run_precision(lbm, torch, geo, precision, steps, warmup, dist, peak):
                          bytes_per_launch=bulk_bytes, avg_launch_ms=bulk_ms,
                          traffic=(TRAFFIC_PER_FLUID_NODE_PACK_FP32 * nf if s == 4 else None),
                          traffic_source=("ncu dram__bytes_read+write on a 192^3 pack, per fluid node, scaled"
-                                         if s == 4 else None)),
+                                         if s == 4 else None),
+                         # the DRAM rate the kernel sustains on its measured traffic (not only the
+                         # algorithmic bytes), as a fraction of the same peak
+                         traffic_rate_frac=(TRAFFIC_PER_FLUID_NODE_PACK_FP32 * nf / (bulk_ms * 1e-3) / 1e9 / peak
+                                            if s == 4 else None)),
         "kernels": {
             "k_bulk": {"launches": n_launch[2], "avg_ms": bulk_ms, "share": kms[2] / max(sum(kms), 1e-30),
                        "gbs": bulk_gbs, "bytes_per_launch": bulk_bytes},
