@@ -247,9 +247,9 @@ def run_precision(lbm, torch, geo, precision, steps, warmup, dist, peak):
 
 # DRAM bytes (read + write) per fluid node of k_bulk<D3Q19, F32S, 0, 256, 1>
 # on the sphere-pack recipe, from an ncu capture of a 192^3 pack of the same
-# recipe (595.1 MB per launch for 2.83M fluid nodes); traffic grows with the
+# recipe (575.5 MB per launch for 2.83M fluid nodes); traffic grows with the
 # fluid node count, so a full launch moves this figure times its fluid nodes.
-TRAFFIC_PER_FLUID_NODE_PACK_FP32 = 210.4
+TRAFFIC_PER_FLUID_NODE_PACK_FP32 = 203.5
 
 
 # FP64 arithmetic peak of GB300, from unit counts and clock: 152 SMs x 2 FP64

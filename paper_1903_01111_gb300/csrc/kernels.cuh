@@ -25,8 +25,9 @@
 //   k_bulk:  pull streaming f_i(x, t+1) = f+_i(x - e_i, t) (Eq. 1), moments,
 //            Guo-forced BGK (Sec. 2, Eq. feq) -> f+(t+1) into the other
 //            buffer; rho, u(t+1) into the moment cache where flagged.  Ghost
-//            and open slots of the output get zeros so that every written
-//            sector is complete.
+//            and open slots of the output get zeros (through the same store
+//            instructions as the fluid slots) so that every written sector
+//            is complete.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -149,11 +150,14 @@ __device__ __forceinline__ typename P::T equilibrium(int i, typename P::T r, typ
 __device__ __forceinline__ int src_coord(int c, int x, int xm, int xp) { return c == 0 ? x : (c > 0 ? xm : xp); }
 
 // Moments, collision and store of one fluid node.  f holds the pre-collision
-// populations f(x, t+1) in storage form; n < 2^31.
+// populations f(x, t+1) in storage form; n < 2^31.  keep == false (a ghost
+// or open slot in the bulk pass): the same instructions store zeros and the
+// moment cache is not written, so that a warp mixing fluid and ghost slots
+// issues one store per direction instead of two divergent store sequences.
 template <class L, class P>
 __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Params& p, const Relax& rx,
                                               typename P::T* __restrict__ fout, size_t S, uint32_t n_,
-                                              Mom4<typename P::T>* __restrict__ mom, bool cache) {
+                                              Mom4<typename P::T>* __restrict__ mom, bool cache, bool keep = true) {
   using T = typename P::T;
   T r = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
@@ -171,7 +175,7 @@ __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Pa
   const T inv = (T)1 / rho;
   // Guo forcing: velocity shifted by half the body force
   const T ux = (jx + (T)0.5 * gx) * inv, uy = (jy + (T)0.5 * gy) * inv, uz = (jz + (T)0.5 * gz) * inv;
-  if (cache) mom[n_] = Mom4<T>{r, ux, uy, L::D == 3 ? uz : (T)0};
+  if (cache && keep) mom[n_] = Mom4<T>{r, ux, uy, L::D == 3 ? uz : (T)0};
   const T omega = (T)rx.omega;
   const T uu15 = (T)1.5 * (ux * ux + uy * uy + uz * uz);
   if constexpr (L::Q == 9) {
@@ -212,7 +216,7 @@ __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Pa
 #pragma unroll
         for (int k = 0; k < 9; ++k)
           if (mrt_m(k, i) != 0) d += (T)mrt_m(k, i) * dm[k];
-        fout[(size_t)i * S + n_] = f[i] - d;
+        fout[(size_t)i * S + n_] = keep ? f[i] - d : (T)0;
       }
       return;
     }
@@ -248,12 +252,12 @@ __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Pa
         So = fw * eg;
         oi += Sc + So;
       }
-      fout[(size_t)i * S + n_] = oi;
+      fout[(size_t)i * S + n_] = keep ? oi : (T)0;
       if (i != 0) {
         const T feqj = w * (r + rho * (sym - (T)3 * eu));
         T oj = f[j] + omega * (feqj - f[j]);
         if (rx.has_force) oj += Sc - So;
-        fout[(size_t)j * S + n_] = oj;
+        fout[(size_t)j * S + n_] = keep ? oj : (T)0;
       }
     }
   } else {
@@ -269,7 +273,7 @@ __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Pa
       const T w = (T)L::w(0);
       T out = om1 * f[0] + omega * ((w * rho) * ((T)1 - uu15));
       if (rx.has_force) out -= fpre3 * w * ug;
-      fout[n_] = out;
+      fout[n_] = keep ? out : (T)0;
     }
 #pragma unroll
     for (int i = 1; i < L::Q; ++i) {
@@ -286,8 +290,8 @@ __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Pa
         Pv += fw * ((T)3 * eg * eu - ug);
         Mv += fw * eg;
       }
-      fout[(size_t)i * S + n_] = om1 * f[i] + (Pv + Mv);
-      fout[(size_t)j * S + n_] = om1 * f[j] + (Pv - Mv);
+      fout[(size_t)i * S + n_] = keep ? om1 * f[i] + (Pv + Mv) : (T)0;
+      fout[(size_t)j * S + n_] = keep ? om1 * f[j] + (Pv - Mv) : (T)0;
     }
   }
 }
@@ -429,13 +433,14 @@ __global__ void __launch_bounds__(BT, (bulk_blocks_per_sm<L, P, BT, NPT>())) k_b
 #pragma unroll
   for (int j = 0; j < NPT; ++j) {
     if (!live[j]) continue;
-    if (w[j] & (W_GHOST | W_OPEN)) {
+    // ghost and open slots: zeros through the same stores (inputs at rest)
+    const bool fl = !(w[j] & (W_GHOST | W_OPEN));
+    if (!fl) {
 #pragma unroll
-      for (int i = 0; i < L::Q; ++i) fout[(size_t)i * S + k[j]] = (T)0;
-      continue;
+      for (int i = 0; i < L::Q; ++i) f[j][i] = P::shifted ? (T)0 : (T)L::w(i);
     }
     const Relax rx = MULTI ? relax_domain(lay.dom, dom[j]) : relax_params(p);
-    collide_store<L, P>(f[j], p, rx, fout, S, k[j], mom, (w[j] & W_CACHE) != 0);
+    collide_store<L, P>(f[j], p, rx, fout, S, k[j], mom, (w[j] & W_CACHE) != 0, fl);
   }
 }
 
@@ -504,11 +509,10 @@ __global__ void __launch_bounds__(BT, (bulk_seq_blocks_per_sm<P, BT>())) k_bulk_
     const uint32_t w3 = ((uint64_t)k + 2ull * G < S) ? __ldg(lay.word + k + 2 * G) : W_GHOST;
     if (!fluid) {
 #pragma unroll
-      for (int i = 0; i < L::Q; ++i) fout[(size_t)i * S + k] = (T)0;
-    } else {
-      const Relax rx = MULTI ? relax_domain(lay.dom, run.dom) : relax_params(p);
-      collide_store<L, P>(f, p, rx, fout, S, k, mom, (w & W_CACHE) != 0);
+      for (int i = 0; i < L::Q; ++i) f[i] = P::shifted ? (T)0 : (T)L::w(i);
     }
+    const Relax rx = MULTI ? relax_domain(lay.dom, run.dom) : relax_params(p);
+    collide_store<L, P>(f, p, rx, fout, S, k, mom, (w & W_CACHE) != 0, fluid);
     // the next node's run record, loaded before its pulls are needed
     w = w2;
     if ((uint64_t)k + G < S && !(w & (W_GHOST | W_OPEN))) run = load_run_lite<L, MULTI>(lay.runs, w & W_RUN);
