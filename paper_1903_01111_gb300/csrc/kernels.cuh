@@ -507,12 +507,15 @@ __global__ void __launch_bounds__(BT, (bulk_seq_blocks_per_sm<P, BT>())) k_bulk_
       for (int i = 0; i < L::Q; ++i) f[i] = __ldg(fk + ((ptrdiff_t)i * (ptrdiff_t)S + d[i]));
     }
     const uint32_t w3 = ((uint64_t)k + 2ull * G < S) ? __ldg(lay.word + k + 2 * G) : W_GHOST;
+    // (a separate zero-store branch here: the walk serves dense lattices,
+    // where selecting zeros in every store measured about 2 % slower)
     if (!fluid) {
 #pragma unroll
-      for (int i = 0; i < L::Q; ++i) f[i] = P::shifted ? (T)0 : (T)L::w(i);
+      for (int i = 0; i < L::Q; ++i) fout[(size_t)i * S + k] = (T)0;
+    } else {
+      const Relax rx = MULTI ? relax_domain(lay.dom, run.dom) : relax_params(p);
+      collide_store<L, P>(f, p, rx, fout, S, k, mom, (w & W_CACHE) != 0);
     }
-    const Relax rx = MULTI ? relax_domain(lay.dom, run.dom) : relax_params(p);
-    collide_store<L, P>(f, p, rx, fout, S, k, mom, (w & W_CACHE) != 0, fluid);
     // the next node's run record, loaded before its pulls are needed
     w = w2;
     if ((uint64_t)k + G < S && !(w & (W_GHOST | W_OPEN))) run = load_run_lite<L, MULTI>(lay.runs, w & W_RUN);
