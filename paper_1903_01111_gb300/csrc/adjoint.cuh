@@ -22,9 +22,14 @@
 //                atomics; dJ/dq accumulated per link.
 //   k_adj_open   inlet (non-equilibrium extrapolation) and outlet (copy)
 //                transposes into the first and last fluid columns.
-// Every kernel clears the lambda entries it consumes (lambda(s+1) at fluid
-// nodes, the ghost and open entries of lambda(s)), so that the buffer of
-// lambda(s+1) is zero when it becomes the output of the next step back.
+// The buffer of lambda(s+1) becomes the output of the next step back.  There
+// k_adj_bulk assigns every entry (j, m) of a fluid node m whose neighbour
+// m + e_j is a fluid node (each such entry is the pull source of exactly one
+// node), so only the entries that the pass does not assign have to be zero
+// when the link and open kernels add into them: (i', x_f) of every cut link
+// and (j, m) with m + e_j an open node.  The link and open kernels clear
+// those of lambda(s+1) once k_adj_bulk has read it, and clear the ghost and
+// open entries of lambda(s) they consume; no pass clears whole nodes.
 #pragma once
 #include "kernels.cuh"
 
@@ -176,10 +181,6 @@ __global__ void __launch_bounds__(256, (adj_bulk_blocks_per_sm<L, P>())) k_adj_b
       dt = collide_adjoint<L, P>(f, lam, mu, p, rx);
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) lam_out[(size_t)i * S + src[i]] = mu[i];
-      // consumed: clear after the compute (a store right behind the load of
-      // the same address would hold up the warp's following loads)
-#pragma unroll
-      for (int i = 0; i < L::Q; ++i) lam_next[(size_t)i * S + k] = (T)0;
     }
   }
   block_add_keyed<T>(dt, key, dtau);
@@ -199,12 +200,15 @@ __device__ __forceinline__ void scatter_moment_adjoint(T* __restrict__ lam, size
 }
 
 // One thread per link.  lam: lambda(s) under construction (ghost slots hold
-// the weights of the link values).  final_step: add the objective's direct
-// terms J = sum_b wbody[b] . F_b(step) (wbody: [nbody][3] FP64).
+// the weights of the link values); lam_in: lambda(s+1), already read by
+// k_adj_bulk, whose entry (i', x_f) is cleared here.  final_step: add the
+// objective's direct terms J = sum_b wbody[b] . F_b(step) (wbody: [nbody][3]
+// FP64).
 template <class L, class P>
 __global__ void __launch_bounds__(256) k_adj_links(const typename P::T* __restrict__ f,
                                                    const Mom4<typename P::T>* __restrict__ mom,
-                                                   typename P::T* __restrict__ lam, const LinkRec* __restrict__ recs,
+                                                   typename P::T* __restrict__ lam, typename P::T* __restrict__ lam_in,
+                                                   const LinkRec* __restrict__ recs,
                                                    const typename P::T* __restrict__ qv,
                                                    const typename P::T* __restrict__ uwv, int64_t nl, Params p,
                                                    int64_t S_, double* __restrict__ dq_acc, int final_step,
@@ -339,14 +343,38 @@ __global__ void __launch_bounds__(256) k_adj_links(const typename P::T* __restri
   }
   dq_acc[k] += (double)om * dLdq;
   lam[(size_t)i * S + ks] = (T)0;
+  lam_in[(size_t)ip * S + kf] = (T)0;
+}
+
+// Clears in lam_in the entries (j, m) whose neighbour m + e_j is the open
+// node of row y, for the directions j with cx(j) = cx: m is the fluid node
+// next to the open column in row y - cy(j) (table: row_in1 for the inlet,
+// cx = -1; row_out1 for the outlet, cx = +1).
+template <class L, class T>
+__device__ __forceinline__ void clear_open_neighbours(T* __restrict__ lam_in, const Layout& lay, const Params& p, int y,
+                                                      int cx) {
+  const int32_t* __restrict__ next = cx < 0 ? lay.row_in1 : lay.row_out1;
+#pragma unroll
+  for (int j = 0; j < L::Q; ++j) {
+    if (L::cx(j) != cx) continue;
+    int yy = y - L::cy(j);
+    if (yy < 0 || yy >= p.ny) {
+      if (!p.periodic[1]) continue;
+      yy = (yy + p.ny) % p.ny;
+    }
+    const int32_t m = next[yy];
+    if (m >= 0) lam_in[(size_t)j * lay.S + m] = (T)0;
+  }
 }
 
 // Open columns (D2Q9): inlet f+(0) = feq(rho1, u_in) + f+(1) - feq(rho1, u1)
 // and outlet f+(nx-1) = f+(nx-2), transposed into columns 1 and nx-2; the
-// open nodes' entries are then cleared (they are not state).
+// open nodes' entries are then cleared (they are not state), and so are the
+// entries of lambda(s+1) (lam_in, read by k_adj_bulk) that point into an open
+// node.
 template <class L, class P>
-__global__ void k_adj_open(typename P::T* __restrict__ lam, const Mom4<typename P::T>* __restrict__ mom, Layout lay,
-                           Params p) {
+__global__ void k_adj_open(typename P::T* __restrict__ lam, typename P::T* __restrict__ lam_in,
+                           const Mom4<typename P::T>* __restrict__ mom, Layout lay, Params p) {
   using T = typename P::T;
   const int y = blockIdx.x * blockDim.x + threadIdx.x;
   if (y >= p.ny) return;
@@ -379,6 +407,7 @@ __global__ void k_adj_open(typename P::T* __restrict__ lam, const Mom4<typename 
         lam[(size_t)j * S + k1] = l1[j] + l0[j] + sp - (B0 * ((T)L::cx(j) - m1.ux) + B1 * ((T)L::cy(j) - m1.uy));
 #pragma unroll
       for (int j = 0; j < L::Q; ++j) lam[(size_t)j * S + k0] = (T)0;
+      clear_open_neighbours<L, T>(lam_in, lay, p, y, -1);
     }
   }
   if (p.outlet) {
@@ -394,6 +423,7 @@ __global__ void k_adj_open(typename P::T* __restrict__ lam, const Mom4<typename 
       for (int i = 0; i < L::Q; ++i) lam[(size_t)i * S + kl - 1] = a[i] + b[i];
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) lam[(size_t)i * S + kl] = (T)0;
+      clear_open_neighbours<L, T>(lam_in, lay, p, y, 1);
     }
   }
 }
@@ -446,10 +476,11 @@ __global__ void __launch_bounds__(256) k_adj_init(const typename P::T* __restric
 struct AdjointOps {
   void (*bulk)(const void* fin, void* lam_next, void* lam_out, const Layout& lay, const Params& p, double* dtau,
                void* mom, cudaStream_t s);
-  void (*links)(const void* f, const void* mom, void* lam, const LinkRec* recs, const void* q, const void* uw,
-                int64_t nl, const Params& p, int64_t S, double* dq_acc, int final_step, const double* wbody,
-                cudaStream_t s);
-  void (*open)(void* lam, const void* mom, const Layout& lay, const Params& p, cudaStream_t s);
+  // lam: lambda(s) (output); lam_in: lambda(s+1), read by bulk before
+  void (*links)(const void* f, const void* mom, void* lam, void* lam_in, const LinkRec* recs, const void* q,
+                const void* uw, int64_t nl, const Params& p, int64_t S, double* dq_acc, int final_step,
+                const double* wbody, cudaStream_t s);
+  void (*open)(void* lam, void* lam_in, const void* mom, const Layout& lay, const Params& p, cudaStream_t s);
   void (*init)(const void* f0, const void* lam, const Layout& lay, const Params& p, double* dtau, cudaStream_t s);
 };
 
@@ -462,16 +493,16 @@ struct AdjointLaunch {
     k_adj_bulk<L, P><<<blocks_for(lay.S, 256), 256, 0, s>>>((const T*)fin, (T*)lam_next, (T*)lam_out, lay, p, dtau,
                                                            (Mom4<T>*)mom);
   }
-  static void links(const void* f, const void* mom, void* lam, const LinkRec* recs, const void* q, const void* uw,
-                    int64_t nl, const Params& p, int64_t S, double* dq_acc, int final_step, const double* wbody,
-                    cudaStream_t s) {
+  static void links(const void* f, const void* mom, void* lam, void* lam_in, const LinkRec* recs, const void* q,
+                    const void* uw, int64_t nl, const Params& p, int64_t S, double* dq_acc, int final_step,
+                    const double* wbody, cudaStream_t s) {
     if (nl == 0) return;
-    k_adj_links<L, P><<<blocks_for(nl, 256), 256, 0, s>>>((const T*)f, (const Mom4<T>*)mom, (T*)lam, recs,
-                                                         (const T*)q, (const T*)uw, nl, p, S, dq_acc, final_step,
-                                                         wbody);
+    k_adj_links<L, P><<<blocks_for(nl, 256), 256, 0, s>>>((const T*)f, (const Mom4<T>*)mom, (T*)lam, (T*)lam_in,
+                                                         recs, (const T*)q, (const T*)uw, nl, p, S, dq_acc,
+                                                         final_step, wbody);
   }
-  static void open(void* lam, const void* mom, const Layout& lay, const Params& p, cudaStream_t s) {
-    k_adj_open<L, P><<<blocks_for(p.ny, 128), 128, 0, s>>>((T*)lam, (const Mom4<T>*)mom, lay, p);
+  static void open(void* lam, void* lam_in, const void* mom, const Layout& lay, const Params& p, cudaStream_t s) {
+    k_adj_open<L, P><<<blocks_for(p.ny, 128), 128, 0, s>>>((T*)lam, (T*)lam_in, (const Mom4<T>*)mom, lay, p);
   }
   static void init(const void* f0, const void* lam, const Layout& lay, const Params& p, double* dtau,
                    cudaStream_t s) {

@@ -104,6 +104,8 @@ struct Layout {
   const RunRec* runs;
   const int32_t* row_first;    // [ny*nz] storage index of the row's first stored node (-1: none)
   const int32_t* row_last;     // [ny*nz] ... last stored node
+  const int32_t* row_in1;      // [ny*nz] storage index of the fluid node at x = 1 (open inlet rows), else -1
+  const int32_t* row_out1;     // [ny*nz] ... at x = width - 2 (open outlet rows), else -1
   const DomPar* dom;           // [ndom] when ndom > 1, else null
   const int32_t* row_dom;      // [ny*nz] domain of each row when ndom > 1
   int32_t ndom;

@@ -106,7 +106,7 @@ struct lbm_lattice_s {
   // state over stored nodes
   DeviceBuf f[2], mom;
   // layout
-  DeviceBuf word, node_of, runs, row_first, row_last;
+  DeviceBuf word, node_of, runs, row_first, row_last, row_in1, row_out1;
   Layout lay{};
   // batch: domains along the last axis (empty: one domain run by cfg)
   std::vector<lbm_domain> domains;
@@ -142,8 +142,9 @@ struct lbm_lattice_s {
 namespace {
 
 int64_t device_bytes(const lbm_handle h) {
-  const DeviceBuf* all[] = {&h->f[0], &h->f[1], &h->mom,  &h->word, &h->node_of, &h->runs, &h->row_first,
-                            &h->row_last, &h->recs, &h->q,    &h->uw,   &h->force,   &h->dom,  &h->row_dom};
+  const DeviceBuf* all[] = {&h->f[0],     &h->f[1],     &h->mom,      &h->word, &h->node_of, &h->runs,
+                            &h->row_first, &h->row_last, &h->row_in1, &h->row_out1, &h->recs, &h->q,
+                            &h->uw,       &h->force,    &h->dom,      &h->row_dom};
   int64_t s = 0;
   for (auto* b : all) s += (int64_t)b->bytes;
   return s;
@@ -184,8 +185,9 @@ void drop_graphs(lbm_handle h) {
 }
 
 void release_geometry(lbm_handle h) {
-  DeviceBuf* all[] = {&h->f[0], &h->f[1], &h->mom, &h->word, &h->node_of, &h->runs, &h->row_first,
-                      &h->row_last, &h->recs, &h->q, &h->uw, &h->dom, &h->row_dom};
+  DeviceBuf* all[] = {&h->f[0],      &h->f[1],     &h->mom,     &h->word,     &h->node_of, &h->runs, &h->row_first,
+                      &h->row_last, &h->row_in1, &h->row_out1, &h->recs, &h->q,       &h->uw,   &h->dom,
+                      &h->row_dom};
   for (auto* b : all) release(*b);
   h->lay = Layout{};
 }
@@ -592,6 +594,15 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
           return fail(LBM_ERR_INVALID_ARG, "inlet node (0,%lld) has no fluid node at x = 1", (long long)y);
         m[nx * y + 1] |= H_CACHE;
       }
+  // the outlet copies the fluid node before it
+  if (c.outlet)
+    for (int64_t r = 0; r < rows; ++r) {
+      const int64_t xo = rwidth[r] - 1;
+      if (!(m[nx * r + xo] & H_OPEN)) continue;
+      if (xo < 1 || (m[nx * r + xo - 1] & (H_SOLID | H_OPEN)))
+        return fail(LBM_ERR_INVALID_ARG, "outlet node (%lld, row %lld) has no fluid node before it", (long long)xo,
+                    (long long)r);
+    }
   // link order: (node, dir) -- usually the input order already -- then
   // stably by body; reject duplicate (node, dir)
   raw_vec<int64_t> order(n_links);
@@ -697,6 +708,15 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
       if (k < 0) continue;
       if (row_first[r] < 0) row_first[r] = k;
       row_last[r] = k;
+    }
+  // open columns: the fluid node next to the inlet (x = 1) and to the outlet
+  // (x = width - 2) of every row, -1 where there is none
+  std::vector<int32_t> row_in1(rows, -1), row_out1(rows, -1);
+  if (c.inlet || c.outlet)
+    for (int64_t r = 0; r < rows; ++r) {
+      const int64_t a = nx * r + 1, b = nx * r + rwidth[r] - 2;
+      if (c.inlet && nx > 1 && !(m[a] & (H_SOLID | H_OPEN))) row_in1[r] = sidx[a];
+      if (c.outlet && rwidth[r] > 1 && !(m[b] & (H_SOLID | H_OPEN))) row_out1[r] = sidx[b];
     }
   // neighbour-row slots in use: source-row offsets (dy, dz) = -(cy, cz)
   // and the range of x offsets pulled from each such row
@@ -859,6 +879,8 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
   if (st == LBM_OK) st = upload(h->runs, runs.data(), sizeof(RunRec) * runs.size());
   if (st == LBM_OK) st = upload(h->row_first, row_first.data(), sizeof(int32_t) * rows);
   if (st == LBM_OK) st = upload(h->row_last, row_last.data(), sizeof(int32_t) * rows);
+  if (st == LBM_OK) st = upload(h->row_in1, row_in1.data(), sizeof(int32_t) * rows);
+  if (st == LBM_OK) st = upload(h->row_out1, row_out1.data(), sizeof(int32_t) * rows);
   if (st == LBM_OK) st = upload(h->recs, recs.data(), sizeof(LinkRec) * n_links);
   if (st == LBM_OK && ndom > 0) {
     std::vector<DomPar> dp(ndom);
@@ -911,6 +933,8 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
   h->lay.runs = (const RunRec*)h->runs.p;
   h->lay.row_first = (const int32_t*)h->row_first.p;
   h->lay.row_last = (const int32_t*)h->row_last.p;
+  h->lay.row_in1 = (const int32_t*)h->row_in1.p;
+  h->lay.row_out1 = (const int32_t*)h->row_out1.p;
   h->lay.dom = ndom > 0 ? (const DomPar*)h->dom.p : nullptr;
   h->lay.row_dom = ndom > 0 ? (const int32_t*)h->row_dom.p : nullptr;
   h->lay.ndom = std::max(ndom, 1);
@@ -1307,9 +1331,9 @@ lbm_status lbm_adjoint_step(lbm_handle h, int32_t body, const double dJ_dF[3], i
         if (open) h->ops.open(state, h->mom.p, h->lay, h->p, h->stream);
       }
       h->adj.bulk(state, lam[l].p, lam[l ^ 1].p, h->lay, h->p, dtau, h->mom.p, h->stream);
-      h->adj.links(state, h->mom.p, lam[l ^ 1].p, (const LinkRec*)h->recs.p, h->q.p, h->uw.p, nl, h->p, S,
-                   (double*)dq.p, (last && j == m - 1) ? 1 : 0, wdev, h->stream);
-      if (open) h->adj.open(lam[l ^ 1].p, h->mom.p, h->lay, h->p, h->stream);
+      h->adj.links(state, h->mom.p, lam[l ^ 1].p, lam[l].p, (const LinkRec*)h->recs.p, h->q.p, h->uw.p, nl, h->p,
+                   S, (double*)dq.p, (last && j == m - 1) ? 1 : 0, wdev, h->stream);
+      if (open) h->adj.open(lam[l ^ 1].p, lam[l].p, h->mom.p, h->lay, h->p, h->stream);
       l ^= 1;
     }
     CUDA_TRY(cudaGetLastError());
