@@ -269,6 +269,21 @@ def test_invalid_geometry_is_rejected(L):
     lat.close()
 
 
+def test_outlet_needs_a_fluid_node_before_it(L):
+    """The zero-gradient outlet copies the fluid node before it (Sec. 4.3): an
+    outlet row whose node at x = nx - 2 is solid (a small body touching the
+    outlet column) is rejected by lbm_set_geometry."""
+    geo = G.cylinder_channel(nx=40, ny_fluid=10, center=(38.0, 5.5), radius=0.6)
+    s = geo.solid.reshape(geo.ny, geo.nx)
+    assert s[:, geo.nx - 2].any() and not s[1:-1, geo.nx - 1].any()
+    lat = L.Lattice(None, stencil=0, nx=geo.nx, ny=geo.ny, nz=1, periodic=geo.periodic, tau=0.8, inlet=1,
+                    outlet=1, inlet_umax=0.05, inlet_y0=0.5, inlet_y1=10.5)
+    with pytest.raises(L.LBMError) as ex:
+        lat.set_geometry(geo.solid, geo.links)
+    assert ex.value.status == L.LBM_ERR_INVALID_ARG and "outlet" in str(ex.value)
+    lat.close()
+
+
 def test_bad_configs_are_rejected(L):
     for kw in (dict(tau=0.5), dict(stencil=0, nz=2), dict(stencil=1, collision=1), dict(collision=5),
                dict(stencil=1, inlet=1, periodic=(0, 1, 1)), dict(precision=7), dict(vibb_density=3)):
