@@ -21,7 +21,10 @@ in the oracle fails at least one of them:
   exact at tau = 1/2 + sqrt(3)/4, second-order convergence of Bouzidi and
   VIBB with walls at off-node q, the moving-wall case of Sec. 4.1; circular
   Couette (Sec. 4.2, Eq. exact2) convergence; momentum-exchange force equal
-  to the momentum budget at every step; zero lift on a mirror-symmetric body.
+  to the momentum budget at every step; zero lift on a mirror-symmetric body;
+  the D3Q19 plane channel: the same curvature, force balance and magic-tau
+  exactness, no cross-flow, and the D2Q9 profile (the plane flow sees only
+  the weights of each e_y class, which the two stencils share).
 """
 import os
 
@@ -322,6 +325,54 @@ def test_poiseuille_second_order(bc, q):
     orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert orders.min() > 1.8, (errs, orders)
     assert errs[-1] < 2.5e-3
+
+
+def _poiseuille3(bc, q_lo, q_hi, H, tau, g0=1e-6):
+    """D3Q19 plane channel (walls normal to y, periodic in x and z, nz = 2)."""
+    g = G.channel(1, 2, H, nz=2, q_lo=q_lo, q_hi=q_hi)
+    cfg = _cfg_for(g, tau=tau, g=(g0, 0, 0), bc=bc)
+    st = O.init(cfg, g.solid)
+    nu = (tau - 0.5) / 3
+    Hw = g.info["y_hi"] - g.info["y_lo"]
+    F = O.run(cfg, g.solid, g.links, st, int(32 * Hw * Hw / (nu * np.pi ** 2)))
+    u = st.u.reshape(g.nz, g.ny, g.nx, 3)
+    ex = G.poiseuille_profile(np.arange(1, H + 1), g.info["y_lo"], g.info["y_hi"], g0, nu)
+    return u, ex, F, g
+
+
+def test_d3q19_poiseuille_curvature_force_balance_and_symmetry():
+    """The plane Poiseuille pins on D3Q19: bulk second differences of u_x equal
+    -g/nu, the steady wall force equals the body force on the fluid, and the
+    flow is the same on every x and z with no cross-flow."""
+    u, ex, F, g = _poiseuille3(2, 0.3, 0.3, 24, 0.8)
+    ux = u[0, 1:25, 0, 0]
+    d2 = ux[2:] - 2 * ux[1:-1] + ux[:-2]
+    np.testing.assert_allclose(d2[2:-2], -1e-6 / 0.1, rtol=1e-7)
+    assert abs(F[0, 0] - g.fluid_count() * 1e-6) < 1e-9 * g.fluid_count() * 1e-6
+    assert np.array_equal(u[..., 0], np.broadcast_to(u[0:1, :, 0:1, 0], u[..., 0].shape))
+    assert np.abs(u[..., 1:]).max() < 1e-14
+
+
+def test_d3q19_poiseuille_halfway_exact_at_magic_tau():
+    """The half-way wall sits exactly half a link out at (tau - 1/2)^2 = 3/16
+    on D3Q19 as on D2Q9 (the plane flow sees only the y-moments of the
+    stencil)."""
+    u, ex, _, _ = _poiseuille3(0, 0.5, 0.5, 12, 0.5 + np.sqrt(3) / 4)
+    assert np.abs(u[0, 1:13, 0, 0] - ex).max() / ex.max() < 1e-9
+
+
+@pytest.mark.parametrize("bc", [1, 2])
+def test_d3q19_plane_channel_equals_d2q9(bc):
+    """Plane Poiseuille flow depends on the velocity set only through the
+    weights of each e_y class, which D2Q9 and D3Q19 share (1/6 for e_y = +-1,
+    2/3 for e_y = 0), so the two stencils give the same steady profile: a
+    stencil-specific slip in either (a weight, a direction, a link rule
+    indexed wrong) separates them."""
+    u3, ex, _, _ = _poiseuille3(bc, 0.3, 0.7, 16, 0.8)
+    ux2, ex2, _, _ = _poiseuille(bc, 0.3, 0.7, 16, 0.8)
+    np.testing.assert_allclose(u3[0, 1:17, 0, 0], ux2, rtol=1e-9)
+    err = np.sqrt(((ux2 - ex2) ** 2).sum() / (ex2 ** 2).sum())
+    assert 1e-4 < err < 1e-2
 
 
 def test_poiseuille_moving_wall_paper_case():
