@@ -197,9 +197,11 @@ lbm_status lbm_set_domains(lbm_handle h, const lbm_domain* d, int32_t n);
  * records on the host.  Everything is copied and checked: node in range and
  * fluid, dir in 1..Q-1, q in (0,1], x_s solid and inside the lattice on
  * non-periodic axes, bc and body in range, no duplicate (node, dir), and
- * every fluid node with a solid neighbour in direction i' has a link.  The
- * second fluid node x_ff = x_f - e_i' of a link falls back to x_f when it is
- * not a fluid node (narrow gaps).  Invalidates the state: call
+ * every fluid node with a solid neighbour in direction i' has a link; with
+ * open columns (Sec. 4.3), the nodes next to an open inlet (x = 1) and
+ * before an open outlet (x = width - 2) are fluid nodes.  The second fluid
+ * node x_ff = x_f - e_i' of a link falls back to x_f when it is not a fluid
+ * node (narrow gaps).  Invalidates the state: call
  * lbm_init_equilibrium or lbm_set_distributions next.
  * Errors: INVALID_ARG (message names the first bad item), OOM, CUDA. */
 lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* links, int64_t n_links);
