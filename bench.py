@@ -83,6 +83,13 @@ class Clocks:
         except Exception:
             self.proc.kill()
             out = ""
+        return self.summarise(out)
+
+    @staticmethod
+    def summarise(out):
+        """Median SM clock under load (samples above 200 W, else all), the
+        maximum clock and the throttle reasons seen under load, from the
+        noheader/nounits CSV lines of FIELDS."""
         rows = []
         for line in out.splitlines():
             parts = [p.strip() for p in line.split(",")]
