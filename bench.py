@@ -146,17 +146,19 @@ AUTOTUNE = True  # --tuning default: the stencil's default shapes (reproducible 
 
 BULK_SHAPE = -1  # --bulk-shape: force one bulk kernel shape (profiling a given kernel)
 LINK_SEQ = 0     # --link-seq: force the link kernel's links per thread
+FUSED = -1       # --fused 0/1: force the step form (link kernel + bulk kernel, or the fused kernel)
 
 
 def _tune(lat, steps_per_trial):
     """The lattice's launch shapes: autotuned on its live state, the
-    defaults, or the forced bulk shape / links per thread (where the stencil
-    has them)."""
-    if BULK_SHAPE >= 0 or LINK_SEQ:
+    defaults, or the forced bulk shape / links per thread / step form (where
+    the stencil has them)."""
+    if BULK_SHAPE >= 0 or LINK_SEQ or FUSED >= 0:
+        fused = 1 if FUSED < 0 else FUSED
         try:
-            lat.set_tuning(bulk_shape=BULK_SHAPE, link_seq=LINK_SEQ or 1)
+            lat.set_tuning(bulk_shape=BULK_SHAPE, link_seq=LINK_SEQ or 1, fused=fused)
         except Exception:
-            lat.set_tuning(bulk_shape=-1, link_seq=LINK_SEQ or 1)
+            lat.set_tuning(bulk_shape=-1, link_seq=LINK_SEQ or 1, fused=fused)
         return lat.tuning()
     if AUTOTUNE:
         return lat.autotune(steps_per_trial)[0]
@@ -222,41 +224,60 @@ def run_precision(lbm, torch, geo, precision, steps, warmup, dist, peak):
     nf, nl, N = info.n_fluid, info.n_links, info.n_nodes
     world = dist.get_world_size() if dist is not None else 1
     mlups = replica_mlups(world, nf, steps, ms)
-    bulk_ms = kms[2] / max(n_launch[2], 1)
+    fused = bool(tuning.fused) and nl > 0
+    main_ms = kms[2] / max(n_launch[2], 1)
     link_ms = kms[0] / max(n_launch[0], 1)
     bulk_bytes = nf * (2 * Q3 * s + 1)  # algorithmic bytes per bulk launch
-    # per link: its 16 B record, q, f+_i'(x_f), f+_i'(x_ff), the moment records at x_f and x_ff, one write
-    link_bytes = nl * (16 + s + 2 * s + 2 * 4 * s + s)
-    bulk_gbs = bulk_bytes / (bulk_ms * 1e-3) / 1e9
-    link_gbs = link_bytes / (link_ms * 1e-3) / 1e9
+    link_bytes = nl * LINK_BYTES(s)
+    fused_bytes = bulk_bytes + nl * FUSED_LINK_BYTES(s) + info.n_cached * 4 * s
+    main_bytes = fused_bytes if fused else bulk_bytes
+    name = "k_fused" if fused else "k_bulk"
+    traffic = TRAFFIC_PER_FLUID_NODE_PACK_FP32.get(name) if s == 4 else None
+    kernels = {name: {"launches": n_launch[2], "avg_ms": main_ms, "share": kms[2] / max(sum(kms), 1e-30),
+                      "gbs": main_bytes / (main_ms * 1e-3) / 1e9, "bytes_per_launch": main_bytes}}
+    if not fused:
+        kernels["k_links"] = {"launches": n_launch[0], "avg_ms": link_ms, "share": kms[0] / max(sum(kms), 1e-30),
+                              "gbs": link_bytes / (link_ms * 1e-3) / 1e9, "bytes_per_launch": link_bytes}
+    step_bytes = fused_bytes if fused else bulk_bytes + link_bytes
     return {
         "mlups": mlups, "ms_per_step": ms / steps, "n_fluid": nf, "n_links": nl, "n_nodes": N,
-        "tuning": tuning.as_dict(),
+        "n_cached": info.n_cached, "tuning": tuning.as_dict(),
         "launches": int(sum(n_launch)), "force": F.tolist(),
-        "roofline": dict(roofline_entry(bulk_bytes, nf * FLOPS_PER_NODE[Q3], bulk_ms, s, peak), kernel="k_bulk",
-                         bytes_per_launch=bulk_bytes, avg_launch_ms=bulk_ms,
-                         traffic=(TRAFFIC_PER_FLUID_NODE_PACK_FP32 * nf if s == 4 else None),
+        "roofline": dict(roofline_entry(main_bytes, nf * FLOPS_PER_NODE[Q3], main_ms, s, peak), kernel=name,
+                         bytes_per_launch=main_bytes, avg_launch_ms=main_ms,
+                         traffic=(traffic * nf if traffic else None),
                          traffic_source=("ncu dram__bytes_read+write on a 192^3 pack, per fluid node, scaled"
-                                         if s == 4 else None),
+                                         if traffic else None),
                          # the DRAM rate the kernel sustains on its measured traffic (not only the
                          # algorithmic bytes), as a fraction of the same peak
-                         traffic_rate_frac=(TRAFFIC_PER_FLUID_NODE_PACK_FP32 * nf / (bulk_ms * 1e-3) / 1e9 / peak
-                                            if s == 4 else None)),
-        "kernels": {
-            "k_bulk": {"launches": n_launch[2], "avg_ms": bulk_ms, "share": kms[2] / max(sum(kms), 1e-30),
-                       "gbs": bulk_gbs, "bytes_per_launch": bulk_bytes},
-            "k_links": {"launches": n_launch[0], "avg_ms": link_ms, "share": kms[0] / max(sum(kms), 1e-30),
-                        "gbs": link_gbs, "bytes_per_launch": link_bytes},
-        },
-        "step_gbs": (bulk_bytes + link_bytes) / (ms / steps * 1e-3) / 1e9,
+                         traffic_rate_frac=(traffic * nf / (main_ms * 1e-3) / 1e9 / peak if traffic else None)),
+        "kernels": kernels,
+        "step_gbs": step_bytes / (ms / steps * 1e-3) / 1e9,
+        "step_bytes": step_bytes,
     }
 
 
-# DRAM bytes (read + write) per fluid node of k_bulk<D3Q19, F32S, 0, 256, 1>
-# on the sphere-pack recipe, from an ncu capture of a 192^3 pack of the same
-# recipe (575.5 MB per launch for 2.83M fluid nodes); traffic grows with the
-# fluid node count, so a full launch moves this figure times its fluid nodes.
-TRAFFIC_PER_FLUID_NODE_PACK_FP32 = 203.5
+# DRAM bytes (read + write) per fluid node, by kernel, on the sphere-pack
+# recipe from an ncu capture of a 192^3 pack of the same recipe; traffic
+# grows with the fluid node count, so a full launch moves this figure times
+# its fluid nodes.  k_bulk<D3Q19, F32S, 0, 256, 1>: 575.5 MB per launch for
+# 2.83M fluid nodes.
+TRAFFIC_PER_FLUID_NODE_PACK_FP32 = {"k_bulk": 203.5}
+
+
+def LINK_BYTES(s):
+    """Algorithmic bytes per link of the link kernel: its 16 B record, q,
+    f+_i'(x_f), f+_i'(x_ff), the moment records at x_f and x_ff (4 reals
+    each) and the ghost write."""
+    return 16 + s + 2 * s + 2 * 4 * s + s
+
+
+def FUSED_LINK_BYTES(s):
+    """Algorithmic bytes per link that the fused step adds to the pull pass:
+    x_ff's storage index and the metadata word (4 B each), q and
+    f+_i'(x_f) (f+_i'(x_ff) is the node's own pull); the moment records
+    (4 reals per cached node, read once) are added per cached node."""
+    return 8 + 2 * s
 
 
 # FP64 arithmetic peak of GB300, from unit counts and clock: 152 SMs x 2 FP64
@@ -424,8 +445,12 @@ def run_batch(lbm, torch, peak, n_domains=256, seed=0, steps=2000, warmup=10, ad
     lat.close()
     nf = b.n_fluid
     s = 4
-    bulk_ms = kms[2] / max(nlaunch[2], 1)
-    bulk_bytes = nf * (2 * 9 * s + 1)
+    fused = bool(tuning.fused) and info.n_links > 0
+    main_name = "k_fused" if fused else "k_bulk"
+    main_ms = kms[2] / max(nlaunch[2], 1)
+    main_bytes = nf * (2 * 9 * s + 1)
+    if fused:
+        main_bytes += info.n_links * FUSED_LINK_BYTES(s) + info.n_cached * 4 * s
     mlups32 = sharded_mlups(dist, torch, nf, steps - warmup, ms32)
     # per-domain FP64 lattices on one stream
     lats = []
@@ -450,7 +475,8 @@ def run_batch(lbm, torch, peak, n_domains=256, seed=0, steps=2000, warmup=10, ad
     rel = rel[np.isfinite(rel)]
     # batched adjoint of the summed drag
     lat = lbm.batch_lattice(b, precision=lbm.LBM_FP32_SHIFTED, bc=lbm.LBM_BC_VIBB, stream=stream.cuda_stream)
-    lat.set_tuning(bulk_shape=tuning.bulk_shape, link_threads=tuning.link_threads, graph_steps=tuning.graph_steps)
+    lat.set_tuning(bulk_shape=tuning.bulk_shape, link_threads=tuning.link_threads, graph_steps=tuning.graph_steps,
+                   link_seq=tuning.link_seq, fused=tuning.fused)
     lat.init_equilibrium(u=u0)
     w = np.zeros((b.n_bodies, 3))
     w[:, 0] = 1.0
@@ -464,10 +490,10 @@ def run_batch(lbm, torch, peak, n_domains=256, seed=0, steps=2000, warmup=10, ad
         "tuning": tuning.as_dict(), "diverged_domains": diverged,
         "fp32_batched": {"value": mlups32, "unit": "MLUPS", "ms_per_step": ms32 / (steps - warmup),
                          "steps_timed": steps - warmup,
-                         "roofline": dict(roofline_entry(bulk_bytes, nf * FLOPS_PER_NODE[9], bulk_ms, s, peak),
-                                          kernel="k_bulk", bytes_per_launch=bulk_bytes, avg_launch_ms=bulk_ms),
+                         "roofline": dict(roofline_entry(main_bytes, nf * FLOPS_PER_NODE[9], main_ms, s, peak),
+                                          kernel=main_name, bytes_per_launch=main_bytes, avg_launch_ms=main_ms),
                          "kernel_ms": {"k_links": kms[0] / max(nlaunch[0], 1), "k_open": kms[1] / max(nlaunch[1], 1),
-                                       "k_bulk": bulk_ms}},
+                                       main_name: main_ms}},
         "fp64_per_domain": {"value": mlups64, "unit": "MLUPS", "ms_per_step": s64 * 1e3 / (steps - warmup),
                             "launches_per_step": 3 * n_domains},
         "speedup_fp32_batched_vs_fp64_per_domain": mlups32 / mlups64,
@@ -766,11 +792,14 @@ def main():
                     help="force this bulk kernel shape where the stencil has it (profiling)")
     ap.add_argument("--link-seq", type=int, default=0, choices=[0, 1, 4],
                     help="force the link kernel's links per thread (profiling)")
+    ap.add_argument("--fused", type=int, default=-1, choices=[-1, 0, 1],
+                    help="force the step form: 0 link kernel + bulk kernel, 1 fused kernel (profiling)")
     args = ap.parse_args()
-    global AUTOTUNE, BULK_SHAPE, LINK_SEQ
+    global AUTOTUNE, BULK_SHAPE, LINK_SEQ, FUSED
     AUTOTUNE = args.tuning == "auto"
     BULK_SHAPE = args.bulk_shape
     LINK_SEQ = args.link_seq
+    FUSED = args.fused
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -166,12 +166,24 @@ typedef struct {
  *                 takes link_seq rounds of consecutive links, loading the
  *                 next round's record while it evaluates the current one);
  *                 0 on input means 1.
+ *  fused          1 (the default): a lattice with cut links runs each step
+ *                 as one kernel: a block stages its nodes' pulls in shared
+ *                 memory, evaluates the link rules of its nodes into the
+ *                 staged slots of the link directions and collides from
+ *                 there (the link values never go through device memory);
+ *                 the bulk shape then only gives its threads per block (256
+ *                 for the shapes with two or sequential nodes per thread).
+ *                 0: a link kernel writes each link's value into the ghost
+ *                 slot of its solid neighbour and the bulk kernel pulls it
+ *                 (the adjoint's recompute always takes this form).  Both
+ *                 give the same populations up to rounding.
  * Shapes of the same kernel (same nodes per thread in parallel and in
- * sequence) give the same bits (force sums may differ in the last place, as
- * FP64 atomics are unordered); the kernels are separate compilations of the
- * same arithmetic and agree to rounding. */
+ * sequence, same links per thread) give the same bits (force sums may differ
+ * in the last place, as FP64 atomics are unordered); different kernels are
+ * separate compilations of the same arithmetic and agree to rounding. */
 typedef struct {
   int32_t bulk_shape, link_threads, graph_steps, link_seq;
+  int32_t fused;
 } lbm_tuning;
 
 /* Create a lattice: validates cfg, allocates the device state (two

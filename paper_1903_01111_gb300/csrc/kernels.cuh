@@ -58,7 +58,8 @@ struct __align__(4 * sizeof(T)) Mom4 {
   T r, ux, uy, uz;
 };
 
-// Per stored node word: run id of a fluid node, or the open / ghost bit.
+// Per stored node word: run id of a fluid node and its cache flag, or the
+// open / ghost bit.
 constexpr uint32_t W_RUN = (1u << 29) - 1;
 constexpr uint32_t W_CACHE = 1u << 29;
 constexpr uint32_t W_OPEN = 1u << 30;
@@ -568,6 +569,13 @@ __device__ __forceinline__ typename P::T link_value(int rule, typename P::T q, t
     const T inv2q = (T)1 / two_q;
     return (fpf + wall) * inv2q + (two_q - (T)1) * inv2q * fpi;
   }
+  if (rule == 3) {
+    // Yu: the population reaching the wall, linear between x_f and x_ff at
+    // q - 1 along e_i', bounced back; then x_f linear between x_w (at q)
+    // and x_ff (at -1), whose f_i(x_ff, t+1) is f+_i(x_f, t) in pull form
+    const T i1q = (T)1 / ((T)1 + q);
+    return (q * fpf + ((T)1 - q) * fpff + wall) * i1q + q * i1q * fpi;
+  }
   const T rhof = P::shifted ? (T)rho0 + mf.r : mf.r;
   const T rhoff = P::shifted ? (T)rho0 + mff.r : mff.r;
   // Eq. (rhod) in storage form; optionally rho_d = rho_f when q > 1/2
@@ -599,6 +607,56 @@ __device__ __forceinline__ typename P::T link_value(int rule, typename P::T q, t
   return eq_dir<P>(w, ex, ey, ez, rd, rhod, udx, udy, udz) + nd + wall;
 }
 
+// Direction table of the link kernels in shared memory (filled by the
+// block's first Q threads; the caller synchronises).
+template <class L, class T>
+__device__ __forceinline__ void fill_dir_table(DirTable<T, L::Q>& tab) {
+  if (threadIdx.x < L::Q) {
+    const int d = threadIdx.x;
+    tab.off[d] = 0;
+    tab.opp[d] = L::opp(d);
+    tab.w[d] = (T)L::w(d);
+    tab.e[d][0] = (T)L::cx(d);
+    tab.e[d][1] = (T)L::cy(d);
+    tab.e[d][2] = (T)L::cz(d);
+  }
+}
+
+// Missing population f_i(x_f, t+1) of the link (x_f = node, i' = ip) from
+// the post-collision state f (storage form, [Q][N]) and the moment cache at
+// time t; x_ff = ff (x_f when there is no second fluid node).  fpf receives
+// f+_i'(x_f, t), the link's other term of the momentum exchange.  Each rule
+// loads only what it reads.
+template <class L, class P>
+__device__ __forceinline__ typename P::T eval_link(const DirTable<typename P::T, L::Q>& tab,
+                                                   const typename P::T* __restrict__ f,
+                                                   const Mom4<typename P::T>* __restrict__ mom, size_t N, int ip,
+                                                   int rule, typename P::T q, uint32_t node, uint32_t ff,
+                                                   typename P::T uw0, typename P::T uw1, typename P::T uw2,
+                                                   const Params& p, typename P::T& fpf) {
+  using T = typename P::T;
+  const int i = tab.opp[ip];
+  const T ex = tab.e[ip][0], ey = tab.e[ip][1], ez = tab.e[ip][2];
+  const T w = tab.w[ip];
+  fpf = f[(size_t)ip * N + node];
+  T fpff = 0, fpi = 0;
+  Mom4<T> mf{0, 0, 0, 0}, mff{0, 0, 0, 0};
+  if (rule == 1) {
+    if (q <= (T)0.5)
+      fpff = f[(size_t)ip * N + ff];
+    else
+      fpi = f[(size_t)i * N + node];
+  } else if (rule == 2) {
+    fpff = f[(size_t)ip * N + ff];
+    mf = mom[node];
+    mff = mom[ff];
+  } else if (rule == 3) {
+    fpff = f[(size_t)ip * N + ff];
+    fpi = f[(size_t)i * N + node];
+  }
+  return link_value<P>(rule, q, w, ex, ey, ez, fpf, fpff, fpi, mf, mff, uw0, uw1, uw2, p.rho0, p.vibb_local_rho);
+}
+
 // One thread per link.  recs: storage indices and metadata; qv: q in
 // storage precision; uw: [D][nl] wall velocities or null.  force: the step's
 // accumulator slot [MAX_BODIES][3] (FP64).
@@ -609,6 +667,7 @@ __device__ __forceinline__ typename P::T link_value(int rule, typename P::T q, t
 //   Bouzidi   q <= 1/2: 2q f+_i'(x_f) + (1-2q) f+_i'(x_ff) + wall   (Eq. q_less)
 //             q >  1/2: (f+_i'(x_f) + wall)/(2q) + (2q-1)/(2q) f+_i(x_f)  (Eq. q_larger)
 //   VIBB      feq_i'(rho_d, u_d) + fneq_i'(x_d) + wall                 (Sec. 3.1)
+//   Yu        (q f+_i'(x_f) + (1-q) f+_i'(x_ff) + wall)/(1+q) + q/(1+q) f+_i(x_f)  (Sec. 3)
 // with wall = 6 w rho0 (e_i . u_w).
 template <class L, class P, int SEQ>
 __global__ void __launch_bounds__(256) k_links(typename P::T* __restrict__ f, const Mom4<typename P::T>* __restrict__ mom,
@@ -617,15 +676,7 @@ __global__ void __launch_bounds__(256) k_links(typename P::T* __restrict__ f, co
                                                double* __restrict__ force, Params p, int64_t S_) {
   using T = typename P::T;
   __shared__ DirTable<T, L::Q> tab;
-  if (threadIdx.x < L::Q) {
-    const int d = threadIdx.x;
-    tab.off[d] = 0;
-    tab.opp[d] = L::opp(d);
-    tab.w[d] = (T)L::w(d);
-    tab.e[d][0] = (T)L::cx(d);
-    tab.e[d][1] = (T)L::cy(d);
-    tab.e[d][2] = (T)L::cz(d);
-  }
+  fill_dir_table<L>(tab);
   __syncthreads();
   // the block takes SEQ rounds of blockDim consecutive links; the next
   // round's record and q are loaded while the current link is processed
@@ -659,37 +710,21 @@ __global__ void __launch_bounds__(256) k_links(typename P::T* __restrict__ f, co
       const int ip = (int)(rec.meta & 31);
       const int rule = (int)((rec.meta >> 5) & 3);
       const int body = (int)(rec.meta >> 7) - 1;
-      const uint32_t node = rec.kf, ff = rec.kff, s = rec.ks;
-      const int i = tab.opp[ip];
-      const T ex = tab.e[ip][0], ey = tab.e[ip][1], ez = tab.e[ip][2];
-      const T w = tab.w[ip];
       T uw0 = 0, uw1 = 0, uw2 = 0;
       if (uwv) {
         uw0 = uwv[k];
         uw1 = uwv[nl + k];
         if (L::D == 3) uw2 = uwv[2 * nl + k];
       }
-      const T fpf = f[(size_t)ip * N + node];
-      T fpff = 0, fpi = 0;
-      Mom4<T> mf{0, 0, 0, 0}, mff{0, 0, 0, 0};
-      if (rule == 1) {
-        if (q <= (T)0.5)
-          fpff = f[(size_t)ip * N + ff];
-        else
-          fpi = f[(size_t)i * N + node];
-      } else if (rule == 2) {
-        fpff = f[(size_t)ip * N + ff];
-        mf = mom[node];
-        mff = mom[ff];
-      }
-      const T val = link_value<P>(rule, q, w, ex, ey, ez, fpf, fpff, fpi, mf, mff, uw0, uw1, uw2, p.rho0,
-                                  p.vibb_local_rho);
-      f[(size_t)i * N + s] = val;
+      T fpf;
+      const T val = eval_link<L, P>(tab, f, mom, N, ip, rule, q, rec.kf, rec.kff, uw0, uw1, uw2, p, fpf);
+      f[(size_t)tab.opp[ip] * N + rec.ks] = val;
       if (body >= 0) {
         // momentum exchange (f+_i'(x_f,t) + f_i(x_f,t+1)) e_i'.  In shifted
         // storage this sums (h+_i' + h_i) e_i'; the rest part 2 w_i' rho0 e_i'
         // of every link is a geometric constant that the host adds in FP64.
         const T t = fpf + val;
+        const T ex = tab.e[ip][0], ey = tab.e[ip][1], ez = tab.e[ip][2];
         if (body == b0) {
           F0 += t * ex;
           F1 += t * ey;
@@ -729,6 +764,176 @@ __global__ void __launch_bounds__(256) k_links(typename P::T* __restrict__ f, co
   }
 }
 
+// ------------------------------------------------------------ fused step --
+
+// Links of the fused step kernel, in (node, direction) order: the links of
+// the stored nodes 32 g .. 32 g + 31 are first[g] .. first[g+1] - 1, and
+// mask[k] has bit d set when stored node k has a link in direction d.  One
+// 16-B record per link: the storage indices of x_f and x_ff (x_f when there
+// is no second fluid node), meta = dir | rule << 5 | (body + 1) << 8, and
+// q as FP32 bits (FP32 storage; FP64 keeps q in qd).
+struct __align__(16) FusedRec {
+  uint32_t kf, kff, meta, q32;
+};
+
+template <class T>
+struct FusedLinks {
+  const int32_t* first;    // [ngroups + 1]
+  const uint32_t* mask;    // [S]
+  const FusedRec* rec;     // [nl]
+  const double* qd;        // [nl] (FP64 storage) or null
+  const T* uw;             // [D][nl] wall velocities or null
+  int64_t nl;
+  int64_t ngroups;         // ceil(S / 32)
+};
+
+// Asynchronous global -> shared copies of one real (cp.async, cached in L1;
+// no register holds the value while it is in flight).
+template <class T>
+__device__ __forceinline__ void cp_async_real(T* smem, const T* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Resident blocks per SM of the fused kernel, per 256 threads: FP32 D2Q9 4
+// (64 registers: the link phase spills at the bulk kernel's 40), FP32
+// D3Q19 5 (48), FP64 2.
+template <class L, class P, int BT>
+constexpr int fused_blocks_per_sm() {
+  constexpr int base = !P::shifted ? 2 : (L::Q == 9 ? 4 : 5);
+  return base * 256 / BT < 1 ? 1 : base * 256 / BT;
+}
+
+// One time step with the link rules fused into the pull pass, one thread
+// per stored node (as k_bulk):
+//  1. each fluid node issues the pulls of its non-link directions as
+//     asynchronous copies into its column of the block's shared-memory
+//     stage (ghost and open slots put the rest state there);
+//  2. meanwhile the block evaluates the cut links of its nodes, spread over
+//     all its threads (the same rule code as k_links, on f+(t) and the
+//     moment cache at t, mom_in), and writes each link value into the
+//     stage at its node and direction i = opp(i');
+//  3. after one barrier every node collides from its staged column.
+// The link values never go through HBM and no ghost slot is read or written
+// by the link rules; ghost and open slots of fout get zeros as in k_bulk.
+// The moments at t+1 go to mom_out (a second cache buffer: other blocks'
+// link phases still read mom_in).  Momentum exchange: per thread in storage
+// precision, per warp by shuffles, per block in FP64 and one atomic per
+// block and component for the body of the block's first link; links of
+// other bodies add their terms with FP64 atomics directly.
+template <class L, class P, bool MULTI, int BT>
+__global__ void __launch_bounds__(BT, (fused_blocks_per_sm<L, P, BT>())) k_fused(
+    const typename P::T* __restrict__ fin, typename P::T* __restrict__ fout, Layout lay,
+    FusedLinks<typename P::T> fl, const Mom4<typename P::T>* __restrict__ mom_in,
+    Mom4<typename P::T>* __restrict__ mom_out, double* __restrict__ force, double* __restrict__ force_next,
+    Params p) {
+  using T = typename P::T;
+  constexpr int NW = BT / 32;
+  __shared__ T stage[NW][L::Q][32];
+  __shared__ DirTable<T, L::Q> tab;
+  __shared__ double red[3][NW];
+  fill_dir_table<L>(tab);
+  if (force_next && blockIdx.x == 0)
+    for (int t = threadIdx.x; t < 3 * p.nbody; t += BT) force_next[t] = 0.0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t base = blockIdx.x * BT;
+  const uint32_t k = base + threadIdx.x;
+  const size_t S = (size_t)lay.S;
+  const bool live = (uint64_t)k < S;
+  const uint32_t w = live ? __ldg(lay.word + k) : W_GHOST;
+  const uint32_t mask = live ? __ldg(fl.mask + k) : 0u;
+  // the block's range of the link list (the same two words in every thread)
+  const int64_t g0 = base >> 5, g1 = g0 + NW < fl.ngroups ? g0 + NW : fl.ngroups;
+  const int64_t l0 = __ldg(fl.first + g0), l1 = __ldg(fl.first + g1);
+  const bool fluid = live && !(w & (W_GHOST | W_OPEN));
+  T(&col)[L::Q][32] = stage[warp];
+  int dom = 0;
+  if (fluid) {
+    const RunRec run = lay.runs[w & W_RUN];
+    if (MULTI) dom = run.dom;
+    int d[L::Q];
+    pull_offsets<L>(k, run, lay, p, d);
+    const T* __restrict__ fk = fin + k;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i)
+      // direction i comes from the solid side when its opposite is a link
+      if (!((mask >> L::opp(i)) & 1u)) cp_async_real(&col[i][lane], fk + ((ptrdiff_t)i * (ptrdiff_t)S + d[i]));
+  } else if (live) {
+    // ghost and open slots: zeros through the same stores (inputs at rest)
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) col[i][lane] = P::shifted ? (T)0 : (T)L::w(i);
+  }
+  cp_async_commit();
+  __syncthreads();  // the direction table
+  const int total = (int)(l1 - l0);
+  const int wb = total > 0 ? (int)(__ldg(&fl.rec[l0].meta) >> 8) - 1 : -1;
+  T F0 = 0, F1 = 0, F2 = 0;
+  for (int j = threadIdx.x; j < total; j += BT) {
+    const int64_t li = l0 + j;
+    const FusedRec r = fl.rec[li];
+    const T q = P::shifted ? (T)__uint_as_float(r.q32) : (T)__ldg(fl.qd + li);
+    const int ip = (int)(r.meta & 31);
+    const int rule = (int)((r.meta >> 5) & 7);
+    const int body = (int)(r.meta >> 8) - 1;
+    T uw0 = 0, uw1 = 0, uw2 = 0;
+    if (fl.uw) {
+      uw0 = fl.uw[li];
+      uw1 = fl.uw[fl.nl + li];
+      if (L::D == 3) uw2 = fl.uw[2 * fl.nl + li];
+    }
+    T fpf;
+    const T val = eval_link<L, P>(tab, fin, mom_in, S, ip, rule, q, r.kf, r.kff, uw0, uw1, uw2, p, fpf);
+    const uint32_t o = r.kf - base;  // the node's place in the block
+    stage[o >> 5][tab.opp[ip]][o & 31] = val;
+    if (body >= 0) {
+      // momentum exchange as in k_links
+      const T t = fpf + val;
+      const T ex = tab.e[ip][0], ey = tab.e[ip][1], ez = tab.e[ip][2];
+      if (body == wb) {
+        F0 += t * ex;
+        F1 += t * ey;
+        F2 += t * ez;
+      } else {
+        atomicAdd(&force[3 * body + 0], (double)(t * ex));
+        atomicAdd(&force[3 * body + 1], (double)(t * ey));
+        atomicAdd(&force[3 * body + 2], (double)(t * ez));
+      }
+    }
+  }
+  if (wb >= 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      F0 += __shfl_down_sync(0xffffffffu, F0, o);
+      F1 += __shfl_down_sync(0xffffffffu, F1, o);
+      F2 += __shfl_down_sync(0xffffffffu, F2, o);
+    }
+    if (lane == 0) {
+      red[0][warp] = (double)F0;
+      red[1][warp] = (double)F1;
+      red[2][warp] = (double)F2;
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();  // staged pulls, link values and warp sums of the whole block
+  if (wb >= 0 && threadIdx.x < 3) {
+    double acc = 0.0;
+#pragma unroll
+    for (int wi = 0; wi < NW; ++wi) acc += red[threadIdx.x][wi];
+    atomicAdd(&force[3 * wb + threadIdx.x], acc);
+  }
+  if (live) {
+    T f[L::Q];
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) f[i] = col[i][lane];
+    const Relax rx = MULTI ? relax_domain(lay.dom, dom) : relax_params(p);
+    collide_store<L, P>(f, p, rx, fout, S, k, mom_out, (w & W_CACHE) != 0, fluid);
+  }
+}
 
 // ------------------------------------------------------------ open sides --
 
@@ -934,6 +1139,17 @@ __global__ void k_check(const typename P::T* __restrict__ f, Layout lay, int* __
 
 // ------------------------------------------------------------- launchers --
 
+// Link arrays of the fused step kernel without the storage type (the
+// launchers cast q and uw).
+struct FusedRaw {
+  const int32_t* first;
+  const uint32_t* mask;
+  const FusedRec* rec;
+  const double* qd;
+  const void* uw;
+  int64_t nl, ngroups;
+};
+
 struct KernelOps {
   int Q, D;
   size_t real_bytes;
@@ -945,6 +1161,10 @@ struct KernelOps {
                int shape, cudaStream_t s);
   void (*links)(void* f, const void* mom, const LinkRec* recs, const void* q, const void* uw, int64_t nl,
                 double* force, const Params& p, int64_t S, int threads, int seq, cudaStream_t s);
+  // fused step (threads per block 128, 256 or 512; 512 runs as 256 for
+  // FP64 D3Q19, whose link buffer would not fit the static shared memory)
+  void (*fused)(const void* fin, void* fout, const Layout& lay, const FusedRaw& fl, const void* mom_in,
+                void* mom_out, double* force, double* force_next, const Params& p, int threads, cudaStream_t s);
   void (*open)(void* f, const void* mom, const Layout& lay, const Params& p, cudaStream_t s);
   void (*init)(void* f, void* mom, const Layout& lay, const double* rho, const double* u, const Params& p,
                cudaStream_t s);
@@ -1013,6 +1233,33 @@ struct Launch {
       k_links<L, P, 1><<<blocks_for(nl, bt), bt, 0, s>>>((T*)f, (const Mom4<T>*)mom, recs, (const T*)q,
                                                          (const T*)uw, nl, force, p, S);
   }
+  template <bool M, int BT>
+  static void fused_shape(const void* fin, void* fout, const Layout& lay, const FusedRaw& r, const void* mom_in,
+                          void* mom_out, double* force, double* force_next, const Params& p, cudaStream_t s) {
+    const FusedLinks<T> fl{r.first, r.mask, r.rec, r.qd, (const T*)r.uw, r.nl, r.ngroups};
+    k_fused<L, P, M, BT><<<blocks_for(lay.S, BT), BT, 0, s>>>((const T*)fin, (T*)fout, lay, fl,
+                                                              (const Mom4<T>*)mom_in, (Mom4<T>*)mom_out, force,
+                                                              force_next, p);
+  }
+  template <bool M>
+  static void fused_m(const void* fin, void* fout, const Layout& lay, const FusedRaw& r, const void* mom_in,
+                      void* mom_out, double* force, double* force_next, const Params& p, int threads,
+                      cudaStream_t s) {
+    constexpr bool big_ok = P::shifted || L::Q == 9;
+    if (threads == 128) return fused_shape<M, 128>(fin, fout, lay, r, mom_in, mom_out, force, force_next, p, s);
+    if (big_ok && threads == 512)
+      return fused_shape<M, big_ok ? 512 : 256>(fin, fout, lay, r, mom_in, mom_out, force, force_next, p, s);
+    fused_shape<M, 256>(fin, fout, lay, r, mom_in, mom_out, force, force_next, p, s);
+  }
+  static void fused(const void* fin, void* fout, const Layout& lay, const FusedRaw& r, const void* mom_in,
+                    void* mom_out, double* force, double* force_next, const Params& p, int threads,
+                    cudaStream_t s) {
+    if (lay.S == 0) return;
+    if (lay.ndom > 1)
+      fused_m<true>(fin, fout, lay, r, mom_in, mom_out, force, force_next, p, threads, s);
+    else
+      fused_m<false>(fin, fout, lay, r, mom_in, mom_out, force, force_next, p, threads, s);
+  }
   static void open(void* f, const void* mom, const Layout& lay, const Params& p, cudaStream_t s) {
     k_open<L, P><<<blocks_for(p.ny, 128), 128, 0, s>>>((T*)f, (const Mom4<T>*)mom, lay, p);
   }
@@ -1047,8 +1294,8 @@ struct Launch {
     k_gather<L, P><<<blocks_for(n, 256), 256, 0, s>>>((const T*)f, lay, sk, n, out, p);
   }
   static KernelOps ops() {
-    return KernelOps{L::Q,    L::D,    sizeof(T), bulk_default_shape<L>(), bulk_shape_mask<L>(), bulk, links, open, init,
-                     moments, refresh, get_dir, set_dir, check,     gather};
+    return KernelOps{L::Q,   L::D,    sizeof(T), bulk_default_shape<L>(), bulk_shape_mask<L>(), bulk, links, fused,
+                     open,   init,    moments,   refresh, get_dir, set_dir, check, gather};
   }
 };
 

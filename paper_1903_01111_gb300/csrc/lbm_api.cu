@@ -2,8 +2,10 @@
 //
 // A lattice owns two population buffers (ping-pong) over the stored nodes of
 // the compacted layout (fluid, open-column and ghost nodes, see
-// kernels.cuh), the moment cache, the layout tables, the link records, the
-// domain table of a batch and two FP64 force slots.  lbm_step replays
+// kernels.cuh), two moment caches (the moments of buffer c live in cache c),
+// the layout tables, the link records (in the link kernel's order and in the
+// fused step kernel's (node, direction) order), the domain table of a batch
+// and two FP64 force slots.  lbm_step replays
 // captured CUDA graphs (graph_steps steps, then two) and launches single
 // steps directly for an odd remainder; with profiling on it launches kernel
 // by kernel between CUDA events.  lbm_autotune picks the launch shapes.
@@ -103,8 +105,8 @@ struct lbm_lattice_s {
   int Q = 0, D = 0;
   int64_t N = 0;
   size_t rb = 0;  // bytes per stored real
-  // state over stored nodes
-  DeviceBuf f[2], mom;
+  // state over stored nodes: f[c] and its moment cache mom[c]
+  DeviceBuf f[2], mom[2];
   // layout
   DeviceBuf word, node_of, runs, row_first, row_last, row_in1, row_out1;
   Layout lay{};
@@ -112,10 +114,12 @@ struct lbm_lattice_s {
   std::vector<lbm_domain> domains;
   DeviceBuf dom, row_dom;
   int nbody = 1;  // force accumulators per slot
-  lbm_tuning tune{-1, 256, 2, 1};
+  lbm_tuning tune{-1, 256, 2, 1, 1};
   raw_vec<int32_t> sidx;  // dense -> storage index (-1: not stored), host
-  // links
+  // links, in the link kernel's order (body, node, dir)
   DeviceBuf recs, q, uw;
+  // links of the fused step kernel, in (node, dir) order (FusedLinks)
+  DeviceBuf lfirst, lmask, lrec, lqd, luw;
   int64_t n_links = 0, n_fluid = 0, n_cached = 0, n_runs = 0;
   DeviceBuf force;  // [2][nbody][3]
   // shifted storage: sum over each body's links of 2 w_i' rho0 e_i' (FP64),
@@ -142,9 +146,10 @@ struct lbm_lattice_s {
 namespace {
 
 int64_t device_bytes(const lbm_handle h) {
-  const DeviceBuf* all[] = {&h->f[0],     &h->f[1],     &h->mom,      &h->word, &h->node_of, &h->runs,
-                            &h->row_first, &h->row_last, &h->row_in1, &h->row_out1, &h->recs, &h->q,
-                            &h->uw,       &h->force,    &h->dom,      &h->row_dom};
+  const DeviceBuf* all[] = {&h->f[0],     &h->f[1],     &h->mom[0],   &h->mom[1], &h->word,  &h->node_of,
+                            &h->runs,     &h->row_first, &h->row_last, &h->row_in1, &h->row_out1, &h->recs,
+                            &h->q,        &h->uw,       &h->lfirst, &h->lmask, &h->lrec,
+                            &h->lqd,      &h->luw,      &h->force,    &h->dom,    &h->row_dom};
   int64_t s = 0;
   for (auto* b : all) s += (int64_t)b->bytes;
   return s;
@@ -185,9 +190,10 @@ void drop_graphs(lbm_handle h) {
 }
 
 void release_geometry(lbm_handle h) {
-  DeviceBuf* all[] = {&h->f[0],      &h->f[1],     &h->mom,     &h->word,     &h->node_of, &h->runs, &h->row_first,
-                      &h->row_last, &h->row_in1, &h->row_out1, &h->recs, &h->q,       &h->uw,   &h->dom,
-                      &h->row_dom};
+  DeviceBuf* all[] = {&h->f[0],     &h->f[1],      &h->mom[0],   &h->mom[1], &h->word,  &h->node_of,
+                      &h->runs,     &h->row_first, &h->row_last, &h->row_in1, &h->row_out1, &h->recs,
+                      &h->q,        &h->uw,        &h->lfirst, &h->lmask, &h->lrec,
+                      &h->lqd,      &h->luw,       &h->dom,      &h->row_dom};
   for (auto* b : all) release(*b);
   h->lay = Layout{};
 }
@@ -196,19 +202,36 @@ int cx_of(const lbm_handle h, int i) { return h->Q == 9 ? D2Q9::cx(i) : D3Q19::c
 int cy_of(const lbm_handle h, int i) { return h->Q == 9 ? D2Q9::cy(i) : D3Q19::cy(i); }
 int cz_of(const lbm_handle h, int i) { return h->Q == 9 ? D2Q9::cz(i) : D3Q19::cz(i); }
 
-// Enqueue one time step from buffer fc (f+(t)) into fn, adding the force to
-// `slot` and clearing `next`.
-lbm_status enqueue_step_buf(lbm_handle h, void* fc, void* fn, double* slot, double* next, bool timed);
+// Enqueue one time step from buffer fc (f+(t), moments mc) into fn (moments
+// at t+1 into mn), adding the force to `slot` and clearing `next`.  fused:
+// the link rules run inside the pull pass (k_fused; mn must differ from mc),
+// else the link kernel writes the ghost slots of fc and the bulk kernel
+// pulls them (mn may equal mc: the link kernel reads mc before the bulk
+// kernel writes it).
+lbm_status enqueue_step_buf(lbm_handle h, void* fc, void* fn, void* mc, void* mn, double* slot, double* next,
+                            bool timed, bool fused);
+
+// Whether lbm_step runs the fused kernel: chosen by the tuning, and only
+// where there are links (without them the bulk kernel is the same pass).
+bool use_fused(const lbm_handle h) { return h->tune.fused && h->n_links > 0; }
+
+// Threads per block of the fused kernel: those of the bulk shape when it
+// has one node per thread, else 256.
+int fused_threads(const lbm_handle h) {
+  const BulkShape& b = kBulkShapes[h->tune.bulk_shape < 0 ? 0 : h->tune.bulk_shape];
+  return (b.npt == 1 && b.seq == 1) ? b.threads : 256;
+}
 
 // Enqueue one time step on the stream (parity = buffer holding f+(t)).
 lbm_status enqueue_step(lbm_handle h, int parity, int64_t step_index, bool timed) {
   double* force = (double*)h->force.p;
   const int64_t nb3 = 3 * (int64_t)h->nbody;
-  return enqueue_step_buf(h, h->f[parity].p, h->f[parity ^ 1].p, force + nb3 * (step_index & 1),
-                          force + nb3 * ((step_index + 1) & 1), timed);
+  return enqueue_step_buf(h, h->f[parity].p, h->f[parity ^ 1].p, h->mom[parity].p, h->mom[parity ^ 1].p,
+                          force + nb3 * (step_index & 1), force + nb3 * ((step_index + 1) & 1), timed, use_fused(h));
 }
 
-lbm_status enqueue_step_buf(lbm_handle h, void* fc, void* fn, double* slot, double* next, bool timed) {
+lbm_status enqueue_step_buf(lbm_handle h, void* fc, void* fn, void* mc, void* mn, double* slot, double* next,
+                            bool timed, bool fused) {
   auto timed_launch = [&](int kid, auto&& fn_launch) -> lbm_status {
     if (!timed) {
       fn_launch();
@@ -231,16 +254,26 @@ lbm_status enqueue_step_buf(lbm_handle h, void* fc, void* fn, double* slot, doub
     return LBM_OK;
   };
   lbm_status st;
-  st = timed_launch(0, [&] {
-    h->ops.links(fc, h->mom.p, (const LinkRec*)h->recs.p, h->q.p, h->uw.p, h->n_links, slot, h->p, h->lay.S,
-                 h->tune.link_threads, h->tune.link_seq, h->stream);
-  });
-  if (st != LBM_OK) return st;
-  if (h->p.inlet || h->p.outlet) {
-    st = timed_launch(1, [&] { h->ops.open(fc, h->mom.p, h->lay, h->p, h->stream); });
+  if (!fused) {
+    st = timed_launch(0, [&] {
+      h->ops.links(fc, mc, (const LinkRec*)h->recs.p, h->q.p, h->uw.p, h->n_links, slot, h->p, h->lay.S,
+                   h->tune.link_threads, h->tune.link_seq, h->stream);
+    });
     if (st != LBM_OK) return st;
   }
-  st = timed_launch(2, [&] { h->ops.bulk(fc, fn, h->lay, h->mom.p, next, h->p, h->tune.bulk_shape, h->stream); });
+  if (h->p.inlet || h->p.outlet) {
+    st = timed_launch(1, [&] { h->ops.open(fc, mc, h->lay, h->p, h->stream); });
+    if (st != LBM_OK) return st;
+  }
+  if (fused) {
+    const FusedRaw fl{(const int32_t*)h->lfirst.p, (const uint32_t*)h->lmask.p, (const FusedRec*)h->lrec.p,
+                      (const double*)h->lqd.p, h->luw.p, h->n_links, (h->lay.S + 31) / 32};
+    st = timed_launch(2, [&] {
+      h->ops.fused(fc, fn, h->lay, fl, mc, mn, slot, next, h->p, fused_threads(h), h->stream);
+    });
+  } else {
+    st = timed_launch(2, [&] { h->ops.bulk(fc, fn, h->lay, mn, next, h->p, h->tune.bulk_shape, h->stream); });
+  }
   if (st != LBM_OK) return st;
   CUDA_TRY(cudaGetLastError());
   return LBM_OK;
@@ -626,13 +659,18 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
   if (first_dup < n_links)
     return fail(LBM_ERR_INVALID_ARG, "duplicate link at node %lld direction %d",
                 (long long)(nodedir(order[first_dup]) / 32), (int)(nodedir(order[first_dup]) % 32));
+  // (node, dir) order of the fused kernel's link arrays: `order` before the
+  // body sort below (ond points into whichever vector holds it)
+  raw_vec<int64_t> byb;
+  const int64_t* ond = order.data();
   if (min_body < max_body) {  // (one body for every link: the order stands)
     std::vector<int64_t> count(nbody + 2, 0);
     for (int64_t k = 0; k < n_links; ++k) count[links[k].body + 2]++;
     for (int b = 1; b < nbody + 2; ++b) count[b] += count[b - 1];
-    raw_vec<int64_t> byb(n_links);
+    byb.resize(n_links);
     for (int64_t k = 0; k < n_links; ++k) byb[count[links[order[k]].body + 1]++] = order[k];
     order.swap(byb);
+    ond = byb.data();
   }
   // completeness: count (fluid node, dir) pairs with a solid neighbour, row
   // by row (each direction's neighbour row is found once per row).  A
@@ -865,6 +903,46 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
       for (int a = 0; a < D; ++a) uws[a * n_links + j] = L.uw[a];
   }
 
+  // fused-kernel link arrays in (node, dir) order: storage indices of x_f
+  // are non-decreasing along it, so the first link of each 32-node group is
+  // a lower bound
+  const int64_t ngroups = (S + 31) / 32;
+  raw_vec<int32_t> ffirst((size_t)ngroups + 1);
+  raw_vec<uint32_t> fmask((size_t)S);
+  par_fill(fmask, 0u);
+  raw_vec<FusedRec> frec(n_links);  // written in full below
+  raw_vec<double> fq(h->rb == 8 ? n_links : 0);
+  raw_vec<double> fuw(moving ? (size_t)D * n_links : 0);
+  auto kf_of = [&](int64_t j) -> int64_t { return sidx[links[ond[j]].node]; };
+#pragma omp parallel for schedule(static)
+  for (int64_t g = 0; g <= ngroups; ++g) {
+    int64_t lo = 0, hi = n_links;  // first j with kf_of(j) >= 32 g
+    while (lo < hi) {
+      const int64_t mid = lo + (hi - lo) / 2;
+      if (kf_of(mid) < 32 * g)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    ffirst[g] = (int32_t)lo;
+  }
+#pragma omp parallel for schedule(static)
+  for (int64_t j = 0; j < n_links; ++j) {
+    const int64_t k = ond[j];
+    const lbm_link& L = links[k];
+    const uint32_t kf = (uint32_t)sidx[L.node];
+#pragma omp atomic update
+    fmask[kf] |= 1u << L.dir;
+    const float q32 = (float)L.q;
+    uint32_t qbits;
+    memcpy(&qbits, &q32, 4);
+    frec[j] = FusedRec{kf, (uint32_t)sidx[lk_ff[k]],
+                       (uint32_t)L.dir | ((uint32_t)lk_rule[k] << 5) | ((uint32_t)(L.body + 1) << 8), qbits};
+    if (h->rb == 8) fq[j] = L.q;
+    if (moving)
+      for (int a = 0; a < D; ++a) fuw[a * n_links + j] = L.uw[a];
+  }
+
   // ---- device
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   drop_graphs(h);
@@ -873,7 +951,7 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
   lbm_status st = LBM_OK;
   const size_t rb = h->rb;
   for (int k = 0; k < 2 && st == LBM_OK; ++k) st = acquire(h->f[k], (size_t)Q * S * rb);
-  if (st == LBM_OK) st = acquire(h->mom, (size_t)S * 4 * rb);
+  for (int k = 0; k < 2 && st == LBM_OK; ++k) st = acquire(h->mom[k], (size_t)S * 4 * rb);
   if (st == LBM_OK) st = upload(h->word, word.data(), sizeof(uint32_t) * S);
   if (st == LBM_OK) st = upload(h->node_of, node_of.data(), sizeof(int32_t) * S);
   if (st == LBM_OK) st = upload(h->runs, runs.data(), sizeof(RunRec) * runs.size());
@@ -882,6 +960,10 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
   if (st == LBM_OK) st = upload(h->row_in1, row_in1.data(), sizeof(int32_t) * rows);
   if (st == LBM_OK) st = upload(h->row_out1, row_out1.data(), sizeof(int32_t) * rows);
   if (st == LBM_OK) st = upload(h->recs, recs.data(), sizeof(LinkRec) * n_links);
+  if (st == LBM_OK && n_links > 0) st = upload(h->lfirst, ffirst.data(), sizeof(int32_t) * (ngroups + 1));
+  if (st == LBM_OK && n_links > 0) st = upload(h->lmask, fmask.data(), sizeof(uint32_t) * S);
+  if (st == LBM_OK) st = upload(h->lrec, frec.data(), sizeof(FusedRec) * n_links);
+  if (st == LBM_OK) st = upload(h->lqd, fq.data(), sizeof(double) * fq.size());
   if (st == LBM_OK && ndom > 0) {
     std::vector<DomPar> dp(ndom);
     for (int k = 0; k < ndom; ++k) {
@@ -906,23 +988,23 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
     }
   }
   if (st == LBM_OK) {
-    if (rb == 8) {
-      st = upload(h->q, qs.data(), 8 * n_links);
-      if (st == LBM_OK && moving) st = upload(h->uw, uws.data(), 8 * uws.size());
-    } else {
-      raw_vec<float> tq(qs.size()), tw(uws.size());
+    // q and u_w in storage precision, for both link orders
+    auto put = [&](DeviceBuf& b, const raw_vec<double>& v) -> lbm_status {
+      if (rb == 8) return upload(b, v.data(), 8 * v.size());
+      raw_vec<float> t(v.size());
 #pragma omp parallel for schedule(static)
-      for (int64_t j = 0; j < (int64_t)qs.size(); ++j) tq[j] = (float)qs[j];
-#pragma omp parallel for schedule(static)
-      for (int64_t j = 0; j < (int64_t)uws.size(); ++j) tw[j] = (float)uws[j];
-      st = upload(h->q, tq.data(), 4 * n_links);
-      if (st == LBM_OK && moving) st = upload(h->uw, tw.data(), 4 * tw.size());
+      for (int64_t j = 0; j < (int64_t)v.size(); ++j) t[j] = (float)v[j];
+      return upload(b, t.data(), 4 * t.size());
+    };
+    st = put(h->q, qs);
+    if (st == LBM_OK && moving) st = put(h->uw, uws);
+    if (st == LBM_OK && moving) st = put(h->luw, fuw);
+  }
+  for (int k = 0; k < 2 && st == LBM_OK; ++k)
+    if (h->mom[k].bytes) {
+      cudaError_t e = cudaMemsetAsync(h->mom[k].p, 0, h->mom[k].bytes, h->stream);
+      if (e != cudaSuccess) st = fail(LBM_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
     }
-  }
-  if (st == LBM_OK && h->mom.bytes) {
-    cudaError_t e = cudaMemsetAsync(h->mom.p, 0, h->mom.bytes, h->stream);
-    if (e != cudaSuccess) st = fail(LBM_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
-  }
   if (st != LBM_OK) {
     release_geometry(h);
     return st;
@@ -980,9 +1062,9 @@ lbm_status lbm_init_equilibrium(lbm_handle h, const double* rho, const double* u
   cudaError_t e = cudaSuccess;
   if (rho) e = cudaMemcpyAsync(drho, rho, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream);
   if (u && e == cudaSuccess) e = cudaMemcpyAsync(du, u, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess && h->mom.bytes) e = cudaMemsetAsync(h->mom.p, 0, h->mom.bytes, h->stream);
+  if (e == cudaSuccess && h->mom[0].bytes) e = cudaMemsetAsync(h->mom[0].p, 0, h->mom[0].bytes, h->stream);
   if (e == cudaSuccess) {
-    h->ops.init(h->f[0].p, h->mom.p, h->lay, drho, du, h->p, h->stream);
+    h->ops.init(h->f[0].p, h->mom[0].p, h->lay, drho, du, h->p, h->stream);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(h->force.p, 0, h->force.bytes, h->stream);
@@ -1154,7 +1236,7 @@ lbm_status lbm_set_distributions(lbm_handle h, const double* f) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   }
   if (e == cudaSuccess) {
-    h->ops.refresh(h->f[h->cur].p, h->lay, h->mom.p, h->p, h->stream);
+    h->ops.refresh(h->f[h->cur].p, h->lay, h->mom[h->cur].p, h->p, h->stream);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -1305,13 +1387,18 @@ lbm_status lbm_adjoint_step(lbm_handle h, int32_t body, const double dJ_dF[3], i
     if (e != cudaSuccess) st = fail(LBM_ERR_CUDA, "adjoint: %s", cudaGetErrorString(e));
   }
   const bool open = h->p.inlet || h->p.outlet;
+  // moment cache of the recomputed and transposed states: the cache of the
+  // buffer that does not hold the current state (the current state and its
+  // moments stay as they are)
+  void* am = h->mom[h->cur ^ 1].p;
   // the states f+(s0) .. f+(s0 + m - 1) of a segment from its first state
   // (copied into seg[0]); the link and open kernels leave the link values
   // of step s0 + j in the ghost slots of seg[j] for j < m - 1
   auto enqueue_recompute = [&](int64_t m) -> lbm_status {
-    h->ops.refresh(segp, h->lay, h->mom.p, h->p, h->stream);
+    h->ops.refresh(segp, h->lay, am, h->p, h->stream);
     for (int64_t j = 0; j + 1 < m; ++j) {
-      const lbm_status r = enqueue_step_buf(h, segp + sb * j, segp + sb * (j + 1), fslot, fslot + 3 * (size_t)nb, false);
+      const lbm_status r = enqueue_step_buf(h, segp + sb * j, segp + sb * (j + 1), am, am, fslot,
+                                            fslot + 3 * (size_t)nb, false, false);
       if (r != LBM_OK) return r;
     }
     CUDA_TRY(cudaGetLastError());
@@ -1325,15 +1412,15 @@ lbm_status lbm_adjoint_step(lbm_handle h, int32_t body, const double dJ_dF[3], i
       void* state = segp + sb * j;
       if (j == m - 1) {
         // the last state of the segment has no link values yet
-        h->ops.refresh(state, h->lay, h->mom.p, h->p, h->stream);
-        h->ops.links(state, h->mom.p, (const LinkRec*)h->recs.p, h->q.p, h->uw.p, nl, fslot, h->p, S,
+        h->ops.refresh(state, h->lay, am, h->p, h->stream);
+        h->ops.links(state, am, (const LinkRec*)h->recs.p, h->q.p, h->uw.p, nl, fslot, h->p, S,
                      h->tune.link_threads, h->tune.link_seq, h->stream);
-        if (open) h->ops.open(state, h->mom.p, h->lay, h->p, h->stream);
+        if (open) h->ops.open(state, am, h->lay, h->p, h->stream);
       }
-      h->adj.bulk(state, lam[l].p, lam[l ^ 1].p, h->lay, h->p, dtau, h->mom.p, h->stream);
-      h->adj.links(state, h->mom.p, lam[l ^ 1].p, lam[l].p, (const LinkRec*)h->recs.p, h->q.p, h->uw.p, nl, h->p,
+      h->adj.bulk(state, lam[l].p, lam[l ^ 1].p, h->lay, h->p, dtau, am, h->stream);
+      h->adj.links(state, am, lam[l ^ 1].p, lam[l].p, (const LinkRec*)h->recs.p, h->q.p, h->uw.p, nl, h->p,
                    S, (double*)dq.p, (last && j == m - 1) ? 1 : 0, wdev, h->stream);
-      if (open) h->adj.open(lam[l ^ 1].p, lam[l].p, h->mom.p, h->lay, h->p, h->stream);
+      if (open) h->adj.open(lam[l ^ 1].p, lam[l].p, am, h->lay, h->p, h->stream);
       l ^= 1;
     }
     CUDA_TRY(cudaGetLastError());
@@ -1396,7 +1483,7 @@ lbm_status lbm_adjoint_step(lbm_handle h, int32_t body, const double dJ_dF[3], i
     e = cudaMemcpyAsync(dqh.data(), dq.p, sizeof(double) * nl, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dt.data(), dtau, sizeof(double) * ndom, cudaMemcpyDeviceToHost, h->stream);
     // leave the moment cache consistent with the final state
-    h->ops.refresh(h->f[h->cur].p, h->lay, h->mom.p, h->p, h->stream);
+    h->ops.refresh(h->f[h->cur].p, h->lay, h->mom[h->cur].p, h->p, h->stream);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) st = fail(LBM_ERR_CUDA, "adjoint: %s", cudaGetErrorString(e));
@@ -1454,8 +1541,9 @@ lbm_status lbm_set_tuning(lbm_handle h, const lbm_tuning* t) {
     return fail(LBM_ERR_INVALID_ARG, "graph_steps must be even and in 2..64");
   if (v.link_seq == 0) v.link_seq = 1;
   if (v.link_seq != 1 && v.link_seq != 4) return fail(LBM_ERR_INVALID_ARG, "link_seq must be 1 or 4");
+  if (v.fused != 0 && v.fused != 1) return fail(LBM_ERR_INVALID_ARG, "fused must be 0 or 1");
   if (v.bulk_shape != h->tune.bulk_shape || v.link_threads != h->tune.link_threads ||
-      v.graph_steps != h->tune.graph_steps || v.link_seq != h->tune.link_seq) {
+      v.graph_steps != h->tune.graph_steps || v.link_seq != h->tune.link_seq || v.fused != h->tune.fused) {
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     drop_graphs(h);
   }
@@ -1479,7 +1567,7 @@ lbm_status lbm_autotune(lbm_handle h, int32_t steps_per_trial, lbm_tuning* best,
   const size_t sb = (size_t)h->Q * h->lay.S * h->rb;
   DeviceBuf save_f, save_m, save_force;
   lbm_status st = acquire(save_f, sb);
-  if (st == LBM_OK) st = acquire(save_m, h->mom.bytes);
+  if (st == LBM_OK) st = acquire(save_m, h->mom[0].bytes);
   if (st == LBM_OK) st = acquire(save_force, h->force.bytes);
   auto cleanup = [&]() {
     release(save_f);
@@ -1498,7 +1586,7 @@ lbm_status lbm_autotune(lbm_handle h, int32_t steps_per_trial, lbm_tuning* best,
     return n ? cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToDevice, h->stream) : cudaSuccess;
   };
   cudaError_t e = copy(save_f.p, h->f[cur0].p, sb);
-  if (e == cudaSuccess) e = copy(save_m.p, h->mom.p, h->mom.bytes);
+  if (e == cudaSuccess) e = copy(save_m.p, h->mom[cur0].p, h->mom[cur0].bytes);
   if (e == cudaSuccess) e = copy(save_force.p, h->force.p, h->force.bytes);
   if (e != cudaSuccess) {
     cleanup();
@@ -1508,7 +1596,7 @@ lbm_status lbm_autotune(lbm_handle h, int32_t steps_per_trial, lbm_tuning* best,
   // the warm-up builds every graph the timed replays use
   auto restore = [&](int64_t step) -> cudaError_t {
     cudaError_t r = copy(h->f[cur0].p, save_f.p, sb);
-    if (r == cudaSuccess) r = copy(h->mom.p, save_m.p, h->mom.bytes);
+    if (r == cudaSuccess) r = copy(h->mom[cur0].p, save_m.p, h->mom[cur0].bytes);
     if (r == cudaSuccess) r = copy(h->force.p, save_force.p, h->force.bytes);
     h->cur = cur0;
     h->step = step;
@@ -1538,7 +1626,9 @@ lbm_status lbm_autotune(lbm_handle h, int32_t steps_per_trial, lbm_tuning* best,
     *ms = bestms;
     return LBM_OK;
   };
-  lbm_tuning cand{h->ops.default_shape, 256, 8, 1}, chosen = cand;
+  // split pass (link kernel, then bulk kernel) first, then the fused step
+  // with the block sizes of the one-node bulk shapes
+  lbm_tuning cand{h->ops.default_shape, 256, 8, 1, 0}, chosen = cand;
   double chosen_ms = 1e300;
   auto consider = [&](const lbm_tuning& t) -> lbm_status {
     double ms = 0.0;
@@ -1565,6 +1655,14 @@ lbm_status lbm_autotune(lbm_handle h, int32_t steps_per_trial, lbm_tuning* best,
     cand.link_seq = 4;
     st = consider(cand);
   }
+  if (h->n_links > 0)
+    for (int sh = 0; sh < kNumBulkShapes && st == LBM_OK; ++sh) {
+      if (!((h->ops.shape_mask >> sh) & 1u) || kBulkShapes[sh].npt != 1 || kBulkShapes[sh].seq != 1) continue;
+      cand = chosen;
+      cand.fused = 1;
+      cand.bulk_shape = sh;
+      st = consider(cand);
+    }
   const int graph_opts[] = {2, 32};
   for (int k = 0; k < 2 && st == LBM_OK; ++k) {
     cand = chosen;

@@ -108,13 +108,14 @@ class lbm_tuning(ctypes.Structure):
         ("link_threads", ctypes.c_int32),
         ("graph_steps", ctypes.c_int32),
         ("link_seq", ctypes.c_int32),
+        ("fused", ctypes.c_int32),
     ]
 
     def as_dict(self):
         t, npt, seq = BULK_SHAPES[self.bulk_shape]
         return {"bulk_shape": self.bulk_shape, "bulk_threads": t, "bulk_nodes_per_thread": npt,
                 "bulk_sequential_nodes": seq, "link_threads": self.link_threads, "link_seq": self.link_seq,
-                "graph_steps": self.graph_steps}
+                "graph_steps": self.graph_steps, "fused": self.fused}
 
 
 # (threads per block, nodes per thread, nodes per thread in sequence) of
@@ -312,8 +313,8 @@ def lbm_forces(h, n: int) -> np.ndarray:
     return out[:n]
 
 
-def lbm_set_tuning(h, bulk_shape=-1, link_threads=256, graph_steps=2, link_seq=1) -> None:
-    t = lbm_tuning(int(bulk_shape), int(link_threads), int(graph_steps), int(link_seq))
+def lbm_set_tuning(h, bulk_shape=-1, link_threads=256, graph_steps=2, link_seq=1, fused=1) -> None:
+    t = lbm_tuning(int(bulk_shape), int(link_threads), int(graph_steps), int(link_seq), int(fused))
     _check(_lib.lbm_set_tuning(h, ctypes.byref(t)))
 
 

@@ -143,27 +143,33 @@ def _shapes(L, stencil):
 @pytest.mark.parametrize("stencil", [0, 1])
 def test_launch_shapes(L, prec, stencil):
     """Block sizes, link block sizes and graph lengths change no bits; the
-    kernels with one or two nodes per thread, and the sequential walk, are
-    separate compilations of the same arithmetic and agree to rounding (the
-    parity bound of 37 steps)."""
+    kernels with one or two nodes per thread, the sequential walk, the link
+    kernel with one or four links per thread and the fused step are separate
+    compilations of the same arithmetic and agree to rounding (the parity
+    bound of 37 steps)."""
     precision = L.LBM_FP64 if prec == "fp64" else L.LBM_FP32_SHIFTED
     if stencil == 0:
         geo = G.build(0, (83, 41, 1), (1, 1, 1), [G.ball((30.37, 20.61, 0), 7.3, force_id=0)])
     else:
         geo = G.sphere_pack(24, porosity=0.5, rmin=2.5, rmax=4.5, seed=3)
     ref = {}
-    for shape in _shapes(L, stencil):
-        npt = L.BULK_SHAPES[shape][1:]
-        for lt, gs, ls in ((256, 2, 1), (64, 8, 4), (128, 32, 4)):
-            with L.Lattice(geo, precision=precision, bc=2, tau=0.7, g=(1e-5, 0, 0)) as lat:
-                lat.set_tuning(bulk_shape=shape, link_threads=lt, graph_steps=gs, link_seq=ls)
-                lat.init_equilibrium()
-                lat.step(37)
-                f = lat.distributions()
-            ref.setdefault(npt, f)
-            assert np.array_equal(f, ref[npt]), (shape, lt, gs, ls)
+    for fused in (0, 1):
+        for shape in _shapes(L, stencil):
+            npt = L.BULK_SHAPES[shape][1:]
+            if fused and npt != (1, 1):
+                continue  # the fused kernel takes one node per thread
+            for lt, gs, ls in ((256, 2, 1), (64, 8, 4), (128, 32, 4)):
+                # the link kernel with 1 and 4 links per thread: two compilations
+                key = (fused,) + npt + ((0 if fused else ls),)
+                with L.Lattice(geo, precision=precision, bc=2, tau=0.7, g=(1e-5, 0, 0)) as lat:
+                    lat.set_tuning(bulk_shape=shape, link_threads=lt, graph_steps=gs, link_seq=ls, fused=fused)
+                    lat.init_equilibrium()
+                    lat.step(37)
+                    f = lat.distributions()
+                ref.setdefault(key, f)
+                assert np.array_equal(f, ref[key]), (fused, shape, lt, gs, ls)
     _, w = O.velocity_set(stencil)
-    base = ref[(1, 1)]
+    base = ref[(0, 1, 1, 1)]
     h = np.abs(base - (w[:, None] if precision == L.LBM_FP32_SHIFTED else 0.0)).max()
     tol = 1e-12 if precision == L.LBM_FP64 else 4 * 37 * EPS32 * h
     for key, f in ref.items():
@@ -179,8 +185,8 @@ def test_autotune_restores_state_and_picks_a_valid_shape(L):
     f0 = lat.distributions()
     t, ms = lat.autotune(10)
     assert ms > 0 and 0 <= t.bulk_shape < 8 and t.link_threads in (64, 128, 256) and t.graph_steps % 2 == 0
-    assert t.link_seq in (1, 4)
-    assert lat.tuning().bulk_shape == t.bulk_shape
+    assert t.link_seq in (1, 4) and t.fused in (0, 1)
+    assert lat.tuning().bulk_shape == t.bulk_shape and lat.tuning().fused == t.fused
     assert lat.info().step == 9
     assert np.array_equal(lat.distributions(), f0)
     assert np.array_equal(lat.forces(), F0)
@@ -188,7 +194,7 @@ def test_autotune_restores_state_and_picks_a_valid_shape(L):
     f1 = lat.distributions()
     lat.close()
     lat2 = _batch_lattice(L, b, L.LBM_FP32_SHIFTED)
-    lat2.set_tuning(bulk_shape=t.bulk_shape, link_threads=256, graph_steps=2, link_seq=1)
+    lat2.set_tuning(bulk_shape=t.bulk_shape, link_threads=256, graph_steps=2, link_seq=1, fused=t.fused)
     lat2.step(29)
     assert np.array_equal(lat2.distributions(), f1)
     lat2.close()

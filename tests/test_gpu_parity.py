@@ -38,18 +38,30 @@ def _cfg(geo, **kw):
     return base
 
 
-def _run_both(L, geo, steps, precision, nbody=1, init_u=None, **kw):
-    cfg = _cfg(geo, **kw)
-    ocfg = O.make_config(**cfg)
+def _run_oracle(geo, steps, nbody=1, init_u=None, **kw):
+    ocfg = O.make_config(**_cfg(geo, **kw))
     st = O.init(ocfg, geo.solid, u=init_u)
     F_ref = O.run(ocfg, geo.solid, geo.links, st, steps, nbody=nbody)
+    return st, F_ref
+
+
+def _run_gpu(L, geo, steps, precision, nbody=1, init_u=None, fused=1, **kw):
+    """The lattice through the C ABI; fused = 1: link rules inside the pull
+    pass (k_fused), 0: link kernel + bulk kernel."""
     lat = L.Lattice(geo, precision=precision, **{k: v for k, v in kw.items()})
+    lat.set_tuning(fused=fused)
     lat.init_equilibrium(u=init_u)
     lat.step(steps)
     f = lat.distributions()
     F = np.array([lat.force(b) for b in range(nbody)]) if steps > 0 else None
     rho, u = lat.moments()
     lat.close()
+    return f, F, rho, u
+
+
+def _run_both(L, geo, steps, precision, nbody=1, init_u=None, fused=1, **kw):
+    st, F_ref = _run_oracle(geo, steps, nbody=nbody, init_u=init_u, **kw)
+    f, F, rho, u = _run_gpu(L, geo, steps, precision, nbody=nbody, init_u=init_u, fused=fused, **kw)
     return f, F, rho, u, st, F_ref
 
 
@@ -72,22 +84,28 @@ def _tol(L, precision, steps, st, geo):
 
 
 def _compare(L, geo, steps, precision, nbody=1, init_u=None, **kw):
-    f, F, rho, u, st, F_ref = _run_both(L, geo, steps, precision, nbody=nbody, init_u=init_u, **kw)
+    """Both step forms (link rules fused into the pull pass, and the separate
+    link kernel) against the oracle, element by element."""
+    st, F_ref = _run_oracle(geo, steps, nbody=nbody, init_u=init_u, **kw)
     fl = _fluid(geo)
     tol = _tol(L, precision, steps, st, geo)
-    err = np.abs(f[:, fl] - st.fp[:, fl]).max()
-    assert err <= tol, f"max |f - oracle| = {err:.3e} > {tol:.3e}"
-    assert np.all(f[:, ~fl] == 0.0)
-    # moments of the state: rho, u (D x N) against the oracle's
-    D = 2 + geo.stencil
-    urel = 1e-12 if precision == L.LBM_FP64 else 50 * tol
-    assert np.abs(rho[fl] - st.rho[fl]).max() <= urel
-    assert np.abs(u[:, fl] - st.u[fl, :D].T).max() <= urel
-    if F is not None and nbody:
-        scale = max(np.abs(F_ref).max(), 1e-12)
-        ftol = 1e-10 * scale + 1e-15 if precision == L.LBM_FP64 else 1e-4 * scale + len(geo.links) * tol
-        assert np.abs(F - F_ref).max() <= ftol, (F, F_ref)
-    return err, tol
+    errs = []
+    for fused in ((1, 0) if len(geo.links) else (1,)):
+        f, F, rho, u = _run_gpu(L, geo, steps, precision, nbody=nbody, init_u=init_u, fused=fused, **kw)
+        err = np.abs(f[:, fl] - st.fp[:, fl]).max()
+        assert err <= tol, f"fused={fused}: max |f - oracle| = {err:.3e} > {tol:.3e}"
+        assert np.all(f[:, ~fl] == 0.0)
+        # moments of the state: rho, u (D x N) against the oracle's
+        D = 2 + geo.stencil
+        urel = 1e-12 if precision == L.LBM_FP64 else 50 * tol
+        assert np.abs(rho[fl] - st.rho[fl]).max() <= urel
+        assert np.abs(u[:, fl] - st.u[fl, :D].T).max() <= urel
+        if F is not None and nbody:
+            scale = max(np.abs(F_ref).max(), 1e-12)
+            ftol = 1e-10 * scale + 1e-15 if precision == L.LBM_FP64 else 1e-4 * scale + len(geo.links) * tol
+            assert np.abs(F - F_ref).max() <= ftol, (fused, F, F_ref)
+        errs.append(err)
+    return max(errs), tol
 
 
 PRECISIONS = ["fp64", "fp32s"]
@@ -170,13 +188,15 @@ def test_no_links_periodic_box_spanning_tiles(L, prec):
     _compare(L, geo, 50, _p(L, prec), nbody=0, init_u=u0, tau=0.55, g=(1e-5, 0, 0), bc=0)
 
 
-def test_step_chunks_and_profiling_are_bitwise_equal(L):
+@pytest.mark.parametrize("fused", [1, 0])
+def test_step_chunks_and_profiling_are_bitwise_equal(L, fused):
     """lbm_step(n) (graph replay), n x lbm_step(1) and profiled launches
-    compute the same bits."""
+    compute the same bits, in both step forms."""
     geo = G.build(0, (45, 33, 1), (1, 1, 1), [G.ball((20.37, 15.61, 0), 6.3, omega=(0, 0, 0.004))])
     outs = []
     for mode in ("graph", "single", "profiled"):
         lat = L.Lattice(geo, tau=0.7, g=(2e-5, 1e-5, 0), bc=2)
+        lat.set_tuning(fused=fused, graph_steps=8)
         lat.init_equilibrium()
         if mode == "graph":
             lat.step(37)
@@ -187,13 +207,38 @@ def test_step_chunks_and_profiling_are_bitwise_equal(L):
             L.lbm_set_profiling(lat.h, True)
             lat.step(37)
             n, ms = L.lbm_kernel_times(lat.h)
-            assert n[0] == 37 and n[2] == 37 and n[1] == 0 and ms[2] > 0
+            assert n[0] == (0 if fused else 37) and n[2] == 37 and n[1] == 0 and ms[2] > 0
         outs.append((lat.distributions(), lat.force(0)))
         lat.close()
     for f, F in outs[1:]:
         assert np.array_equal(f, outs[0][0])
         # block partial sums meet in FP64 atomics, whose order may vary
         np.testing.assert_allclose(F, outs[0][1], rtol=1e-13, atol=1e-18)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_fused_and_split_steps_agree_on_a_moving_pack(L, prec):
+    """The fused step and the link-kernel step on a D3Q19 pack with moving
+    spheres, two bodies, every rule mixed per link and open rows absent:
+    the populations agree to rounding (FP64 1e-13, FP32 the parity bound)
+    and the per-body forces to their summation order."""
+    geo = G.sphere_pack(28, porosity=0.5, rmin=2.5, rmax=5.0, seed=11)
+    links = geo.links.copy()
+    rng = np.random.default_rng(4)
+    links["bc"] = rng.integers(0, 3, len(links))
+    links["body"] = rng.integers(0, 2, len(links))
+    links["uw"][:, 0] = 0.01 * rng.standard_normal(len(links))
+    geo.links = links
+    out = {}
+    for fused in (1, 0):
+        f, F, _, _ = _run_gpu(L, geo, 60, _p(L, prec), nbody=2, fused=fused, tau=0.7, g=(1e-5, 0, 0), bc=2)
+        out[fused] = (f, F)
+    _, w = O.velocity_set(1)
+    h = np.abs(out[0][0] - (w[:, None] if prec == "fp32s" else 0.0)).max()
+    tol = 1e-13 if prec == "fp64" else 4 * 60 * EPS32 * h
+    assert np.abs(out[1][0] - out[0][0]).max() <= tol
+    scale = np.abs(out[0][1]).max()
+    assert np.abs(out[1][1] - out[0][1]).max() <= (1e-12 if prec == "fp64" else 1e-5) * scale
 
 
 def test_moments_device_pointers(L):
@@ -390,7 +435,7 @@ def test_full_size_sphere_pack_sampled_nodes(L, arm):
         vd, shifted = 0, False
     else:
         lat = L.Lattice(geo, precision=L.LBM_FP32_SHIFTED, tau=tau, g=g, bc=2, vibb_density=L.LBM_VIBB_RHO_LOCAL)
-        lat.set_tuning(bulk_shape=0, link_threads=128, link_seq=4, graph_steps=8)
+        lat.set_tuning(bulk_shape=0, link_threads=128, link_seq=4, graph_steps=8, fused=1)
         vd, shifted = 1, True
     lat.init_equilibrium()
     lat.step(3)  # non-uniform state near the walls
