@@ -325,17 +325,27 @@ lbm_status lbm_kernel_times(lbm_handle h, int64_t launches[3], double ms[3]);
  *  f_post   device, FP64 [Q][N]: post-collision populations f+(x, t) as
  *           returned by lbm_get_distributions.
  *  solid    device, N bytes (nonzero = solid); links: device, n_links
- *           lbm_link records as given to lbm_set_geometry.
+ *           lbm_link records as given to lbm_set_geometry.  The records are
+ *           not validated on the host (they are device memory); a record
+ *           whose direction is outside [1, Q), whose node is outside
+ *           [0, N) or solid, or whose rule is unknown contributes nothing.
+ *           Other malformed input (a solid neighbour that is missing, a q
+ *           outside (0, 1]) gives a meaningless force, not an error.
  *  F        device, 3 doubles: receives the force of step t -> t+1, the value
  *           lbm_force(body) reports after lbm_step(1) from the same state
  *           (moments are recomputed from f+, so the two agree to rounding).
+ * Covers a lattice of one domain: the per-domain tau, g, row widths and
+ * inlet settings of lbm_set_domains are not read (cfg's are used for every
+ * row), so the force of a batched lattice would be wrong.
  * Work is queued on cfg->cuda_stream (NULL: the legacy default stream) and
  * the call returns without synchronising.  It allocates nothing: its block
  * partial sums live in a static device array of 3 x 65,536 doubles
  * (1.5 MiB, held by every GPU that loads the library until exit), so
  * n_links is limited to LBM_NOALLOC_MAX_LINKS; larger counts return
  * LBM_ERR_INVALID_ARG.  The first call on a device looks up that array's
- * device address (make it before any stream capture).  All calls share the
+ * device address (make it before any stream capture) and keeps it for the
+ * process: it assumes the device's primary context is not reset
+ * (cudaDeviceReset) afterwards.  All calls share the
  * array: calls that overlap on the GPU race; calls ordered on one stream do
  * not, and each call overwrites every entry it reads.  Deterministic: the
  * same inputs give the same bits.  Errors: INVALID_ARG, UNSUPPORTED, CUDA. */

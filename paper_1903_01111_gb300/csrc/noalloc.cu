@@ -63,8 +63,13 @@ __global__ void __launch_bounds__(kBlock) k_force_partial(const double* __restri
   __syncthreads();
   const int64_t k = blockIdx.x * (int64_t)kBlock + threadIdx.x;
   double F0 = 0.0, F1 = 0.0, F2 = 0.0;
-  if (k < nl && links[k].body == body) {
-    const lbm_link lk = links[k];
+  const lbm_link lk = k < nl ? links[k] : lbm_link{};
+  // the caller's records are not validated on the host: one that would read
+  // outside f or solid (direction outside [1, Q), node outside [0, N) or on
+  // a solid node) or names an unknown rule contributes nothing
+  const bool valid = k < nl && lk.dir >= 1 && lk.dir < L::Q && lk.node >= 0 && lk.node < p.N &&
+                     !solid[lk.node] && lk.bc >= LBM_BC_DEFAULT && lk.bc <= LBM_BC_VIBB;
+  if (valid && lk.body == body) {
     const int64_t N = p.N, nx = p.nx, ny = p.ny, nz = p.nz;
     const int ip = lk.dir, i = tab.opp[ip];
     const double ex = tab.e[ip][0], ey = tab.e[ip][1], ez = tab.e[ip][2];

@@ -353,10 +353,38 @@ def lbm_kernel_times(h):
     return list(n), list(ms)
 
 
+def _check_device_tensor(name, t, dtype, min_bytes):
+    """Type, size and device of a torch tensor handed to the C library as a
+    device pointer (raw integer addresses are passed through unchecked)."""
+    if isinstance(t, int):
+        return
+    import torch
+
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: a torch CUDA tensor or an integer device address is required")
+    if not t.is_cuda or t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name}: must live on the current CUDA device")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name}: dtype {t.dtype}, expected {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if t.numel() * t.element_size() < min_bytes:
+        raise ValueError(f"{name}: {t.numel() * t.element_size()} bytes, at least {min_bytes} needed")
+
+
 def lbm_force_noalloc(cfg: lbm_config, f_post, solid, links, n_links: int, body: int, F) -> None:
     """Momentum-exchange force of the next step from caller-owned device
     memory (torch CUDA tensors or raw device addresses); allocates nothing.
-    Queued on cfg.cuda_stream without synchronising."""
+    Queued on cfg.cuda_stream without synchronising.  Tensors are checked
+    for dtype, size and device before the call (raw addresses are not)."""
+    import torch
+
+    Q = 9 if cfg.stencil == LBM_D2Q9 else 19
+    N = int(cfg.nx) * int(cfg.ny) * int(cfg.nz)
+    _check_device_tensor("f_post", f_post, torch.float64, 8 * Q * N)
+    _check_device_tensor("solid", solid, None, N)
+    _check_device_tensor("links", links, None, LINK_DTYPE.itemsize * int(n_links))
+    _check_device_tensor("F", F, torch.float64, 24)
     _check(_lib.lbm_force_noalloc(ctypes.byref(cfg), _ptr_or_int(f_post), _ptr_or_int(solid), _ptr_or_int(links),
                                   int(n_links), int(body), _ptr_or_int(F)))
 

@@ -66,3 +66,19 @@ def test_config_layouts_agree_with_the_oracle():
     lfields = [f[0] for f in lbm.lbm_config._fields_]
     assert lfields[: len(ofields)] == ofields
     assert O.LINK_DTYPE == lbm.LINK_DTYPE
+
+
+def test_noalloc_binding_rejects_host_tensors_before_the_call():
+    """lbm_force_noalloc's binding checks its tensor arguments (device,
+    dtype, size) before it calls into the library; a host tensor is refused
+    without touching a GPU."""
+    torch = pytest.importorskip("torch")
+    from paper_1903_01111_gb300 import lbm
+
+    cfg = lbm.make_config(stencil=0, nx=8, ny=8, nz=1, tau=0.8)
+    f = torch.zeros(9 * 64, dtype=torch.float64)
+    solid = torch.zeros(64, dtype=torch.uint8)
+    links = torch.zeros(lbm.LINK_DTYPE.itemsize, dtype=torch.uint8)
+    F = torch.zeros(3, dtype=torch.float64)
+    with pytest.raises(ValueError, match="f_post"):
+        lbm.lbm_force_noalloc(cfg, f, solid, links, 1, 0, F)

@@ -65,6 +65,31 @@ def test_noalloc_force_matches_lbm_force_on_two_calls(env, case):
     lat.close()
 
 
+def test_noalloc_calls_leave_free_device_memory_unchanged(env):
+    """The entry point allocates nothing: after a first call on the device
+    (which looks up the scratch array's address), ten more calls leave the
+    device's free memory as it was."""
+    torch, lbm = env
+    geo, kw = _cases()[0]
+    lat = lbm.Lattice(geo, precision=lbm.LBM_FP64, **kw)
+    lat.init_equilibrium()
+    lat.step(5)
+    cfg = lbm.make_config(stencil=geo.stencil, nx=geo.nx, ny=geo.ny, nz=geo.nz, periodic=geo.periodic, **kw)
+    dev = torch.device("cuda")
+    f = torch.from_numpy(lat.distributions()).to(dev)
+    solid = torch.from_numpy(np.ascontiguousarray(geo.solid, np.uint8)).to(dev)
+    links = torch.from_numpy(np.ascontiguousarray(geo.links, dtype=lbm.LINK_DTYPE).view(np.uint8)).to(dev)
+    F = torch.zeros(3, dtype=torch.float64, device=dev)
+    lbm.lbm_force_noalloc(cfg, f, solid, links, len(geo.links), 0, F)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(10):
+        lbm.lbm_force_noalloc(cfg, f, solid, links, len(geo.links), 0, F)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    lat.close()
+
+
 def test_noalloc_rejects_link_counts_beyond_its_scratch(env):
     torch, lbm = env
     cfg = lbm.make_config(stencil=0, nx=8, ny=8, nz=1)
