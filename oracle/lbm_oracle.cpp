@@ -14,7 +14,8 @@
 //      inlet, zero-gradient outlet)
 //   2. streaming by push, Eq. (1):  f_i(x+e_i, t+1) = f+_i(x, t)
 //   3. each cut link rebuilds its missing population (Sec. 3, Eqs. q_less,
-//      q_larger and the VIBB equations of Sec. 3.1); momentum exchange force
+//      q_larger, Yu's two equations, and the VIBB equations of Sec. 3.1);
+//      momentum exchange force
 //   4. moments (Sec. 2, density and velocity sums; velocity shifted by half the
 //      body force, Guo forcing) and BGK collision (Sec. 2, Eq. feq), or the
 //      MRT collision of Eq. (mrt) with the relaxation rates of Sec. 2.
@@ -58,7 +59,7 @@ const double kM[9][9] = {{1, 1, 1, 1, 1, 1, 1, 1, 1},     {-4, -1, -1, -1, -1, 2
                          {0, 0, -2, 0, 2, 1, 1, -1, -1},  {0, 1, -1, 1, -1, 0, 0, 0, 0},
                          {0, 0, 0, 0, 0, 1, -1, 1, -1}};
 
-enum { BC_HALFWAY = 0, BC_BOUZIDI = 1, BC_VIBB = 2 };
+enum { BC_HALFWAY = 0, BC_BOUZIDI = 1, BC_VIBB = 2, BC_YU = 3 };
 enum { NODE_FLUID = 0, NODE_SOLID = 1, NODE_INLET = 2, NODE_OUTLET = 3 };
 
 }  // namespace
@@ -70,7 +71,7 @@ extern "C" {
 struct oracle_config {
   int32_t stencil;    // 0 = D2Q9, 1 = D3Q19
   int32_t collision;  // 0 = BGK, 1 = MRT (D2Q9 only)
-  int32_t bc;         // default link rule: 0 half-way, 1 Bouzidi, 2 VIBB
+  int32_t bc;         // default link rule: 0 half-way, 1 Bouzidi, 2 VIBB, 3 Yu
   int32_t nx, ny, nz;
   int32_t periodic[3];
   int32_t inlet;   // 1: column x = 0 is a velocity inlet (D2Q9)
@@ -305,6 +306,19 @@ struct Oracle {
       // Eq. (q_larger); its last term is read as the post-collision f+_i(x_f, t),
       // which is the population that reaches x_ff at t+1.
       return (fp_f[ip] + wall) / (2.0 * q) + (2.0 * q - 1.0) / (2.0 * q) * fp_f[i];
+    }
+    if (rule == BC_YU) {
+      // Yu's unified interpolation (Sec. 3, the two displayed equations).
+      // First the population that reaches the wall at t+1: it left x_w - e_i'
+      // at t, which lies at q - 1 on the link (x_f at 0, x_ff at -1), so it is
+      // interpolated linearly between f+_i'(x_f) and f+_i'(x_ff), and the
+      // bounce-back at the wall adds the moving-wall term.
+      const T f_wall = q * fp_f[ip] + (1.0 - q) * fp_ff[ip] + wall;
+      // Then x_f lies between x_w (at q) and x_ff (at -1): the second
+      // equation, read with its parenthesis closed after f_i(x_w, t+1), with
+      // f_i(x_ff, t+1) = f+_i(x_f, t) (the population that streams from x_f
+      // to x_ff).
+      return f_wall / (1.0 + q) + q / (1.0 + q) * fp_f[i];
     }
     // VIBB (Sec. 3.1): f_i(x_f,t+1) = feq_i'(rho_d, u_d) + fneq_i'(x_d) + wall
     // Eq. (rhod) as printed extrapolates for q > 1/2; the optional reading

@@ -14,12 +14,14 @@ in the oracle fails at least one of them:
   exact mass and momentum budgets in periodic boxes;
 * link rules (Sec. 3): exactness of the VIBB reconstruction and of Bouzidi's
   interpolation for fields that are linear along the link (departure point
-  x_d = 2q - 1 in link units); Bouzidi at q = 1/2 equals half-way bit for
+  x_d = 2q - 1 in link units); Yu's two interpolations (the wall value at
+  q - 1 from x_f and x_ff, then x_f between x_w and x_ff) rebuilt with
+  numpy's linear interpolation; Bouzidi at q = 1/2 equals half-way bit for
   bit; VIBB at q = 1/2 does not (the paper says so in Sec. 3.1); rest and
   sliding-wall uniform flows are exact fixed points of every rule;
 * whole runs: Poiseuille (Sec. 4.1, Eq. exact) bulk curvature -g/nu, half-way
   exact at tau = 1/2 + sqrt(3)/4, second-order convergence of Bouzidi and
-  VIBB with walls at off-node q, the moving-wall case of Sec. 4.1; circular
+  VIBB and Yu with walls at off-node q, the moving-wall case of Sec. 4.1; circular
   Couette (Sec. 4.2, Eq. exact2) convergence; momentum-exchange force equal
   to the momentum budget at every step; zero lift on a mirror-symmetric body;
   the D3Q19 plane channel: the same curvature, force balance and magic-tau
@@ -239,6 +241,31 @@ def test_bouzidi_linear_interpolation_geometry(q):
     assert abs(got - expect) < 5e-16
 
 
+@pytest.mark.parametrize("stencil", [0, 1])
+@pytest.mark.parametrize("q", [0.05, 0.3, 0.5, 0.8, 1.0])
+def test_yu_interpolation_geometry(stencil, q):
+    """Yu's scheme (Sec. 3): the population that reaches the wall at t+1
+    left x_w - e_i', at q - 1 on the link (x_f at 0, x_ff at -1), and is
+    bounced back with the wall term; x_f then lies between x_w (at q) and
+    x_ff (at -1), where the population moving along e_i at t+1 is
+    f+_i(x_f, t).  Both steps are rebuilt here with numpy's linear
+    interpolation between the given points, for every direction."""
+    e, w = _dirs(stencil)
+    Q = len(w)
+    cfg = O.make_config(stencil=stencil)
+    rng = np.random.default_rng(11)
+    uw = np.array([0.013, -0.021, 0.008 if stencil else 0.0])
+    for ip in range(1, Q):
+        i = [j for j in range(Q) if (e[j] == -e[ip]).all()][0]
+        fpf = rng.uniform(0.02, 0.3, Q)
+        fpff = rng.uniform(0.02, 0.3, Q)
+        wall = 6 * w[ip] * float(e[i] @ uw)
+        at_wall = np.interp(q - 1.0, [-1.0, 0.0], [fpff[ip], fpf[ip]]) + wall
+        expect = np.interp(0.0, [-1.0, q], [fpf[i], at_wall])
+        got = O.link_value(cfg, 3, ip, q, uw, fpf, fpff, 1.0, np.zeros(3), 1.0, np.zeros(3))
+        assert abs(got - expect) < 4e-16, (ip, got, expect)
+
+
 # ------------------------------------------------------------------ runs ---
 
 def _cfg_for(geo, **kw):
@@ -256,7 +283,7 @@ def _small_cylinder(bc=-1, stencil=0):
 
 
 @pytest.mark.parametrize("stencil", [0, 1])
-@pytest.mark.parametrize("bc", [0, 1, 2])
+@pytest.mark.parametrize("bc", [0, 1, 2, 3])
 def test_rest_state_is_fixed_point(stencil, bc):
     g = _small_cylinder(stencil=stencil)
     cfg = _cfg_for(g, tau=0.7, bc=bc)
@@ -268,7 +295,7 @@ def test_rest_state_is_fixed_point(stencil, bc):
 
 
 @pytest.mark.parametrize("stencil", [0, 1])
-@pytest.mark.parametrize("bc", [0, 1, 2])
+@pytest.mark.parametrize("bc", [0, 1, 2, 3])
 def test_sliding_walls_keep_uniform_flow(stencil, bc):
     """Walls at generic q moving tangentially at U carry a uniform flow U
     unchanged (Galilean fixed point): pins the sign and size of the wall
@@ -315,7 +342,7 @@ def test_poiseuille_halfway_exact_at_magic_tau():
     assert np.abs(ux - ex).max() / ex.max() < 1e-9
 
 
-@pytest.mark.parametrize("bc", [1, 2])
+@pytest.mark.parametrize("bc", [1, 2, 3])
 @pytest.mark.parametrize("q", [0.3, 0.7])
 def test_poiseuille_second_order(bc, q):
     errs = []
@@ -469,7 +496,7 @@ def test_shear_wave_decay_rate(stencil, collision):
 def test_force_equals_momentum_budget_every_step():
     """Momentum exchange (Ladd) is the momentum the link rule removes from the
     fluid: J(t+1) - J(t) = N_f g - F(t) at every step, for every rule."""
-    for bc in (0, 1, 2):
+    for bc in (0, 1, 2, 3):
         g = _small_cylinder(bc=-1)
         gvec = np.array([3e-5, 1e-5, 0.0])
         cfg = _cfg_for(g, tau=0.75, bc=bc, g=gvec)
@@ -499,7 +526,7 @@ def test_halfway_conserves_mass_exactly():
         assert abs(st.rho.sum() - m0) > 1e-9
 
 
-@pytest.mark.parametrize("bc", [0, 1, 2])
+@pytest.mark.parametrize("bc", [0, 1, 2, 3])
 def test_mirror_symmetric_body_has_no_lift(bc):
     # circle centred on the mid-plane of a channel with half-way walls
     ny_f = 15
@@ -516,7 +543,7 @@ def test_mirror_symmetric_body_has_no_lift(bc):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("bc", [1, 2])
+@pytest.mark.parametrize("bc", [1, 2, 3])
 def test_couette_convergence(bc):
     """Sec. 4.2, Eq. (exact2): the azimuthal velocity converges to the
     analytic profile; over L = 20 -> 80 at fixed tau the mean order is at
@@ -656,7 +683,7 @@ def _cylinder_case(c, R, tau):
     return G.build(0, (34, 24, 1), (1, 1, 1), bodies)
 
 
-@pytest.mark.parametrize("bc,vd", [(2, 0), (2, 1), (1, 0)])
+@pytest.mark.parametrize("bc,vd", [(2, 0), (2, 1), (1, 0), (3, 0)])
 def test_dual_gradient_matches_finite_differences(bc, vd):
     """Forward-mode derivatives of the drag after 60 steps with respect to the
     cylinder centre, radius and tau equal central differences of the plain
@@ -714,7 +741,7 @@ def test_poiseuille_columns_are_identical():
 
 
 @pytest.mark.parametrize("stencil", [0, 1])
-@pytest.mark.parametrize("bc", [0, 1, 2])
+@pytest.mark.parametrize("bc", [0, 1, 2, 3])
 def test_translated_geometry_gives_translated_state(stencil, bc):
     """An integer shift of a periodic geometry (mask and links moved, q kept)
     moves the state by the same shift, bit for bit."""
