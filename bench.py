@@ -20,7 +20,7 @@ same recipe.
 --part permeability runs the pack for --perm-steps steps (20,000 by default)
 in FP32 shifted and FP64 and reports the Darcy permeability of each;
 --part studies runs the link rules' accuracy studies (Poiseuille over q and
-tau, Couette convergence) on the FP64 path.
+tau, Couette convergence, the Magnus lift curve) on the FP64 path.
 """
 from __future__ import annotations
 
@@ -614,6 +614,52 @@ def run_permeability(lbm, torch, geo, steps, tau=0.7, g=1e-6, samples=4):
     return out
 
 
+def run_magnus(lbm, torch, spins=(0.0, 0.5, 1.0, 1.5, 2.0), rules=(2, 1, 3), steps=40000, sample_every=100):
+    """Magnus effect (Sec. 4.3) on the GPU FP64 path: a cylinder of radius
+    R = 10 spinning at omega = S U / R in a channel of width L = 400 (half-way
+    walls), velocity inlet with the Poiseuille profile of centre-line speed
+    U = 0.05 (non-equilibrium extrapolation), zero-gradient outlet, the field
+    started from that profile.  The paper states Re = 20 with nu = 0.02,
+    which gives 2 U R / nu = 50; the run keeps U and R and takes nu = 0.05
+    (tau = 0.65) so that Re = 2 U R / nu = 20.  The domain is L x L with the
+    cylinder at (100.37, 199.61) in fluid-row coordinates (the channel's
+    centre line is y = 199.5; the paper gives no position).  Lift and drag
+    coefficients C_L = F_y / (rho0 U^2 R), C_D = F_x / (rho0 U^2 R) as in
+    Sec. 4.3, averaged over the last tenth of the run, per link rule.  No
+    literature values are in this repository, so the curve is reported, not
+    compared."""
+    from paper_1903_01111_gb300 import geometry as G
+
+    L, R, U, re = 400, 10.0, 0.05, 20.0
+    nu = 2 * U * R / re
+    tau = 3 * nu + 0.5
+    names = {0: "halfway", 1: "bouzidi", 2: "vibb", 3: "yu"}
+    out = {"L": L, "R": R, "U": U, "Re": re, "nu": nu, "tau": tau, "steps": steps, "center": [100.37, 199.61],
+           "runs": []}
+    for spin in spins:
+        omega = spin * U / R
+        geo = G.cylinder_channel(nx=L, ny_fluid=L, center=(100.37, 199.61), radius=R, u_max=U, omega=omega)
+        y = (np.arange(geo.N) // geo.nx) % geo.ny
+        u0 = np.zeros((geo.N, 3))
+        u0[:, 0] = np.where(geo.solid == 0, 4 * U * (y - 0.5) * (L + 0.5 - y) / L ** 2, 0.0)
+        row = {"S_pa": spin, "omega": omega}
+        for bc in rules:
+            with lbm.Lattice(geo, precision=lbm.LBM_FP64, tau=tau, bc=bc, inlet_umax=U, inlet_y0=0.5,
+                             inlet_y1=L + 0.5) as lat:
+                lat.init_equilibrium(u=u0)
+                Fs = []
+                for _ in range(steps // sample_every):
+                    lat.step(sample_every)
+                    Fs.append(lat.force(0))
+                lat.check()
+            Fs = np.array(Fs[-max(1, len(Fs) // 10):])
+            row[names[bc]] = {"C_L": float(Fs[:, 1].mean() / (U * U * R)),
+                              "C_D": float(Fs[:, 0].mean() / (U * U * R)),
+                              "C_L_spread_last_tenth": float(np.ptp(Fs[:, 1]) / (U * U * R))}
+        out["runs"].append(row)
+    return out
+
+
 def run_studies(lbm, torch):
     """Accuracy studies of the link rules on the GPU FP64 path (the paper's
     validation flows): plane Poiseuille flow (Sec. 4.1) between walls at
@@ -625,8 +671,8 @@ def run_studies(lbm, torch):
     times) from rest; errors are relative L2 over the fluid nodes."""
     from paper_1903_01111_gb300 import geometry as G
 
-    names = {0: "halfway", 1: "bouzidi", 2: "vibb", 3: "vibb_local_rho"}
-    rules = ((0, 0), (1, 0), (2, 0), (2, 1))  # (link rule, VIBB density reading)
+    names = {0: "halfway", 1: "bouzidi", 2: "vibb", 3: "vibb_local_rho", 4: "yu"}
+    rules = ((0, 0), (1, 0), (2, 0), (2, 1), (3, 0))  # (link rule, VIBB density reading)
     out = {"poiseuille": [], "couette": []}
     H, g0 = 24, 1e-6
     for tau in (0.6, 0.8, 1.2):
@@ -675,6 +721,7 @@ def run_studies(lbm, torch):
         c = [row for row in out["couette"] if row["scaling"] == scaling]
         out[f"couette_order_{scaling}"] = {n: [float(np.log2(c[k][n] / c[k + 1][n])) for k in range(len(c) - 1)]
                                            for n in names.values()}
+    out["magnus"] = run_magnus(lbm, torch)
     return out
 
 

@@ -48,7 +48,7 @@ typedef enum {
 
 enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 };
 enum { LBM_BGK = 0, LBM_MRT = 1 };
-enum { LBM_BC_DEFAULT = -1, LBM_BC_HALFWAY = 0, LBM_BC_BOUZIDI = 1, LBM_BC_VIBB = 2 };
+enum { LBM_BC_DEFAULT = -1, LBM_BC_HALFWAY = 0, LBM_BC_BOUZIDI = 1, LBM_BC_VIBB = 2, LBM_BC_YU = 3 };
 enum { LBM_FP64 = 0, LBM_FP32_SHIFTED = 1 };
 enum { LBM_VIBB_RHO_PRINTED = 0, LBM_VIBB_RHO_LOCAL = 1 };
 
@@ -67,7 +67,15 @@ typedef struct lbm_lattice_s* lbm_handle;
  *             relaxation of f - feq in the moment basis M with rates s = 0.3
  *             (moments 0, 3, 5), 1.5 (1, 2), 1.2 (4, 6), 1/tau (7, 8), and
  *             the Guo source projected with (1 - s_k/2) per moment.
- *  bc         default link rule for links whose own rule is LBM_BC_DEFAULT.
+ *  bc         default link rule for links whose own rule is LBM_BC_DEFAULT:
+ *             LBM_BC_HALFWAY (bounce-back, Sec. 3), LBM_BC_BOUZIDI (Eqs.
+ *             q_less, q_larger), LBM_BC_VIBB (Sec. 3.1) or LBM_BC_YU (Yu's
+ *             unified interpolation, Sec. 3: the wall value
+ *             q f+_i'(x_f) + (1 - q) f+_i'(x_ff) + 6 w rho0 (e_i.u_w), then
+ *             f_i(x_f, t+1) = (wall value)/(1 + q) + q/(1 + q) f+_i(x_f, t),
+ *             reading the unbalanced parenthesis of the second equation as
+ *             closing after f_i(x_w, t+1) and f_i(x_ff, t+1) = f+_i(x_f, t)
+ *             by streaming).
  *  nx,ny,nz   lattice size; N = nx*ny*nz nodes.
  *  periodic   per axis, 1 = periodic.  On a non-periodic axis every node of
  *             the two end faces must be solid (or an open column, below).

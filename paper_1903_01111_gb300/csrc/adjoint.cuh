@@ -270,6 +270,16 @@ __global__ void __launch_bounds__(256) k_adj_links(const typename P::T* __restri
       atomic_add_real(lam + (size_t)i * S + kf, om * ((T)1 - inv2q));
       dLdq = -((double)fpf + (double)wall - (double)fpi) / (2.0 * (double)q * (double)q);
     }
+  } else if (rule == 3) {
+    // Yu: L = (q f+_i'(x_f) + (1-q) f+_i'(x_ff) + wall)/(1+q) + q/(1+q) f+_i(x_f)
+    const T fpff = f[(size_t)ip * S + kff];
+    const T fpi = f[(size_t)i * S + kf];
+    const T i1q = (T)1 / ((T)1 + q);
+    atomic_add_real(lam + (size_t)ip * S + kf, om * q * i1q);
+    atomic_add_real(lam + (size_t)ip * S + kff, om * ((T)1 - q) * i1q);
+    atomic_add_real(lam + (size_t)i * S + kf, om * q * i1q);
+    const double q1 = 1.0 + (double)q;
+    dLdq = ((double)fpf - 2.0 * (double)fpff - (double)wall + (double)fpi) / (q1 * q1);
   } else {
     const T fpff = f[(size_t)ip * S + kff];
     const Mom4<T> mf = mom[kf], mff = mom[kff];

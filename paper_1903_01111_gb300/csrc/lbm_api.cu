@@ -337,7 +337,7 @@ lbm_status lbm_create_lattice(const lbm_config* cfg, lbm_handle* out) {
   if (c.collision != LBM_BGK && c.collision != LBM_MRT) return fail(LBM_ERR_INVALID_ARG, "unknown collision %d", c.collision);
   if (c.collision == LBM_MRT && c.stencil != LBM_D2Q9)
     return fail(LBM_ERR_UNSUPPORTED, "MRT is defined for D2Q9 (the moment matrix of the paper)");
-  if (c.bc < LBM_BC_HALFWAY || c.bc > LBM_BC_VIBB) return fail(LBM_ERR_INVALID_ARG, "unknown default rule %d", c.bc);
+  if (c.bc < LBM_BC_HALFWAY || c.bc > LBM_BC_YU) return fail(LBM_ERR_INVALID_ARG, "unknown default rule %d", c.bc);
   if (c.vibb_density != LBM_VIBB_RHO_PRINTED && c.vibb_density != LBM_VIBB_RHO_LOCAL)
     return fail(LBM_ERR_INVALID_ARG, "unknown vibb_density %d", c.vibb_density);
   if (c.nx < 1 || c.ny < 1 || c.nz < 1) return fail(LBM_ERR_INVALID_ARG, "lattice size must be positive");
@@ -547,7 +547,7 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
     if (m[L.node] & (H_SOLID | H_OPEN)) return 2;
     if (L.dir < 1 || L.dir >= Q) return 3;
     if (!(L.q > 0.0 && L.q <= 1.0)) return 4;
-    if (L.bc < LBM_BC_DEFAULT || L.bc > LBM_BC_VIBB) return 5;
+    if (L.bc < LBM_BC_DEFAULT || L.bc > LBM_BC_YU) return 5;
     if (L.body < -1 || L.body >= MAX_BODIES) return 6;
     for (int a = 0; a < 3; ++a)
       if (!std::isfinite(L.uw[a])) return 7;

@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(kBlock) k_force_partial(const double* __restri
   // outside f or solid (direction outside [1, Q), node outside [0, N) or on
   // a solid node) or names an unknown rule contributes nothing
   const bool valid = k < nl && lk.dir >= 1 && lk.dir < L::Q && lk.node >= 0 && lk.node < p.N &&
-                     !solid[lk.node] && lk.bc >= LBM_BC_DEFAULT && lk.bc <= LBM_BC_VIBB;
+                     !solid[lk.node] && lk.bc >= LBM_BC_DEFAULT && lk.bc <= LBM_BC_YU;
   if (valid && lk.body == body) {
     const int64_t N = p.N, nx = p.nx, ny = p.ny, nz = p.nz;
     const int ip = lk.dir, i = tab.opp[ip];
@@ -187,7 +187,7 @@ extern "C" lbm_status lbm_force_noalloc(const lbm_config* cfg, const double* f_p
   if (c.stencil != LBM_D2Q9 && c.stencil != LBM_D3Q19) return fail(LBM_ERR_INVALID_ARG, "unknown stencil");
   if (c.nx < 1 || c.ny < 1 || c.nz < 1 || (c.stencil == LBM_D2Q9 && c.nz != 1))
     return fail(LBM_ERR_INVALID_ARG, "bad lattice size");
-  if (c.bc < LBM_BC_HALFWAY || c.bc > LBM_BC_VIBB) return fail(LBM_ERR_INVALID_ARG, "unknown default rule");
+  if (c.bc < LBM_BC_HALFWAY || c.bc > LBM_BC_YU) return fail(LBM_ERR_INVALID_ARG, "unknown default rule");
   if (!(c.rho0 > 0.0)) return fail(LBM_ERR_INVALID_ARG, "rho0 must be positive");
   double* scratch = nullptr;
   lbm_status st = scratch_for_current_device(&scratch);

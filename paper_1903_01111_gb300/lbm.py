@@ -26,7 +26,7 @@ LBM_OK, LBM_ERR_INVALID_ARG, LBM_ERR_STATE, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_D
     LBM_ERR_UNSUPPORTED = range(8)
 LBM_D2Q9, LBM_D3Q19 = 0, 1
 LBM_BGK, LBM_MRT = 0, 1
-LBM_BC_DEFAULT, LBM_BC_HALFWAY, LBM_BC_BOUZIDI, LBM_BC_VIBB = -1, 0, 1, 2
+LBM_BC_DEFAULT, LBM_BC_HALFWAY, LBM_BC_BOUZIDI, LBM_BC_VIBB, LBM_BC_YU = -1, 0, 1, 2, 3
 LBM_FP64, LBM_FP32_SHIFTED = 0, 1
 LBM_VIBB_RHO_PRINTED, LBM_VIBB_RHO_LOCAL = 0, 1
 LBM_MAX_BODIES = 32768

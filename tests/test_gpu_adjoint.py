@@ -54,6 +54,7 @@ CASES = {
     "vibb_local": dict(bc=2, vibb_density=1),
     "bouzidi": dict(bc=1),
     "halfway": dict(bc=0),
+    "yu": dict(bc=3),
 }
 
 

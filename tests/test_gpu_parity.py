@@ -118,7 +118,7 @@ def _p(L, name):
 # ------------------------------------------------------------------ cases --
 
 @pytest.mark.parametrize("prec", PRECISIONS)
-@pytest.mark.parametrize("bc", [0, 1, 2])
+@pytest.mark.parametrize("bc", [0, 1, 2, 3])
 def test_poiseuille_32x24(L, bc, prec):
     """Plane Poiseuille flow, 32 x 24 fluid nodes, walls at q = 0.3 from the
     first and last fluid rows, g = 1e-6, tau = 0.8, 200 steps."""
@@ -134,7 +134,7 @@ def test_poiseuille_32x24_5000_steps(L):
 
 
 @pytest.mark.parametrize("prec", PRECISIONS)
-@pytest.mark.parametrize("bc", [0, 1, 2])
+@pytest.mark.parametrize("bc", [0, 1, 2, 3])
 def test_rotating_cylinder_ragged_lattice(L, bc, prec):
     """Off-grid rotating cylinder (moving wall velocity per link) in a
     periodic 45 x 33 lattice; the body force has two components."""
@@ -143,7 +143,7 @@ def test_rotating_cylinder_ragged_lattice(L, bc, prec):
 
 
 @pytest.mark.parametrize("prec", PRECISIONS)
-@pytest.mark.parametrize("bc", [0, 1, 2])
+@pytest.mark.parametrize("bc", [0, 1, 2, 3])
 def test_sphere_pack_32(L, bc, prec):
     """D3Q19 body-force flow through a periodic overlapping sphere pack
     (the 384^3 workload's recipe at 32^3 with smaller radii)."""
@@ -173,7 +173,7 @@ def test_open_channel_cylinder(L, prec):
 def test_narrow_gap_second_node_fallback(L):
     """Two circles 0.6 apart: links whose x_ff is solid fall back to x_f."""
     geo = G.build(0, (40, 30, 1), (1, 1, 1), [G.ball((12.2, 15.3, 0), 6.1), G.ball((25.0, 15.3, 0), 6.1)])
-    for bc in (1, 2):
+    for bc in (1, 2, 3):
         _compare(L, geo, 100, L.LBM_FP64, tau=0.75, g=(1e-5, 2e-6, 0), bc=bc)
 
 
@@ -225,7 +225,7 @@ def test_fused_and_split_steps_agree_on_a_moving_pack(L, prec):
     geo = G.sphere_pack(28, porosity=0.5, rmin=2.5, rmax=5.0, seed=11)
     links = geo.links.copy()
     rng = np.random.default_rng(4)
-    links["bc"] = rng.integers(0, 3, len(links))
+    links["bc"] = rng.integers(0, 4, len(links))
     links["body"] = rng.integers(0, 2, len(links))
     links["uw"][:, 0] = 0.01 * rng.standard_normal(len(links))
     geo.links = links
@@ -487,7 +487,7 @@ def test_sphere_pack_32_local_density(L, prec):
 
 
 @pytest.mark.parametrize("prec", PRECISIONS)
-@pytest.mark.parametrize("bc", [0, 1, 2])
+@pytest.mark.parametrize("bc", [0, 1, 2, 3])
 def test_mrt_rotating_cylinder(L, bc, prec):
     """MRT collision (Sec. 2, Eq. mrt, the paper's own operator) with every
     link rule around a rotating off-grid cylinder."""
@@ -505,7 +505,7 @@ def test_mrt_open_channel_cylinder(L, prec):
              inlet_y0=0.5, inlet_y1=30.5)
 
 
-@pytest.mark.parametrize("bc", [0, 1, 2])
+@pytest.mark.parametrize("bc", [0, 1, 2, 3])
 def test_poiseuille_l2_error_fp32_no_worse_than_fp64(L, bc):
     """Analytic case: L2 error of the velocity against the parabolic profile
     of body-force-driven Poiseuille flow (Sec. 4.1) after 12000 steps (about
