@@ -239,11 +239,15 @@ def run_precision(lbm, torch, geo, precision, steps, warmup, dist, peak):
         kernels["k_links"] = {"launches": n_launch[0], "avg_ms": link_ms, "share": kms[0] / max(sum(kms), 1e-30),
                               "gbs": link_bytes / (link_ms * 1e-3) / 1e9, "bytes_per_launch": link_bytes}
     step_bytes = fused_bytes if fused else bulk_bytes + link_bytes
+    link_flops = nl * FLOPS_PER_LINK[2]  # every link of the pack is a VIBB link
+    main_flops = nf * FLOPS_PER_NODE[Q3] + (link_flops if fused else 0)
+    if s == 8 and not fused:
+        kernels["k_links"]["roofline"] = roofline_entry(link_bytes, link_flops, link_ms, s, peak)
     return {
         "mlups": mlups, "ms_per_step": ms / steps, "n_fluid": nf, "n_links": nl, "n_nodes": N,
         "n_cached": info.n_cached, "tuning": tuning.as_dict(),
         "launches": int(sum(n_launch)), "force": F.tolist(),
-        "roofline": dict(roofline_entry(main_bytes, nf * FLOPS_PER_NODE[Q3], main_ms, s, peak), kernel=name,
+        "roofline": dict(roofline_entry(main_bytes, main_flops, main_ms, s, peak), kernel=name,
                          bytes_per_launch=main_bytes, avg_launch_ms=main_ms,
                          traffic=(traffic * nf if traffic else None),
                          traffic_source=("ncu dram__bytes_read+write on a 192^3 pack, per fluid node, scaled"
@@ -280,26 +284,50 @@ def FUSED_LINK_BYTES(s):
     return 8 + 2 * s
 
 
-# FP64 arithmetic peak of GB300, from unit counts and clock: 152 SMs x 2 FP64
-# FMA per clock per SM x 2 flops x 2.07 GHz = 1.26 TFLOP/s (nominal 1.25).
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 arithmetic peak: measured on the device at start-up (lbm_probe_fp64,
+# independent FP64 FMA chains filling every SM, CUDA events); the figure from
+# unit counts (152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz = 1.26
+# TFLOP/s, nominal 1.25) is kept as context.
+FP64_PEAK = {"tflops": None, "source": None}
+FP64_PEAK_DERIVED_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def measure_fp64_peak(lbm):
+    tf, ms = lbm.lbm_probe_fp64()
+    FP64_PEAK.update(tflops=tf, source=f"measured: lbm_probe_fp64 FP64 FMA chains, best of 5 launches ({ms:.3f} ms)",
+                     derived_tflops=FP64_PEAK_DERIVED_TFLOPS)
+    return tf
+
+
 # Algorithmic FP64 flops of one BGK + Guo node update (FMA = 2) in the form
 # the kernel evaluates, per pair of opposite directions (e.u, 4.5 (e.u)^2 -
 # 1.5 u.u, A, B, omega A and omega B, the two source terms, two outputs: 20
 # plus the adds of e.u) and once per node (moments, velocity, u.u, u.g, the
 # rest direction, weight products): D2Q9 4 pairs -> 125, D3Q19 9 pairs -> 263.
 FLOPS_PER_NODE = {9: 125, 19: 263}
+# Algorithmic flops of one link rule as link_value evaluates it (a division
+# counts 1) plus the momentum-exchange term (t = f+ + value, 3 FMA = 7):
+# VIBB 108-112 (wall term 8, rho_d 4, the two non-equilibrium parts 2 x 20,
+# n_d 7 with 2 divisions, the u*, u** weights 6-10 with 1-2 divisions, u_d
+# 15, the equilibrium at d and the sum 21) -> 118 with the force term;
+# Bouzidi 14-16 -> 22; half-way 9 -> 16; Yu 19 -> 26.
+FLOPS_PER_LINK = {0: 16, 1: 22, 2: 118, 3: 26}
+
+
+HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e specification, context for the measured copy rate
 
 
 def roofline_entry(bytes_per_launch, flops_per_launch, avg_ms, s, peak_gbs):
     gbs = bytes_per_launch / (avg_ms * 1e-3) / 1e9
     if s == 8:
         tf = flops_per_launch / (avg_ms * 1e-3) / 1e12
-        return {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": tf / FP64_PEAK_TFLOPS, "traffic": None, "hbm_gbs": gbs, "hbm_frac": gbs / peak_gbs,
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz"}
+        pk = FP64_PEAK["tflops"] or FP64_PEAK_DERIVED_TFLOPS
+        return {"bound": "alu", "achieved": tf, "peak": pk, "unit": "TFLOP/s",
+                "frac": tf / pk, "traffic": None, "hbm_gbs": gbs, "hbm_frac": gbs / peak_gbs,
+                "peak_source": FP64_PEAK["source"] or "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz",
+                "peak_derived": FP64_PEAK_DERIVED_TFLOPS}
     return {"bound": "hbm", "achieved": gbs, "peak": peak_gbs, "unit": "GB/s", "frac": gbs / peak_gbs,
-            "traffic": None}
+            "traffic": None, "nominal_peak": HBM_NOMINAL_GBS, "frac_of_nominal": gbs / HBM_NOMINAL_GBS}
 
 
 def run_sweep(lbm, torch, steps, peak, scale=1):
@@ -660,6 +688,36 @@ def run_magnus(lbm, torch, spins=(0.0, 0.5, 1.0, 1.5, 2.0), rules=(2, 1, 3), ste
     return out
 
 
+def run_rho_d(lbm, torch, geo, steps=3000, check_every=100):
+    """The printed VIBB density rule (Sec. 3.1, Eq. rhod: rho_d = 2q rho_f +
+    (1 - 2q) rho_ff for every q) against the local reading (rho_d = rho_f for
+    q > 1/2) on the sphere pack, in FP64 and FP32 shifted: the step at which
+    lbm_check first reports a non-finite population or a non-positive
+    density (None: stable over `steps`), and the mean density and its
+    extremes at the end (or at the last good check)."""
+    out = {"steps": steps, "check_every": check_every}
+    for vd, vname in ((lbm.LBM_VIBB_RHO_PRINTED, "printed"), (lbm.LBM_VIBB_RHO_LOCAL, "local")):
+        for prec, pname in ((lbm.LBM_FP64, "fp64"), (lbm.LBM_FP32_SHIFTED, "fp32s")):
+            with lbm.Lattice(geo, precision=prec, tau=0.7, g=(1e-6, 0.0, 0.0), bc=lbm.LBM_BC_VIBB,
+                             vibb_density=vd) as lat:
+                lat.init_equilibrium()
+                diverged, last = None, None
+                for k in range(steps // check_every):
+                    lat.step(check_every)
+                    try:
+                        lat.check()
+                    except lbm.LBMError:
+                        diverged = (k + 1) * check_every
+                        break
+                    if (k + 1) % max(1, steps // check_every // 5) == 0 or k + 1 == steps // check_every:
+                        rho, _ = lat.moments()
+                        r = rho[geo.solid == 0]
+                        last = {"step": (k + 1) * check_every, "rho_mean": float(r.mean()),
+                                "rho_min": float(r.min()), "rho_max": float(r.max())}
+            out[f"{vname}_{pname}"] = {"diverged_at": diverged, "last_check": last}
+    return out
+
+
 def run_studies(lbm, torch):
     """Accuracy studies of the link rules on the GPU FP64 path (the paper's
     validation flows): plane Poiseuille flow (Sec. 4.1) between walls at
@@ -728,7 +786,10 @@ def run_studies(lbm, torch):
 def run_e2e(lbm, torch, geo, steps):
     """Same workload through the C ABI with host buffers: geometry upload,
     initialisation, per step lbm_step(1) + lbm_force to a host array, and the
-    final macroscopic fields copied to host memory."""
+    final macroscopic fields copied to host memory.  `value` is the whole
+    region; setup_s (create is outside it; set_geometry + init_equilibrium),
+    the per-step loop rate and the final read-back are reported apart, so the
+    figure can be read at any step count."""
     import ctypes
 
     solid = np.ascontiguousarray(geo.solid, np.uint8)
@@ -744,36 +805,52 @@ def run_e2e(lbm, torch, geo, steps):
     t0 = time.perf_counter()
     lbm.lbm_set_geometry(h, solid, links)
     lbm.lbm_init_equilibrium(h)
+    ts = time.perf_counter()
     for _ in range(steps):
         lbm.lbm_step(h, 1)
         lbm._check(lbm._lib.lbm_force(h, 0, F))
+    tl = time.perf_counter()
     lbm.lbm_moments(h, rho, u)
     t1 = time.perf_counter()
     info = lbm.lbm_query(h)
+    tuning = lbm.lbm_get_tuning(h)
     lbm.lbm_destroy(h)
     h2d = solid.nbytes + links.nbytes
     d2h = 24 * steps + rho.nbytes + u.nbytes
+    per_step_launches = 1 if tuning.fused and info.n_links else 2
     return {"value": info.n_fluid * steps / (t1 - t0) / 1e6, "unit": "MLUPS",
             "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps, "seconds": t1 - t0,
-            "gpu_launches": steps * 2 + 2}
+            "setup_s": ts - t0, "loop_s": tl - ts, "readback_s": t1 - tl, "steps": steps,
+            "loop_mlups": info.n_fluid * steps / (tl - ts) / 1e6,
+            "loop_note": "per step lbm_step(1) + lbm_force (24 B to the host, one stream synchronisation)",
+            "gpu_launches": steps * per_step_launches + 2}
 
 
 def run_oracle(n, steps):
-    """The FP64 CPU oracle on an n^3 sub-case of the same recipe."""
+    """The FP64 CPU oracle on an n^3 sub-case of the same recipe, on every
+    host core (OpenMP over its per-node passes; the result does not depend
+    on the thread count) and on one thread."""
     import oracle as O
 
     geo = geometry(n)
     cfg = O.make_config(stencil=1, nx=n, ny=n, nz=n, periodic=(1, 1, 1), tau=0.7, g=(1e-6, 0, 0), bc=2,
                         vibb_density=1)
-    st = O.init(cfg, geo.solid)
-    O.run(cfg, geo.solid, geo.links, st, 1)
-    t0 = time.perf_counter()
-    O.run(cfg, geo.solid, geo.links, st, steps)
-    dt = time.perf_counter() - t0
     nf = geo.fluid_count()
-    return {"value": nf * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+    out = {}
+    for threads in (os.cpu_count() or 1, 1):
+        used = O.set_threads(threads)
+        st = O.init(cfg, geo.solid)
+        O.run(cfg, geo.solid, geo.links, st, 1)
+        t0 = time.perf_counter()
+        O.run(cfg, geo.solid, geo.links, st, steps)
+        dt = time.perf_counter() - t0
+        out[threads] = (nf * steps / dt / 1e6, used, dt)
+    v, used, dt = out[os.cpu_count() or 1]
+    v1, _, dt1 = out[1]
+    return {"value": v, "unit": "MLUPS", "cores": used, "kind": "oracle",
             "sample": f"{n}^3 sub-case of the same sphere-pack recipe ({nf} fluid nodes, {len(geo.links)} links), "
-                      f"{steps} steps, FP64 oracle, single thread, {dt:.1f} s"}
+                      f"{steps} steps, FP64 oracle, {used} OpenMP threads (nproc), {dt:.1f} s",
+            "single_thread": {"value": v1, "unit": "MLUPS", "cores": 1, "seconds": dt1}}
 
 
 def reference_arm(args):
@@ -785,6 +862,7 @@ def reference_arm(args):
     n = max(32, min(96, n))
     import oracle as O
 
+    cores = O.set_threads(os.cpu_count() or 1)
     geo = geometry(n)
     cfg = O.make_config(stencil=1, nx=n, ny=n, nz=n, periodic=(1, 1, 1), tau=0.7, g=(1e-6, 0, 0), bc=2,
                         vibb_density=1)
@@ -800,8 +878,8 @@ def reference_arm(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "sample": f"{n}^3 sub-case of the same recipe",
                        "fluid_nodes": nf, "links": int(len(geo.links)), "parallelism": "replicas"},
-            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                             "sample": f"{n}^3 sub-case, {args.steps} steps, FP64 oracle, single thread"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                             "sample": f"{n}^3 sub-case, {args.steps} steps, FP64 oracle, {cores} OpenMP threads"},
             "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -824,13 +902,15 @@ def main():
     ap.add_argument("--cylinder-steps", type=int, default=60000)
     ap.add_argument("--sweep-steps", type=int, default=100)
     ap.add_argument("--part", default="all",
-                    choices=["all", "batch", "adjoint", "sweep", "cylinder", "permeability", "studies"],
+                    choices=["all", "batch", "adjoint", "sweep", "cylinder", "permeability", "studies", "rho_d"],
                     help="run one section alone (for profiling) and print its JSON")
     ap.add_argument("--batch-domains", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=2000)
     ap.add_argument("--adjoint-steps", type=int, default=20000)
     ap.add_argument("--adjoint-fd", action="store_true", help="with --part adjoint: also the FD check")
     ap.add_argument("--sweep-scale", type=int, default=1, help="divide the sweep lattices' sides by this")
+    ap.add_argument("--rho-d-steps", type=int, default=3000,
+                    help="with --part rho_d: steps of each sphere-pack run (printed and local rho_d, FP64 and FP32)")
     ap.add_argument("--perm-steps", type=int, default=20000,
                     help="with --part permeability: steps of the sphere-pack run (FP32 shifted and FP64)")
     ap.add_argument("--tuning", default="auto", choices=["auto", "default"],
@@ -857,11 +937,14 @@ def main():
         from paper_1903_01111_gb300 import lbm
 
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        measure_fp64_peak(lbm)
         if args.part == "cylinder":
             out = [run_cylinder(lbm, torch, 20, args.cylinder_steps // 2),
                    run_cylinder(lbm, torch, 100, args.cylinder_steps)]
         elif args.part == "studies":
             out = run_studies(lbm, torch)
+        elif args.part == "rho_d":
+            out = run_rho_d(lbm, torch, geometry(args.n), steps=args.rho_d_steps)
         elif args.part == "permeability":
             out = run_permeability(lbm, torch, geometry(args.n), args.perm_steps)
         elif args.part == "sweep":
@@ -884,6 +967,7 @@ def main():
     from paper_1903_01111_gb300 import lbm
 
     peak, peak_src = _peaks()
+    measure_fp64_peak(lbm)
     t0 = time.perf_counter()
     geo = geometry(args.n)
     t_geo = time.perf_counter() - t0
@@ -907,7 +991,7 @@ def main():
                     run_cylinder(lbm, torch, 100, args.cylinder_steps)]
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cpu = run_oracle(96, 16)
+        cpu = run_oracle(96, 24)
     if rank != 0:
         return 0
     world = dist.get_world_size() if dist is not None else 1
@@ -922,6 +1006,7 @@ def main():
                    "geometry_build_s": t_geo},
         "roofline": dict(r32["roofline"], peak_source=peak_src),
         "hbm_peak_source": peak_src,
+        "fp64_peak": dict(FP64_PEAK),
         "kernels": r32["kernels"], "step_gbs": r32["step_gbs"], "tuning": r32["tuning"],
         "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": r32["launches"],

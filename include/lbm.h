@@ -377,6 +377,15 @@ lbm_status lbm_get_tuning(lbm_handle h, lbm_tuning* t);
  * Errors: STATE, INVALID_ARG, OOM, CUDA. */
 lbm_status lbm_autotune(lbm_handle h, int32_t steps_per_trial, lbm_tuning* best, double* ms_per_step);
 
+/* Measured FP64 arithmetic rate of the current device (no counterpart in
+ * the paper: a measurement aid for the FP64 kernels, which are bound by the
+ * FP64 pipe).  Runs 8 independent FP64 FMA chains per thread in 8 blocks of
+ * 256 threads per SM, 5 timed launches after a warm-up, on the legacy
+ * default stream, and reports the best launch: *tflops = FP64 flops (an FMA
+ * counts 2) per second / 1e12, *ms (NULL allowed) its duration.
+ * Synchronises.  Errors: INVALID_ARG, OOM, CUDA. */
+lbm_status lbm_probe_fp64(double* tflops, double* ms);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* lbm_last_error(void);
 

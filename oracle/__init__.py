@@ -62,7 +62,7 @@ def build(force: bool = False) -> str:
     with _lock:
         if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
             tmp = _LIB + f".tmp{os.getpid()}"
-            subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", _SRC, "-o", tmp])
+            subprocess.check_call(["g++", "-O2", "-std=c++17", "-fopenmp", "-shared", "-fPIC", _SRC, "-o", tmp])
             os.replace(tmp, _LIB)
     return _LIB
 
@@ -87,8 +87,15 @@ def _load():
         lib.oracle_moments.argtypes = [P(OracleConfig), P(u8), P(d), P(d), P(d)]
         lib.oracle_run_dual.argtypes = [P(OracleConfig), P(u8), ctypes.c_void_p, i64, P(d), P(d), ctypes.c_void_p,
                                         ctypes.c_void_p, i64, P(d), P(d), ctypes.c_int]
+        lib.oracle_set_threads.argtypes = [ctypes.c_int]
         _lib = lib
     return _lib
+
+
+def set_threads(n: int = 0) -> int:
+    """OpenMP threads of the oracle's per-node passes (n <= 0: leave as is);
+    returns the count now in use.  Results do not depend on it."""
+    return int(_load().oracle_set_threads(int(n)))
 
 
 def _dp(a):

@@ -25,11 +25,15 @@
 //
 // Parity pins: see tests/test_oracle_pins.py (every function here is pinned
 // there by a closed form, an invariant or a special case).
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace {
 
@@ -386,10 +390,14 @@ int step_once(const Oracle<T>& o, const std::vector<uint8_t>& type, const oracle
       }
     }
   }
-  // 2. streaming by push into fluid nodes (Eq. 1)
+  // 2. streaming by push into fluid nodes (Eq. 1).  The per-node passes run
+  // on OpenMP threads: every node writes its own entries (push targets are
+  // distinct), so the result does not depend on the thread count.
   const T nan = std::nan("");
+#pragma omp parallel for schedule(static)
   for (int64_t k = 0; k < (int64_t)Q * N; ++k) fnew[k] = nan;
   const int64_t len[3] = {o.c.nx, o.c.ny, o.c.nz};
+#pragma omp parallel for collapse(2) schedule(static)
   for (int64_t z = 0; z < len[2]; ++z)
     for (int64_t y = 0; y < len[1]; ++y)
       for (int64_t x = 0; x < len[0]; ++x) {
@@ -409,8 +417,10 @@ int step_once(const Oracle<T>& o, const std::vector<uint8_t>& type, const oracle
           if (type[m] == NODE_FLUID) fnew[i * N + m] = fp[i * N + n];
         }
       }
-  // 3. cut links
-  for (int b = 0; b < nbody * 3; ++b) force[b] = 0.0;
+  // 3. cut links: each link's value (links write distinct entries), then the
+  // momentum exchange summed over the links in order
+  std::vector<T> val(nl);
+#pragma omp parallel for schedule(static)
   for (int64_t k = 0; k < nl; ++k) {
     const oracle_link& L = links[k];
     const int ip = L.dir, i = o.opp[ip];
@@ -425,32 +435,48 @@ int step_once(const Oracle<T>& o, const std::vector<uint8_t>& type, const oracle
     const T uf[3] = {u[3 * f], u[3 * f + 1], u[3 * f + 2]};
     const T uff[3] = {u[3 * ff], u[3 * ff + 1], u[3 * ff + 2]};
     const int rule = L.bc >= 0 ? L.bc : o.c.bc;
-    const T val = o.link_value(rule, ip, qv[k], L.uw, fpf, fpff, rho[f], uf, rho[ff], uff);
-    fnew[i * N + f] = val;
+    val[k] = o.link_value(rule, ip, qv[k], L.uw, fpf, fpff, rho[f], uf, rho[ff], uff);
+  }
+  for (int b = 0; b < nbody * 3; ++b) force[b] = 0.0;
+  for (int64_t k = 0; k < nl; ++k) {
+    const oracle_link& L = links[k];
+    const int ip = L.dir, i = o.opp[ip];
+    fnew[i * N + L.node] = val[k];
     // momentum exchange (Ladd): (f+_i'(x_f,t) + f_i(x_f,t+1)) e_i' on the solid
     if (L.body >= 0 && L.body < nbody)
-      for (int a = 0; a < 3; ++a) force[3 * L.body + a] = force[3 * L.body + a] + (fpf[ip] + val) * (double)o.e[ip][a];
+      for (int a = 0; a < 3; ++a)
+        force[3 * L.body + a] = force[3 * L.body + a] + (fp[ip * N + L.node] + val[k]) * (double)o.e[ip][a];
   }
-  // 4. moments and collision at fluid nodes
-  T f[19], fo[19];
+  // 4. moments and collision at fluid nodes (a node that received no
+  // population is reported: the first such node in node order)
+  int64_t missing = N;
+#pragma omp parallel for schedule(static) reduction(min : missing)
   for (int64_t n = 0; n < N; ++n) {
     if (type[n] != NODE_FLUID) continue;
+    T f[19], fo[19];
+    bool ok = true;
     for (int i = 0; i < Q; ++i) {
       f[i] = fnew[i * N + n];
-      if (std::isnan(value_of(f[i]))) {
-        int64_t x[3];
-        o.coords(n, x);
-        snprintf(g_err, sizeof g_err,
-                 "fluid node (%lld,%lld,%lld) received no population in direction %d: missing link", (long long)x[0],
-                 (long long)x[1], (long long)x[2], i);
-        return -1;
-      }
+      if (std::isnan(value_of(f[i]))) ok = false;
+    }
+    if (!ok) {
+      missing = std::min(missing, n);
+      continue;
     }
     T r, uu[3];
     o.collide(f, fo, r, uu);
     rho[n] = r;
     for (int a = 0; a < 3; ++a) u[3 * n + a] = uu[a];
     for (int i = 0; i < Q; ++i) fp[i * N + n] = fo[i];
+  }
+  if (missing < N) {
+    int64_t x[3];
+    o.coords(missing, x);
+    int dir = 0;
+    while (dir < Q && !std::isnan(value_of(fnew[dir * N + missing]))) ++dir;
+    snprintf(g_err, sizeof g_err, "fluid node (%lld,%lld,%lld) received no population in direction %d: missing link",
+             (long long)x[0], (long long)x[1], (long long)x[2], dir);
+    return -1;
   }
   return 0;
 }
@@ -480,6 +506,17 @@ bool check_config(const oracle_config* c) {
 extern "C" {
 
 const char* oracle_last_error() { return g_err; }
+
+// OpenMP threads of the per-node passes (the results do not depend on it).
+int oracle_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 int oracle_num_velocities(int stencil) { return stencil == 0 ? 9 : 19; }
 

@@ -143,6 +143,7 @@ _sig = {
     "lbm_set_profiling": [_H, ctypes.c_int32],
     "lbm_kernel_times": [_H, _P(ctypes.c_int64), _P(ctypes.c_double)],
     "lbm_force_noalloc": [_P(lbm_config), _vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32, _vp],
+    "lbm_probe_fp64": [_P(ctypes.c_double), _P(ctypes.c_double)],
     "lbm_adjoint_step": [_H, ctypes.c_int32, _vp, ctypes.c_int64, ctypes.c_int64,
                          _P(ctypes.c_double), _vp, _vp, _P(ctypes.c_double)],
     "lbm_set_domains": [_H, _vp, ctypes.c_int32],
@@ -351,6 +352,14 @@ def lbm_kernel_times(h):
     ms = (ctypes.c_double * 3)()
     _check(_lib.lbm_kernel_times(h, n, ms))
     return list(n), list(ms)
+
+
+def lbm_probe_fp64():
+    """Measured FP64 arithmetic rate of the current device: (TFLOP/s, ms of
+    the best timed launch)."""
+    tf, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(_lib.lbm_probe_fp64(ctypes.byref(tf), ctypes.byref(ms)))
+    return tf.value, ms.value
 
 
 def _check_device_tensor(name, t, dtype, min_bytes):

@@ -39,7 +39,16 @@ def test_roofline_entry_fp32_and_fp64():
     r64 = bench.roofline_entry(6.0e9, 0.63e9, 1.0, 8, 6000.0)
     assert r64["bound"] == "alu" and r64["unit"] == "TFLOP/s"
     assert abs(r64["achieved"] - 0.63) < 1e-12
-    assert abs(r64["frac"] - 0.63 / bench.FP64_PEAK_TFLOPS) < 1e-12
+    # without a measured FP64 rate the figure from unit counts stands in, and says so
+    assert bench.FP64_PEAK["tflops"] is None
+    assert abs(r64["frac"] - 0.63 / bench.FP64_PEAK_DERIVED_TFLOPS) < 1e-12
+    assert r64["peak_source"].startswith("derived")
+    bench.FP64_PEAK.update(tflops=1.25, source="measured: test")
+    try:
+        r64 = bench.roofline_entry(6.0e9, 0.63e9, 1.0, 8, 6000.0)
+        assert abs(r64["frac"] - 0.63 / 1.25) < 1e-12 and r64["peak_source"] == "measured: test"
+    finally:
+        bench.FP64_PEAK.update(tflops=None, source=None)
 
 
 def test_darcy_permeability_normalisation():
