@@ -212,8 +212,10 @@ def test_step_chunks_and_profiling_are_bitwise_equal(L, fused):
         lat.close()
     for f, F in outs[1:]:
         assert np.array_equal(f, outs[0][0])
-        # block partial sums meet in FP64 atomics, whose order may vary
-        np.testing.assert_allclose(F, outs[0][1], rtol=1e-13, atol=1e-18)
+        # block partial sums meet in FP64 atomics, whose order may vary; the
+        # lift is a sum of link terms that cancel to about 1e-3 of their
+        # magnitudes, so a last-place reordering shows at ~1e-13 of it
+        np.testing.assert_allclose(F, outs[0][1], rtol=1e-12, atol=1e-18)
 
 
 @pytest.mark.parametrize("prec", PRECISIONS)
