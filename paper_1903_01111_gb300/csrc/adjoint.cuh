@@ -57,11 +57,12 @@ __device__ __forceinline__ typename P::T collide_adjoint(const typename P::T (&f
   }
   const T rho = P::shifted ? (T)p.rho0 + r : r;
   const T gx = (T)rx.g[0], gy = (T)rx.g[1], gz = (T)rx.g[2];
-  const T ux = (jx + (T)0.5 * gx) / rho, uy = (jy + (T)0.5 * gy) / rho, uz = (jz + (T)0.5 * gz) / rho;
+  // the velocity as the forward collision forms it (one reciprocal of rho)
+  const T ir = (T)1 / rho;
+  const T ux = (jx + (T)0.5 * gx) * ir, uy = (jy + (T)0.5 * gy) * ir, uz = (jz + (T)0.5 * gz) * ir;
   const T omega = (T)rx.omega;
   const T uu15 = (T)1.5 * (ux * ux + uy * uy + uz * uz);
   const T ug = ux * gx + uy * gy + uz * gz;
-  T A = 0, B0 = 0, B1 = 0, B2 = 0, dtau = 0;
   // The u-derivatives of the equilibrium and of the source, and f - feq +
   // src/2, sum to zero over the directions (mass is conserved and the source
   // carries no mass), so the B and dtau sums may use lambda minus its mean:
@@ -71,26 +72,55 @@ __device__ __forceinline__ typename P::T collide_adjoint(const typename P::T (&f
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) lbar += lam[i];
   lbar *= (T)(1.0 / L::Q);
+  // Every sum over the directions below is a polynomial in e_i of degree
+  // <= 2 weighted by w_i (lam_i - lbar), so it is formed from the moments
+  //   S0 = sum w_i d_i,  S_a = sum w_i d_i e_ia,  T_ab = sum w_i d_i e_ia e_ib
+  // (d_i = lam_i - lbar) and from lf = sum d_i f_i:
+  //   A   = sum lam_i w_i (1 + poly_i) = S0 (1 - 1.5 u.u) + lbar + 3 u.S + 4.5 u.T.u
+  //   B_a = omega rho (3 S_a + 9 (T u)_a - 3 u_a S0) + (1 - omega/2) (9 (T g)_a - 3 g_a S0)
+  //   dtau sum = lf - sum d_i feq_i + sum d_i src_i / 2
+  T S0 = 0, Sx = 0, Sy = 0, Sz = 0, Txx = 0, Tyy = 0, Tzz = 0, Txy = 0, Txz = 0, Tyz = 0, lf = 0;
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
-    const T ex = (T)L::cx(i), ey = (T)L::cy(i), ez = (T)L::cz(i);
-    const T ld = lam[i] - lbar;
-    const T w = (T)L::w(i);
-    const T eu = ex * ux + ey * uy + ez * uz;
-    const T poly = (T)3 * eu + (T)4.5 * eu * eu - uu15;
-    const T feq = P::shifted ? w * (r + rho * poly) : w * rho * ((T)1 + poly);
-    const T eg = ex * gx + ey * gy + ez * gz;
-    const T src = rx.has_force ? w * ((T)3 * (eg - ug) + (T)9 * eu * eg) : (T)0;
-    // d feq_i / d rho at fixed u, and the u-derivatives of feq_i and of the source
-    A += lam[i] * w * ((T)1 + poly);
-    const T c1 = omega * w * rho, c2 = ((T)1 - (T)0.5 * omega) * w;
-    B0 += ld * (c1 * ((T)3 * ex + (T)9 * eu * ex - (T)3 * ux) + c2 * ((T)-3 * gx + (T)9 * ex * eg));
-    B1 += ld * (c1 * ((T)3 * ey + (T)9 * eu * ey - (T)3 * uy) + c2 * ((T)-3 * gy + (T)9 * ey * eg));
-    B2 += ld * (c1 * ((T)3 * ez + (T)9 * eu * ez - (T)3 * uz) + c2 * ((T)-3 * gz + (T)9 * ez * eg));
-    // dC_i/dtau = (f_i - feq_i + src_i / 2) / tau^2
-    dtau += ld * (f[i] - feq + (T)0.5 * src);
+    const T d = lam[i] - lbar;
+    const T wd = (T)L::w(i) * d;
+    const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+    S0 += wd;
+    if (cx > 0) Sx += wd;
+    if (cx < 0) Sx -= wd;
+    if (cy > 0) Sy += wd;
+    if (cy < 0) Sy -= wd;
+    if (cz > 0) Sz += wd;
+    if (cz < 0) Sz -= wd;
+    if (cx != 0) Txx += wd;
+    if (cy != 0) Tyy += wd;
+    if (cz != 0) Tzz += wd;
+    if (cx * cy > 0) Txy += wd;
+    if (cx * cy < 0) Txy -= wd;
+    if (cx * cz > 0) Txz += wd;
+    if (cx * cz < 0) Txz -= wd;
+    if (cy * cz > 0) Tyz += wd;
+    if (cy * cz < 0) Tyz -= wd;
+    lf += d * f[i];
   }
-  const T ir = (T)1 / rho;
+  const T Tux = Txx * ux + Txy * uy + Txz * uz, Tuy = Txy * ux + Tyy * uy + Tyz * uz,
+          Tuz = Txz * ux + Tyz * uy + Tzz * uz;
+  const T Tgx = Txx * gx + Txy * gy + Txz * gz, Tgy = Txy * gx + Tyy * gy + Tyz * gz,
+          Tgz = Txz * gx + Tyz * gy + Tzz * gz;
+  const T uS = ux * Sx + uy * Sy + uz * Sz, uTu = ux * Tux + uy * Tuy + uz * Tuz;
+  const T A = S0 * ((T)1 - uu15) + lbar + (T)3 * uS + (T)4.5 * uTu;
+  const T orho = omega * rho, c2 = (T)1 - (T)0.5 * omega;
+  const T B0 = orho * ((T)3 * Sx + (T)9 * Tux - (T)3 * ux * S0) + c2 * ((T)9 * Tgx - (T)3 * gx * S0);
+  const T B1 = orho * ((T)3 * Sy + (T)9 * Tuy - (T)3 * uy * S0) + c2 * ((T)9 * Tgy - (T)3 * gy * S0);
+  const T B2 = orho * ((T)3 * Sz + (T)9 * Tuz - (T)3 * uz * S0) + c2 * ((T)9 * Tgz - (T)3 * gz * S0);
+  // sum d_i feq_i (storage form: feq_i = w_i (r + rho poly_i) shifted, w_i rho (1 + poly_i) else)
+  const T dpoly = (T)3 * uS + (T)4.5 * uTu - uu15 * S0;
+  const T dfeq = P::shifted ? r * S0 + rho * dpoly : rho * (S0 + dpoly);
+  // sum d_i src_i, src_i = w_i (3 (e_i.g - u.g) + 9 (e_i.u)(e_i.g))
+  const T dsrc = rx.has_force ? (T)3 * (gx * Sx + gy * Sy + gz * Sz) - (T)3 * ug * S0 +
+                                    (T)9 * (ux * Tgx + uy * Tgy + uz * Tgz)
+                              : (T)0;
+  const T dtau = lf - dfeq + (T)0.5 * dsrc;
 #pragma unroll
   for (int j = 0; j < L::Q; ++j) {
     const T ex = (T)L::cx(j), ey = (T)L::cy(j), ez = (T)L::cz(j);
@@ -99,35 +129,45 @@ __device__ __forceinline__ typename P::T collide_adjoint(const typename P::T (&f
   return dtau * (T)(rx.omega * rx.omega);
 }
 
-// Adds v to target[key] over the block (key < 0: nothing to add): when
-// every contributing thread has the same key, warp sums in the value's own
-// precision, the block sum and one atomic in FP64; else one FP64 atomic per
-// thread.
+// Adds v to target[key] over the block (key < 0: nothing to add): a warp
+// whose contributing lanes share one key sums in the value's own precision
+// by shuffles (any other warp adds per thread with FP64 atomics); after one
+// barrier the first thread adds the warp sums in FP64, one atomic per run of
+// equal keys.
 template <class T>
 __device__ __forceinline__ void block_add_keyed(T v, int key, double* target) {
   __shared__ double red[32];
-  __shared__ int kref;
-  if (threadIdx.x == 0) kref = -1;
-  __syncthreads();
-  const int wmax = __reduce_max_sync(0xffffffffu, key);
-  if ((threadIdx.x & 31) == 0 && wmax >= 0) atomicMax(&kref, wmax);
-  __syncthreads();
-  const int k0 = kref;
-  if (!__syncthreads_and(key < 0 || key == k0)) {
+  __shared__ int rkey[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int wk = __reduce_max_sync(0xffffffffu, key);
+  const bool uniform = __all_sync(0xffffffffu, key < 0 || key == wk);
+  if (!uniform) {
     if (key >= 0 && v != (T)0) atomicAdd(target + key, (double)v);
-    return;
+    v = (T)0;
+  } else if (key < 0) {
+    v = (T)0;
   }
-  if (k0 < 0) return;
-  if (key < 0) v = (T)0;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) red[warp] = (double)v;
+  if (lane == 0) {
+    red[warp] = (double)v;
+    rkey[warp] = uniform ? wk : -1;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
+    int cur = -1;
     double acc = 0.0;
-    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) acc += red[w];
-    atomicAdd(target + k0, acc);
+    for (int wi = 0; wi < (int)((blockDim.x + 31) >> 5); ++wi) {
+      const int kk = rkey[wi];
+      if (kk < 0) continue;
+      if (kk != cur) {
+        if (cur >= 0) atomicAdd(target + cur, acc);
+        cur = kk;
+        acc = 0.0;
+      }
+      acc += red[wi];
+    }
+    if (cur >= 0) atomicAdd(target + cur, acc);
   }
 }
 
@@ -155,12 +195,12 @@ __global__ void __launch_bounds__(256, (adj_bulk_blocks_per_sm<L, P>())) k_adj_b
       const RunRec run = lay.runs[w & W_RUN];
       key = lay.ndom > 1 ? run.dom : 0;
       const Relax rx = lay.ndom > 1 ? relax_domain(lay.dom, key) : relax_params(p);
-      uint32_t src[L::Q];
-      pull_sources<L>(k, run, lay, p, src);
+      int d[L::Q];
+      pull_offsets<L>(k, run, lay, p, d);
       T f[L::Q], lam[L::Q], mu[L::Q];
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) {
-        f[i] = fin[(size_t)i * S + src[i]];
+        f[i] = fin[(ptrdiff_t)i * (ptrdiff_t)S + (ptrdiff_t)k + d[i]];
         lam[i] = lam_next[(size_t)i * S + k];
       }
       if (w & W_CACHE) {
@@ -180,7 +220,7 @@ __global__ void __launch_bounds__(256, (adj_bulk_blocks_per_sm<L, P>())) k_adj_b
       }
       dt = collide_adjoint<L, P>(f, lam, mu, p, rx);
 #pragma unroll
-      for (int i = 0; i < L::Q; ++i) lam_out[(size_t)i * S + src[i]] = mu[i];
+      for (int i = 0; i < L::Q; ++i) lam_out[(ptrdiff_t)i * (ptrdiff_t)S + (ptrdiff_t)k + d[i]] = mu[i];
     }
   }
   block_add_keyed<T>(dt, key, dtau);
@@ -204,29 +244,57 @@ __device__ __forceinline__ void scatter_moment_adjoint(T* __restrict__ lam, size
 // k_adj_bulk, whose entry (i', x_f) is cleared here.  final_step: add the
 // objective's direct terms J = sum_b wbody[b] . F_b(step) (wbody: [nbody][3]
 // FP64).
-template <class L, class P>
-__global__ void __launch_bounds__(256) k_adj_links(const typename P::T* __restrict__ f,
-                                                   const Mom4<typename P::T>* __restrict__ mom,
-                                                   typename P::T* __restrict__ lam, typename P::T* __restrict__ lam_in,
-                                                   const LinkRec* __restrict__ recs,
-                                                   const typename P::T* __restrict__ qv,
-                                                   const typename P::T* __restrict__ uwv, int64_t nl, Params p,
-                                                   int64_t S_, double* __restrict__ dq_acc, int final_step,
-                                                   const double* __restrict__ wbody) {
-  using T = typename P::T;
-  __shared__ DirTable<T, L::Q> tab;
-  if (threadIdx.x < L::Q) {
-    const int d = threadIdx.x;
-    tab.off[d] = 0;
-    tab.opp[d] = L::opp(d);
-    tab.w[d] = (T)L::w(d);
-    tab.e[d][0] = (T)L::cx(d);
-    tab.e[d][1] = (T)L::cy(d);
-    tab.e[d][2] = (T)L::cz(d);
+// Adjoint of the moments (rho, u) of one node (a_r, a_u) that a link
+// leaves to be spread over the node's directions; key = the node's storage
+// index, or ~0 for none.
+template <class T>
+struct MomAdj {
+  uint32_t key;
+  T ar, a0, a1, a2;
+  Mom4<T> m;
+  T rho;
+};
+
+// Spreads each warp's pending moment adjoints: lanes holding the same node
+// (links of one node are consecutive in the link order) are summed by a
+// segmented scan and the segment's last lane adds the sum to the node's
+// directions (one set of atomics per node instead of one per link).  All 32
+// lanes of the warp take part.
+template <class L, class T>
+__device__ __forceinline__ void spread_moment_adjoints(T* __restrict__ lam, size_t S, MomAdj<T> a) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t prev = __shfl_up_sync(0xffffffffu, a.key, 1);
+  const uint32_t next = __shfl_down_sync(0xffffffffu, a.key, 1);
+  const bool head = lane == 0 || prev != a.key;
+  const bool tail = lane == 31 || next != a.key;
+  const unsigned heads = __ballot_sync(0xffffffffu, head);
+  const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));  // head of this lane's segment
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T r = __shfl_up_sync(0xffffffffu, a.ar, o), x = __shfl_up_sync(0xffffffffu, a.a0, o),
+            y = __shfl_up_sync(0xffffffffu, a.a1, o), z = __shfl_up_sync(0xffffffffu, a.a2, o);
+    if (lane - o >= start) {
+      a.ar += r;
+      a.a0 += x;
+      a.a1 += y;
+      a.a2 += z;
+    }
   }
-  __syncthreads();
-  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= nl) return;
+  if (tail && a.key != ~0u) scatter_moment_adjoint<L, T>(lam, S, a.key, a.ar, a.a0, a.a1, a.a2, a.m, a.rho);
+}
+
+// The adjoint of link k (k < nl) with the direction table tab; the
+// adjoint of x_f's moments is left in ma (spread by the caller).
+template <class L, class P>
+__device__ __forceinline__ void adj_link(int64_t k, const DirTable<typename P::T, L::Q>& tab,
+                                         const typename P::T* __restrict__ f,
+                                         const Mom4<typename P::T>* __restrict__ mom, typename P::T* __restrict__ lam,
+                                         typename P::T* __restrict__ lam_in, const LinkRec* __restrict__ recs,
+                                         const typename P::T* __restrict__ qv, const typename P::T* __restrict__ uwv,
+                                         int64_t nl, const Params& p, int64_t S_, double* __restrict__ dq_acc,
+                                         int final_step, const double* __restrict__ wbody,
+                                         MomAdj<typename P::T>& ma) {
+  using T = typename P::T;
   const size_t S = (size_t)S_;
   const LinkRec rec = recs[k];
   const int ip = (int)(rec.meta & 31);
@@ -343,7 +411,7 @@ __global__ void __launch_bounds__(256) k_adj_links(const typename P::T* __restri
     const T a_uff2 = aud2 * cff - wff * ((T)3 * ez + (T)9 * euff * ez - (T)3 * mff.uz);
     atomic_add_real(lam + (size_t)ip * S + kf, om * dn_f);
     atomic_add_real(lam + (size_t)ip * S + kff, om * dn_ff);
-    scatter_moment_adjoint<L, T>(lam, S, kf, om * a_rf, om * a_uf0, om * a_uf1, om * a_uf2, mf, rhof);
+    ma = MomAdj<T>{kf, om * a_rf, om * a_uf0, om * a_uf1, om * a_uf2, mf, rhof};
     scatter_moment_adjoint<L, T>(lam, S, kff, om * a_rff, om * a_uff0, om * a_uff1, om * a_uff2, mff, rhoff);
     const double drd_q = local ? 0.0 : 2.0 * ((double)mf.r - (double)mff.r);
     dLdq = (double)gd * drd_q + (double)rhod * (2.0 * (double)neq_f / (double)rhof - 2.0 * (double)neq_ff / (double)rhoff) +
@@ -354,6 +422,29 @@ __global__ void __launch_bounds__(256) k_adj_links(const typename P::T* __restri
   dq_acc[k] += (double)om * dLdq;
   lam[(size_t)i * S + ks] = (T)0;
   lam_in[(size_t)ip * S + kf] = (T)0;
+}
+
+// One thread per link.  lam: lambda(s) under construction (ghost slots hold
+// the weights of the link values); lam_in: lambda(s+1), already read by
+// k_adj_bulk, whose entry (i', x_f) is cleared here.  final_step: add the
+// objective's direct terms J = sum_b wbody[b] . F_b(step) (wbody: [nbody][3]
+// FP64).
+template <class L, class P>
+__global__ void __launch_bounds__(256) k_adj_links(const typename P::T* __restrict__ f,
+                                                   const Mom4<typename P::T>* __restrict__ mom,
+                                                   typename P::T* __restrict__ lam, typename P::T* __restrict__ lam_in,
+                                                   const LinkRec* __restrict__ recs,
+                                                   const typename P::T* __restrict__ qv,
+                                                   const typename P::T* __restrict__ uwv, int64_t nl, Params p,
+                                                   int64_t S_, double* __restrict__ dq_acc, int final_step,
+                                                   const double* __restrict__ wbody) {
+  __shared__ DirTable<typename P::T, L::Q> tab;
+  fill_dir_table<L>(tab);
+  __syncthreads();
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  MomAdj<typename P::T> ma{~0u, 0, 0, 0, 0, {0, 0, 0, 0}, 1};
+  if (k < nl) adj_link<L, P>(k, tab, f, mom, lam, lam_in, recs, qv, uwv, nl, p, S_, dq_acc, final_step, wbody, ma);
+  spread_moment_adjoints<L>(lam, (size_t)S_, ma);
 }
 
 // Clears in lam_in the entries (j, m) whose neighbour m + e_j is the open
@@ -378,22 +469,26 @@ __device__ __forceinline__ void clear_open_neighbours(T* __restrict__ lam_in, co
 }
 
 // Open columns (D2Q9): inlet f+(0) = feq(rho1, u_in) + f+(1) - feq(rho1, u1)
-// and outlet f+(nx-1) = f+(nx-2), transposed into columns 1 and nx-2; the
-// open nodes' entries are then cleared (they are not state), and so are the
-// entries of lambda(s+1) (lam_in, read by k_adj_bulk) that point into an open
-// node.
+// and outlet f+(nx-1) = f+(nx-2), transposed into columns 1 and nx-2 (by
+// atomics: cut links of the channel walls add into the same nodes); the open
+// nodes' entries are then cleared (they are not state), and so are the
+// entries of lambda(s+1) (lam_in, read by k_adj_bulk) that point into an
+// open node.  t < ny: inlet of row t; ny <= t < 2 ny: outlet of row t - ny.
 template <class L, class P>
-__global__ void k_adj_open(typename P::T* __restrict__ lam, typename P::T* __restrict__ lam_in,
-                           const Mom4<typename P::T>* __restrict__ mom, Layout lay, Params p) {
+__device__ __forceinline__ void adj_open_row(int t, typename P::T* __restrict__ lam, typename P::T* __restrict__ lam_in,
+                                             const Mom4<typename P::T>* __restrict__ mom, const Layout& lay,
+                                             const Params& p) {
   using T = typename P::T;
-  const int y = blockIdx.x * blockDim.x + threadIdx.x;
-  if (y >= p.ny) return;
+  if (t >= 2 * p.ny) return;
+  const bool inlet_side = t < p.ny;
+  const int y = inlet_side ? t : t - p.ny;
   const size_t S = (size_t)lay.S;
-  if (p.inlet) {
+  if (inlet_side && p.inlet) {
+    // the inflow velocity does not depend on the row's storage: issued first
+    const T uin = (T)inlet_velocity(p, lay, y);
     const int32_t k0 = lay.row_first[y];
     if (k0 >= 0 && (lay.word[k0] & W_OPEN)) {
       const uint32_t k1 = (uint32_t)k0 + 1;
-      const T uin = (T)inlet_velocity(p, lay, y);
       const Mom4<T> m1 = mom[k1];
       T l0[L::Q];
       T sp = 0, B0 = 0, B1 = 0;
@@ -409,32 +504,59 @@ __global__ void k_adj_open(typename P::T* __restrict__ lam, typename P::T* __res
         B0 += l0[i] * w * ((T)3 * ex + (T)9 * e1 * ex - (T)3 * m1.ux);
         B1 += l0[i] * w * ((T)3 * ey + (T)9 * e1 * ey - (T)3 * m1.uy);
       }
-      T l1[L::Q];
-#pragma unroll
-      for (int j = 0; j < L::Q; ++j) l1[j] = lam[(size_t)j * S + k1];
 #pragma unroll
       for (int j = 0; j < L::Q; ++j)
-        lam[(size_t)j * S + k1] = l1[j] + l0[j] + sp - (B0 * ((T)L::cx(j) - m1.ux) + B1 * ((T)L::cy(j) - m1.uy));
+        atomic_add_real(lam + (size_t)j * S + k1, l0[j] + sp - (B0 * ((T)L::cx(j) - m1.ux) + B1 * ((T)L::cy(j) - m1.uy)));
 #pragma unroll
       for (int j = 0; j < L::Q; ++j) lam[(size_t)j * S + k0] = (T)0;
       clear_open_neighbours<L, T>(lam_in, lay, p, y, -1);
     }
   }
-  if (p.outlet) {
+  if (!inlet_side && p.outlet) {
     const int32_t kl = lay.row_last[y];
     if (kl >= 0 && (lay.word[kl] & W_OPEN)) {
-      T a[L::Q], b[L::Q];
+      T a[L::Q];
 #pragma unroll
-      for (int i = 0; i < L::Q; ++i) {
-        a[i] = lam[(size_t)i * S + kl];
-        b[i] = lam[(size_t)i * S + kl - 1];
-      }
+      for (int i = 0; i < L::Q; ++i) a[i] = lam[(size_t)i * S + kl];
 #pragma unroll
-      for (int i = 0; i < L::Q; ++i) lam[(size_t)i * S + kl - 1] = a[i] + b[i];
+      for (int i = 0; i < L::Q; ++i) atomic_add_real(lam + (size_t)i * S + kl - 1, a[i]);
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) lam[(size_t)i * S + kl] = (T)0;
       clear_open_neighbours<L, T>(lam_in, lay, p, y, 1);
     }
+  }
+}
+
+template <class L, class P>
+__global__ void k_adj_open(typename P::T* __restrict__ lam, typename P::T* __restrict__ lam_in,
+                           const Mom4<typename P::T>* __restrict__ mom, Layout lay, Params p) {
+  adj_open_row<L, P>(blockIdx.x * blockDim.x + threadIdx.x, lam, lam_in, mom, lay, p);
+}
+
+// The link and open-column transposes of one step in one launch: blocks
+// [0, nbo) take the open rows (as k_adj_open; first, so that their scattered
+// accesses overlap the link blocks), the others the links (as
+// k_adj_links); the two parts touch common entries only through atomics.
+template <class L, class P>
+__global__ void __launch_bounds__(256) k_adj_links_open(const typename P::T* __restrict__ f,
+                                                        const Mom4<typename P::T>* __restrict__ mom,
+                                                        typename P::T* __restrict__ lam,
+                                                        typename P::T* __restrict__ lam_in,
+                                                        const LinkRec* __restrict__ recs,
+                                                        const typename P::T* __restrict__ qv,
+                                                        const typename P::T* __restrict__ uwv, int64_t nl, Params p,
+                                                        int64_t S_, double* __restrict__ dq_acc, int final_step,
+                                                        const double* __restrict__ wbody, Layout lay, int nbo) {
+  if ((int)blockIdx.x >= nbo) {
+    __shared__ DirTable<typename P::T, L::Q> tab;
+    fill_dir_table<L>(tab);
+    __syncthreads();
+    const int64_t k = (blockIdx.x - nbo) * (int64_t)blockDim.x + threadIdx.x;
+    MomAdj<typename P::T> ma{~0u, 0, 0, 0, 0, {0, 0, 0, 0}, 1};
+    if (k < nl) adj_link<L, P>(k, tab, f, mom, lam, lam_in, recs, qv, uwv, nl, p, S_, dq_acc, final_step, wbody, ma);
+    spread_moment_adjoints<L>(lam, (size_t)S_, ma);
+  } else {
+    adj_open_row<L, P>((int)(blockIdx.x * blockDim.x + threadIdx.x), lam, lam_in, mom, lay, p);
   }
 }
 
@@ -491,6 +613,10 @@ struct AdjointOps {
                 const void* uw, int64_t nl, const Params& p, int64_t S, double* dq_acc, int final_step,
                 const double* wbody, cudaStream_t s);
   void (*open)(void* lam, void* lam_in, const void* mom, const Layout& lay, const Params& p, cudaStream_t s);
+  // links and open columns in one launch (lattices with open columns)
+  void (*links_open)(const void* f, const void* mom, void* lam, void* lam_in, const LinkRec* recs, const void* q,
+                     const void* uw, int64_t nl, const Params& p, int64_t S, double* dq_acc, int final_step,
+                     const double* wbody, const Layout& lay, cudaStream_t s);
   void (*init)(const void* f0, const void* lam, const Layout& lay, const Params& p, double* dtau, cudaStream_t s);
 };
 
@@ -511,15 +637,24 @@ struct AdjointLaunch {
                                                          recs, (const T*)q, (const T*)uw, nl, p, S, dq_acc,
                                                          final_step, wbody);
   }
+  static void links_open(const void* f, const void* mom, void* lam, void* lam_in, const LinkRec* recs, const void* q,
+                         const void* uw, int64_t nl, const Params& p, int64_t S, double* dq_acc, int final_step,
+                         const double* wbody, const Layout& lay, cudaStream_t s) {
+    const int nbl = (int)blocks_for(nl, 256);
+    const int nbo = (int)blocks_for(2 * (int64_t)p.ny, 256);
+    k_adj_links_open<L, P><<<nbl + nbo, 256, 0, s>>>((const T*)f, (const Mom4<T>*)mom, (T*)lam, (T*)lam_in, recs,
+                                                     (const T*)q, (const T*)uw, nl, p, S, dq_acc, final_step, wbody,
+                                                     lay, nbo);
+  }
   static void open(void* lam, void* lam_in, const void* mom, const Layout& lay, const Params& p, cudaStream_t s) {
-    k_adj_open<L, P><<<blocks_for(p.ny, 128), 128, 0, s>>>((T*)lam, (T*)lam_in, (const Mom4<T>*)mom, lay, p);
+    k_adj_open<L, P><<<blocks_for(2 * (int64_t)p.ny, 128), 128, 0, s>>>((T*)lam, (T*)lam_in, (const Mom4<T>*)mom, lay, p);
   }
   static void init(const void* f0, const void* lam, const Layout& lay, const Params& p, double* dtau,
                    cudaStream_t s) {
     if (lay.S == 0) return;
     k_adj_init<L, P><<<blocks_for(lay.S, 256), 256, 0, s>>>((const T*)f0, (const T*)lam, lay, p, dtau);
   }
-  static AdjointOps ops() { return AdjointOps{bulk, links, open, init}; }
+  static AdjointOps ops() { return AdjointOps{bulk, links, open, links_open, init}; }
 };
 
 AdjointOps adj_d2q9_f64();

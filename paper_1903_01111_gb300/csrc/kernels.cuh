@@ -954,20 +954,24 @@ __device__ __forceinline__ double inlet_velocity(const Params& p, const Layout& 
 
 // Sec. 4.3: inlet column x = 0 by non-equilibrium extrapolation from x = 1
 // with the parabolic velocity u_in(y); outlet column x = nx-1 copies x = nx-2.
-// One thread per row (D2Q9); the open node is the first (inlet) or last
-// (outlet) stored node of its row and its fluid neighbour is adjacent.
+// One thread per row and side (D2Q9); the open node is the first (inlet) or
+// last (outlet) stored node of its row and its fluid neighbour is adjacent.
 template <class L, class P>
 __global__ void k_open(typename P::T* __restrict__ f, const Mom4<typename P::T>* __restrict__ mom, Layout lay,
                        Params p) {
   using T = typename P::T;
-  const int y = blockIdx.x * blockDim.x + threadIdx.x;
-  if (y >= p.ny) return;
+  // threads 0 .. ny-1: inlet rows; ny .. 2 ny - 1: outlet rows
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * p.ny) return;
+  const bool inlet_side = t < p.ny;
+  const int y = inlet_side ? t : t - p.ny;
   const size_t S = (size_t)lay.S;
-  if (p.inlet) {
+  if (inlet_side && p.inlet) {
+    // the inflow velocity does not depend on the row's storage: issued first
+    const T uin = (T)inlet_velocity(p, lay, y);
     const int32_t k0 = lay.row_first[y];
     if (k0 >= 0 && (lay.word[k0] & W_OPEN)) {
       const uint32_t k1 = (uint32_t)k0 + 1;
-      const T uin = (T)inlet_velocity(p, lay, y);
       const Mom4<T> m1 = mom[k1];
       const T rho1 = P::shifted ? (T)p.rho0 + m1.r : m1.r;
       T v[L::Q];
@@ -979,7 +983,7 @@ __global__ void k_open(typename P::T* __restrict__ f, const Mom4<typename P::T>*
                         (v[i] - equilibrium<L, P>(i, m1.r, rho1, m1.ux, m1.uy, (T)0));
     }
   }
-  if (p.outlet) {
+  if (!inlet_side && p.outlet) {
     const int32_t kl = lay.row_last[y];
     if (kl >= 0 && (lay.word[kl] & W_OPEN)) {
       T v[L::Q];
@@ -1261,7 +1265,7 @@ struct Launch {
       fused_m<false>(fin, fout, lay, r, mom_in, mom_out, force, force_next, p, threads, s);
   }
   static void open(void* f, const void* mom, const Layout& lay, const Params& p, cudaStream_t s) {
-    k_open<L, P><<<blocks_for(p.ny, 128), 128, 0, s>>>((T*)f, (const Mom4<T>*)mom, lay, p);
+    k_open<L, P><<<blocks_for(2 * (int64_t)p.ny, 128), 128, 0, s>>>((T*)f, (const Mom4<T>*)mom, lay, p);
   }
   static void init(void* f, void* mom, const Layout& lay, const double* rho, const double* u, const Params& p,
                    cudaStream_t s) {

@@ -1411,16 +1411,21 @@ lbm_status lbm_adjoint_step(lbm_handle h, int32_t body, const double dJ_dF[3], i
     for (int64_t j = m - 1; j >= 0; --j) {
       void* state = segp + sb * j;
       if (j == m - 1) {
-        // the last state of the segment has no link values yet
-        h->ops.refresh(state, h->lay, am, h->p, h->stream);
+        // the last state of the segment has no link values yet; the moment
+        // cache holds the moments the recompute's last step wrote for it,
+        // those its forward step used (a one-state segment: the refresh of
+        // the recompute)
         h->ops.links(state, am, (const LinkRec*)h->recs.p, h->q.p, h->uw.p, nl, fslot, h->p, S,
                      h->tune.link_threads, h->tune.link_seq, h->stream);
         if (open) h->ops.open(state, am, h->lay, h->p, h->stream);
       }
       h->adj.bulk(state, lam[l].p, lam[l ^ 1].p, h->lay, h->p, dtau, am, h->stream);
-      h->adj.links(state, am, lam[l ^ 1].p, lam[l].p, (const LinkRec*)h->recs.p, h->q.p, h->uw.p, nl, h->p,
-                   S, (double*)dq.p, (last && j == m - 1) ? 1 : 0, wdev, h->stream);
-      if (open) h->adj.open(lam[l ^ 1].p, lam[l].p, am, h->lay, h->p, h->stream);
+      if (open)
+        h->adj.links_open(state, am, lam[l ^ 1].p, lam[l].p, (const LinkRec*)h->recs.p, h->q.p, h->uw.p, nl, h->p, S,
+                          (double*)dq.p, (last && j == m - 1) ? 1 : 0, wdev, h->lay, h->stream);
+      else
+        h->adj.links(state, am, lam[l ^ 1].p, lam[l].p, (const LinkRec*)h->recs.p, h->q.p, h->uw.p, nl, h->p, S,
+                     (double*)dq.p, (last && j == m - 1) ? 1 : 0, wdev, h->stream);
       l ^= 1;
     }
     CUDA_TRY(cudaGetLastError());
