@@ -369,7 +369,7 @@ def run_sweep(lbm, torch, steps, peak, scale=1):
     return out
 
 
-def run_adjoint(lbm, n_steps=20000, checkpoint_every=500, fd=True, fd_all=False):
+def run_adjoint(lbm, n_steps=20000, checkpoint_every=500, fd=True, fd_all=False, fp32_repeats=5):
     """Drag gradient on the 1024 x 256 channel cylinder (radius 16.494, centre
     (256.343, 128.626), u_max 0.1, Re 40 on the mean inflow and the diameter):
     FP32-shifted forward and adjoint with FP64 sensitivity accumulation, cost
@@ -377,7 +377,10 @@ def run_adjoint(lbm, n_steps=20000, checkpoint_every=500, fd=True, fd_all=False)
     and an FP64 fourth-order central-difference check (steps 1e-3, 2e-3) of
     dJ/dR and dJ/dtau; the centre and radius keep every cut link at least
     4e-3 (in theta) away from the q = 1/2 branch switch.  fd_all: the same
-    check of dJ/dc_x and dJ/dc_y (the margin holds for the centre too)."""
+    check of dJ/dc_x and dJ/dc_y (the margin holds for the centre too).  The
+    FP32 adjoint is run fp32_repeats times on the same inputs: its FP32
+    atomic additions land in a different order each run, and the spread of
+    the gradient over the runs is reported next to its error."""
     from paper_1903_01111_gb300.autograd import CylinderSpec, branch_margin, force_only, run
 
     ubar = 2.0 / 3.0 * 0.1
@@ -390,6 +393,7 @@ def run_adjoint(lbm, n_steps=20000, checkpoint_every=500, fd=True, fd_all=False)
     J32, g32 = run(spec, theta)
     sec = spec.last["seconds"]
     cancel = spec.last["cancellation"]
+    g32_runs = [g32] + [run(spec, theta)[1] for _ in range(max(0, fp32_repeats - 1))]
     out = {"workload": "D2Q9 1024x256 channel, cylinder R 16.494 at (256.343, 128.626), u_max 0.1, Re 40, "
                        f"tau {tau:.4f}, {n_steps} steps, checkpoints every {checkpoint_every}",
            "J_drag": J32, "grad_fp32": {"cx": g32[0], "cy": g32[1], "R": g32[2], "tau": g32[3]},
@@ -415,9 +419,15 @@ def run_adjoint(lbm, n_steps=20000, checkpoint_every=500, fd=True, fd_all=False)
         scale = float(np.abs(g64).max())
         for k, name in (((0, "cx"), (1, "cy"), (2, "R"), (3, "tau")) if fd_all else ((2, "R"), (3, "tau"))):
             fd_k = (4 * diff(k, h) - diff(k, 2 * h)) / 3
+            errs = sorted(abs(g[k] - fd_k) / abs(fd_k) for g in g32_runs)
+            vals = [g[k] for g in g32_runs]
             checks[name] = {"adjoint_fp64": g64[k], "fd_fp64": fd_k, "rel_err_fp64": abs(g64[k] - fd_k) / abs(fd_k),
                             "adjoint_fp32": g32[k], "rel_err_fp32_vs_fd": abs(g32[k] - fd_k) / abs(fd_k),
-                            "err_fp32_over_max_grad": abs(g32[k] - fd_k) / scale}
+                            "err_fp32_over_max_grad": abs(g32[k] - fd_k) / scale,
+                            "fp32_runs": len(g32_runs), "rel_err_fp32_min_median_max":
+                                [errs[0], errs[len(errs) // 2], errs[-1]],
+                            "fp32_spread_over_runs_rel": (max(vals) - min(vals)) / abs(fd_k),
+                            "fp32_mean_rel_err": abs(float(np.mean(vals)) - fd_k) / abs(fd_k)}
         out["fd_check"] = checks
     return out
 
