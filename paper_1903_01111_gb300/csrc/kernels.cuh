@@ -163,15 +163,36 @@ __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Pa
                                               Mom4<typename P::T>* __restrict__ mom, bool cache, bool keep = true) {
   using T = typename P::T;
   T r = 0, jx = 0, jy = 0, jz = 0;
+  if constexpr (!P::shifted) {
+    // FP64 (bound by the FP64 pipe, where every add, multiply or FMA takes
+    // one issue slot): density and momentum from the sums and differences of
+    // opposite directions, Q - 1 operations fewer than summing the
+    // directions into each moment
+    r = f[0];
 #pragma unroll
-  for (int i = 0; i < L::Q; ++i) {
-    r += f[i];
-    if (L::cx(i) > 0) jx += f[i];
-    if (L::cx(i) < 0) jx -= f[i];
-    if (L::cy(i) > 0) jy += f[i];
-    if (L::cy(i) < 0) jy -= f[i];
-    if (L::cz(i) > 0) jz += f[i];
-    if (L::cz(i) < 0) jz -= f[i];
+    for (int i = 1; i < L::Q; ++i) {
+      const int j = L::opp(i);
+      if (j < i) continue;
+      r += f[i] + f[j];
+      const T d = f[i] - f[j];
+      if (L::cx(i) > 0) jx += d;
+      if (L::cx(i) < 0) jx -= d;
+      if (L::cy(i) > 0) jy += d;
+      if (L::cy(i) < 0) jy -= d;
+      if (L::cz(i) > 0) jz += d;
+      if (L::cz(i) < 0) jz -= d;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      r += f[i];
+      if (L::cx(i) > 0) jx += f[i];
+      if (L::cx(i) < 0) jx -= f[i];
+      if (L::cy(i) > 0) jy += f[i];
+      if (L::cy(i) < 0) jy -= f[i];
+      if (L::cz(i) > 0) jz += f[i];
+      if (L::cz(i) < 0) jz -= f[i];
+    }
   }
   const T rho = P::shifted ? (T)p.rho0 + r : r;
   const T gx = (T)rx.g[0], gy = (T)rx.g[1], gz = (T)rx.g[2];
@@ -269,29 +290,40 @@ __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Pa
     // sources into Sc +- So with
     //   A  = w rho (1 + 4.5 (e_i.u)^2 - 1.5 u.u),   B = 3 w rho (e_i.u),
     //   Sc = fpre3 w (3 (e_i.g)(e_i.u) - u.g),     So = fpre3 w (e_i.g),
-    // so that f+_i,j = (1 - omega) f_i,j + (omega A + Sc) +- (omega B + So):
-    // fewer operations than one direction at a time.
+    // so that f+_i,j = (1 - omega) f_i,j + (omega A + Sc) +- (omega B + So).
+    // The factors that depend only on the weight class (omega w rho and its
+    // products, fpre3 w and its products) are formed once per node, so that
+    // a pair costs two FMAs and a multiply for omega A and omega B, an FMA
+    // and a multiply for the source, two adds and two FMAs for the outputs.
     const T om1 = (T)1 - omega;
+    const T c0 = (T)1 - uu15;
     {
       const T w = (T)L::w(0);
-      T out = om1 * f[0] + omega * ((w * rho) * ((T)1 - uu15));
+      T out = om1 * f[0] + omega * ((w * rho) * c0);
       if (rx.has_force) out -= fpre3 * w * ug;
       fout[n_] = keep ? out : (T)0;
     }
+    // per weight class k (1: |e| = 1, 2: |e| = sqrt 2): omega w rho and the
+    // products the pairs use
+    const T owr1 = omega * ((T)L::w(1) * rho), owr2 = omega * ((T)L::w(L::Q == 9 ? 5 : 7) * rho);
+    const T a1 = owr1 * c0, a2 = owr2 * c0;                       // omega A at e.u = 0
+    const T h1 = (T)4.5 * owr1, h2 = (T)4.5 * owr2;               // coefficient of (e.u)^2
+    const T b1 = (T)3 * owr1, b2 = (T)3 * owr2;                   // omega B / (e.u)
+    const T fw1 = fpre3 * (T)L::w(1), fw2 = fpre3 * (T)L::w(L::Q == 9 ? 5 : 7);
+    const T s1 = fw1 * ug, s2 = fw2 * ug;                         // fpre3 w (u.g)
+    const T t1 = (T)3 * fw1, t2 = (T)3 * fw2;
 #pragma unroll
     for (int i = 1; i < L::Q; ++i) {
       const int j = L::opp(i);
       if (j < i) continue;
+      const bool diag = L::w(i) < L::w(1);
       const T eu = (T)L::cx(i) * ux + (T)L::cy(i) * uy + (T)L::cz(i) * uz;
-      const T w = (T)L::w(i);
-      const T A = (w * rho) * ((T)1 + (T)4.5 * eu * eu - uu15);
-      const T B = ((T)3 * w * rho) * eu;
-      T Pv = omega * A, Mv = omega * B;
+      T Pv = diag ? (h2 * eu) * eu + a2 : (h1 * eu) * eu + a1;
+      T Mv = (diag ? b2 : b1) * eu;
       if (rx.has_force) {
         const T eg = (T)L::cx(i) * gx + (T)L::cy(i) * gy + (T)L::cz(i) * gz;
-        const T fw = fpre3 * w;
-        Pv += fw * ((T)3 * eg * eu - ug);
-        Mv += fw * eg;
+        Pv += (diag ? t2 : t1) * eg * eu - (diag ? s2 : s1);
+        Mv += (diag ? fw2 : fw1) * eg;
       }
       fout[(size_t)i * S + n_] = keep ? om1 * f[i] + (Pv + Mv) : (T)0;
       fout[(size_t)j * S + n_] = keep ? om1 * f[j] + (Pv - Mv) : (T)0;
