@@ -872,6 +872,7 @@ __global__ void __launch_bounds__(BT, (fused_blocks_per_sm<L, P, BT>())) k_fused
   fill_dir_table<L>(tab);
   if (force_next && blockIdx.x == 0)
     for (int t = threadIdx.x; t < 3 * p.nbody; t += BT) force_next[t] = 0.0;
+  __syncthreads();  // the direction table (every thread arrives here at once)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t base = blockIdx.x * BT;
   const uint32_t k = base + threadIdx.x;
@@ -882,6 +883,15 @@ __global__ void __launch_bounds__(BT, (fused_blocks_per_sm<L, P, BT>())) k_fused
   // the block's range of the link list (the same two words in every thread)
   const int64_t g0 = base >> 5, g1 = g0 + NW < fl.ngroups ? g0 + NW : fl.ngroups;
   const int64_t l0 = __ldg(fl.first + g0), l1 = __ldg(fl.first + g1);
+  const int total = (int)(l1 - l0);
+  // this thread's first link record, requested before the run record and
+  // the pulls so that the link phase does not wait behind them
+  FusedRec r_first{0, 0, 0, 0};
+  T q_first = 0;
+  if ((int)threadIdx.x < total) {
+    r_first = fl.rec[l0 + threadIdx.x];
+    q_first = P::shifted ? (T)__uint_as_float(r_first.q32) : (T)__ldg(fl.qd + l0 + threadIdx.x);
+  }
   const bool fluid = live && !(w & (W_GHOST | W_OPEN));
   T(&col)[L::Q][32] = stage[warp];
   int dom = 0;
@@ -901,14 +911,13 @@ __global__ void __launch_bounds__(BT, (fused_blocks_per_sm<L, P, BT>())) k_fused
     for (int i = 0; i < L::Q; ++i) col[i][lane] = P::shifted ? (T)0 : (T)L::w(i);
   }
   cp_async_commit();
-  __syncthreads();  // the direction table
-  const int total = (int)(l1 - l0);
   const int wb = total > 0 ? (int)(__ldg(&fl.rec[l0].meta) >> 8) - 1 : -1;
   T F0 = 0, F1 = 0, F2 = 0;
   for (int j = threadIdx.x; j < total; j += BT) {
     const int64_t li = l0 + j;
-    const FusedRec r = fl.rec[li];
-    const T q = P::shifted ? (T)__uint_as_float(r.q32) : (T)__ldg(fl.qd + li);
+    const bool first_round = j == (int)threadIdx.x;
+    const FusedRec r = first_round ? r_first : fl.rec[li];
+    const T q = first_round ? q_first : (P::shifted ? (T)__uint_as_float(r.q32) : (T)__ldg(fl.qd + li));
     const int ip = (int)(r.meta & 31);
     const int rule = (int)((r.meta >> 5) & 7);
     const int body = (int)(r.meta >> 8) - 1;
