@@ -25,6 +25,9 @@
  *  - Work is ordered on the lattice's CUDA stream (lbm_config.cuda_stream,
  *    or a stream the library creates).  Calls that return data to the host
  *    synchronise that stream.
+ *  - lbm_set_geometry, lbm_step, lbm_adjoint_step (and each of its
+ *    checkpoint segments) and lbm_autotune mark their host-side span with an
+ *    NVTX range of the same name, for timeline profilers.
  */
 #ifndef LBM_H
 #define LBM_H

@@ -10,6 +10,7 @@
 // steps directly for an odd remainder; with profiling on it launches kernel
 // by kernel between CUDA events.  lbm_autotune picks the launch shapes.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -30,6 +31,15 @@ using namespace lbm;
 namespace {
 
 thread_local char g_msg[1024] = "";
+
+// NVTX range over a scope (host-side annotation for timeline profilers;
+// without a profiler attached the calls return at once).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 lbm_status fail(lbm_status st, const char* fmt, ...) {
   va_list ap;
@@ -457,6 +467,7 @@ lbm_status lbm_set_domains(lbm_handle h, const lbm_domain* d, int32_t n) {
 
 lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* links, int64_t n_links) {
   g_msg[0] = 0;
+  NvtxRange range("lbm_set_geometry");
   if (!h || !solid || n_links < 0 || (n_links > 0 && !links)) return fail(LBM_ERR_INVALID_ARG, "null or negative argument");
   const lbm_config& c = h->cfg;
   const int64_t N = h->N, nx = c.nx, ny = c.ny, nz = c.nz;
@@ -1081,6 +1092,7 @@ lbm_status lbm_init_equilibrium(lbm_handle h, const double* rho, const double* u
 
 lbm_status lbm_step(lbm_handle h, int64_t n) {
   g_msg[0] = 0;
+  NvtxRange range("lbm_step");
   if (!h) return fail(LBM_ERR_INVALID_ARG, "null handle");
   if (n < 0) return fail(LBM_ERR_INVALID_ARG, "negative step count");
   if (!h->has_state) return fail(LBM_ERR_STATE, "initialise the state first");
@@ -1297,6 +1309,7 @@ lbm_status lbm_check(lbm_handle h) {
 lbm_status lbm_adjoint_step(lbm_handle h, int32_t body, const double dJ_dF[3], int64_t n_steps,
                             int64_t checkpoint_every, double* J, double* dJ_dq, double* dJ_dtau, double seconds[3]) {
   g_msg[0] = 0;
+  NvtxRange range("lbm_adjoint_step");
   if (!h || !dJ_dF || !J || !dJ_dtau || (h && h->n_links > 0 && !dJ_dq))
     return fail(LBM_ERR_INVALID_ARG, "null argument");
   if (!h->has_state) return fail(LBM_ERR_STATE, "initialise the state first");
@@ -1466,6 +1479,7 @@ lbm_status lbm_adjoint_step(lbm_handle h, int32_t body, const double dJ_dF[3], i
   for (int64_t c = nck - 1; c >= 0 && st == LBM_OK; --c) {
     const int64_t s0 = c * K, m = std::min(K, n_steps - s0);
     const bool last = c == nck - 1;
+    NvtxRange seg_range("adjoint segment");
     st = timed(t_rec, [&]() -> lbm_status {
       CUDA_TRY(cudaMemcpyAsync(segp, ckp + sb * c, sb, cudaMemcpyDeviceToDevice, h->stream));
       if (last) return enqueue_recompute(m);
@@ -1565,6 +1579,7 @@ lbm_status lbm_get_tuning(lbm_handle h, lbm_tuning* t) {
 
 lbm_status lbm_autotune(lbm_handle h, int32_t steps_per_trial, lbm_tuning* best, double* ms_per_step) {
   g_msg[0] = 0;
+  NvtxRange range("lbm_autotune");
   if (!h) return fail(LBM_ERR_INVALID_ARG, "null handle");
   if (steps_per_trial < 2) return fail(LBM_ERR_INVALID_ARG, "steps_per_trial must be >= 2");
   if (!h->has_state) return fail(LBM_ERR_STATE, "initialise the state first");

@@ -554,3 +554,11 @@ def test_translated_geometry_gives_translated_state(L, prec, stencil):
             lat.step(41)
             out.append(lat.distributions())
     assert np.array_equal(out[1][:, mp], out[0])
+
+
+def test_fp64_rate_probe(L):
+    """lbm_probe_fp64 measures the device's FP64 FMA rate (the FP64 roofline's
+    peak): a positive rate below the FP64 rate of any current GPU, from a
+    launch of positive duration."""
+    tflops, ms = L.lbm_probe_fp64()
+    assert 0.05 < tflops < 100.0 and ms > 0.0
