@@ -171,12 +171,13 @@ __device__ __forceinline__ void block_add_keyed(T v, int key, double* target) {
   }
 }
 
-// Resident 256-thread blocks per SM of the adjoint bulk kernel: 4 (64
-// registers, no spill) for FP32 D2Q9, 2 (up to 128 registers) for FP64 D2Q9
-// and FP32 D3Q19, 1 for FP64 D3Q19 (which spills at 128 registers).
+// Resident 256-thread blocks per SM of the adjoint bulk kernel: 5 (48
+// registers, a few spilled words) for FP32 D2Q9 — measured faster than 4 at
+// 64 registers on the channel batch (backward 0.667 -> 0.641 ms per step) —,
+// 2 (up to 128 registers) for FP64 D2Q9 and FP32 D3Q19, 1 for FP64 D3Q19.
 template <class L, class P>
 constexpr int adj_bulk_blocks_per_sm() {
-  return L::Q == 9 ? (P::shifted ? 4 : 2) : (P::shifted ? 2 : 1);
+  return L::Q == 9 ? (P::shifted ? 5 : 2) : (P::shifted ? 2 : 1);
 }
 
 template <class L, class P>
