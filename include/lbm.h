@@ -320,9 +320,10 @@ lbm_status lbm_query(lbm_handle h, lbm_info* info);
 /* Kernel timing for measurement.  While on, lbm_step launches the kernels
  * one by one (no CUDA graph) with a CUDA event pair around each launch on
  * the lattice's stream.  lbm_kernel_times synchronises and returns, per
- * kernel k (0 = links, 1 = open columns, 2 = bulk), the number of timed
- * launches and their summed duration in milliseconds since profiling was
- * switched on.  Errors: STATE, CUDA, OOM. */
+ * kernel k (0 = links, 1 = open columns, 2 = bulk, or the fused step kernel
+ * when the tuning's fused form runs, in which case slot 0 stays empty), the
+ * number of timed launches and their summed duration in milliseconds since
+ * profiling was switched on.  Errors: STATE, CUDA, OOM. */
 lbm_status lbm_set_profiling(lbm_handle h, int32_t on);
 lbm_status lbm_kernel_times(lbm_handle h, int64_t launches[3], double ms[3]);
 

@@ -135,6 +135,10 @@ struct lbm_lattice_s {
   // shifted storage: sum over each body's links of 2 w_i' rho0 e_i' (FP64),
   // the rest part of the momentum exchange that the link kernel leaves out
   std::vector<double> force_rest = std::vector<double>(3, 0.0);
+  // pinned host copy of the force slot read by lbm_force / lbm_forces (a
+  // device-to-host copy into pageable memory is staged by the driver)
+  double* force_host = nullptr;
+  size_t force_host_n = 0;
   raw_vec<int64_t> link_order;  // device link j = caller's link link_order[j]
   bool from_init = false;           // state is the one lbm_init_equilibrium made
   int cur = 0;      // buffer holding f+(t)
@@ -321,6 +325,19 @@ lbm_status build_graph(lbm_handle h, int parity, int steps, cudaGraphExec_t* out
   return LBM_OK;
 }
 
+// Pinned host buffer of at least n doubles for reading force slots.
+lbm_status force_host_buffer(lbm_handle h, size_t n, double** out) {
+  if (h->force_host_n < n) {
+    if (h->force_host) cudaFreeHost(h->force_host);
+    h->force_host = nullptr;
+    h->force_host_n = 0;
+    CUDA_TRY(cudaMallocHost(&h->force_host, sizeof(double) * n));
+    h->force_host_n = n;
+  }
+  *out = h->force_host;
+  return LBM_OK;
+}
+
 bool is_device_pointer(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -433,6 +450,7 @@ lbm_status lbm_destroy(lbm_handle h) {
   for (auto e : h->ev) cudaEventDestroy(e);
   release_geometry(h);
   release(h->force);
+  if (h->force_host) cudaFreeHost(h->force_host);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
   return LBM_OK;
@@ -1188,9 +1206,12 @@ lbm_status lbm_force(lbm_handle h, int32_t body, double F[3]) {
     return LBM_OK;
   }
   const double* slot = (const double*)h->force.p + 3 * (int64_t)h->nbody * ((h->step - 1) & 1) + 3 * body;
-  CUDA_TRY(cudaMemcpyAsync(F, slot, sizeof(double) * 3, cudaMemcpyDeviceToHost, h->stream));
+  double* pinned = nullptr;
+  lbm_status st = force_host_buffer(h, 3, &pinned);
+  if (st != LBM_OK) return st;
+  CUDA_TRY(cudaMemcpyAsync(pinned, slot, sizeof(double) * 3, cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
-  for (int a = 0; a < 3; ++a) F[a] += h->force_rest[3 * body + a];
+  for (int a = 0; a < 3; ++a) F[a] = pinned[a] + h->force_rest[3 * body + a];
   return LBM_OK;
 }
 
@@ -1201,9 +1222,12 @@ lbm_status lbm_forces(lbm_handle h, int32_t n, double* F) {
   if (!h->has_state || h->step == 0) return fail(LBM_ERR_STATE, "no step has run");
   const int m = std::min(n, h->nbody);
   const double* slot = (const double*)h->force.p + 3 * (int64_t)h->nbody * ((h->step - 1) & 1);
-  if (m > 0) CUDA_TRY(cudaMemcpyAsync(F, slot, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, h->stream));
+  double* pinned = nullptr;
+  lbm_status st = force_host_buffer(h, 3 * (size_t)std::max(m, 1), &pinned);
+  if (st != LBM_OK) return st;
+  if (m > 0) CUDA_TRY(cudaMemcpyAsync(pinned, slot, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
-  for (int64_t k = 0; k < 3 * (int64_t)m; ++k) F[k] += h->force_rest[k];
+  for (int64_t k = 0; k < 3 * (int64_t)m; ++k) F[k] = pinned[k] + h->force_rest[k];
   for (int64_t k = 3 * (int64_t)m; k < 3 * (int64_t)n; ++k) F[k] = 0.0;
   return LBM_OK;
 }

@@ -404,7 +404,7 @@ def _ptr_or_int(a):
 
 LBM_NOALLOC_MAX_LINKS = 16777216
 
-KERNEL_NAMES = ("k_links", "k_open", "k_bulk")
+KERNEL_NAMES = ("k_links", "k_open", "k_bulk or k_fused")
 
 
 class Lattice:
