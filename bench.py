@@ -266,7 +266,7 @@ def run_precision(lbm, torch, geo, precision, steps, warmup, dist, peak):
 # grows with the fluid node count, so a full launch moves this figure times
 # its fluid nodes.  k_bulk<D3Q19, F32S, 0, 256, 1>: 575.5 MB per launch for
 # 2.83M fluid nodes; k_fused<D3Q19, F32S, 0, 128>: 713.8 MB.
-TRAFFIC_PER_FLUID_NODE_PACK_FP32 = {"k_bulk": 203.5, "k_fused": 252.4}
+TRAFFIC_PER_FLUID_NODE_PACK_FP32 = {"k_bulk": 204.1, "k_fused": 253.0}
 
 
 def LINK_BYTES(s):
