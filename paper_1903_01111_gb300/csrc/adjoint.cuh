@@ -55,12 +55,12 @@ __device__ __forceinline__ typename P::T collide_adjoint(const typename P::T (&f
     jy += (T)L::cy(i) * f[i];
     jz += (T)L::cz(i) * f[i];
   }
-  const T rho = P::shifted ? (T)p.rho0 + r : r;
-  const T gx = (T)rx.g[0], gy = (T)rx.g[1], gz = (T)rx.g[2];
+  const T rho = P::shifted ? par<T>(p.rho0, p.rho0_f) + r : r;
+  const T gx = par<T>(rx.g[0], rx.g_f[0]), gy = par<T>(rx.g[1], rx.g_f[1]), gz = par<T>(rx.g[2], rx.g_f[2]);
   // the velocity as the forward collision forms it (one reciprocal of rho)
   const T ir = (T)1 / rho;
   const T ux = (jx + (T)0.5 * gx) * ir, uy = (jy + (T)0.5 * gy) * ir, uz = (jz + (T)0.5 * gz) * ir;
-  const T omega = (T)rx.omega;
+  const T omega = par<T>(rx.omega, rx.omega_f);
   const T uu15 = (T)1.5 * (ux * ux + uy * uy + uz * uz);
   const T ug = ux * gx + uy * gy + uz * gz;
   // The u-derivatives of the equilibrium and of the source, and f - feq +
@@ -126,7 +126,7 @@ __device__ __forceinline__ typename P::T collide_adjoint(const typename P::T (&f
     const T ex = (T)L::cx(j), ey = (T)L::cy(j), ez = (T)L::cz(j);
     mu[j] = ((T)1 - omega) * lam[j] + omega * A + (B0 * (ex - ux) + B1 * (ey - uy) + B2 * (ez - uz)) * ir;
   }
-  return dtau * (T)(rx.omega * rx.omega);
+  return dtau * par<T>(rx.omega * rx.omega, rx.omega2_f);
 }
 
 // Adds v to target[key] over the block (key < 0: nothing to add): a warp
@@ -215,9 +215,10 @@ __global__ void __launch_bounds__(256, (adj_bulk_blocks_per_sm<L, P>())) k_adj_b
           jy += (T)L::cy(i) * v;
           jz += (T)L::cz(i) * v;
         }
-        const T rho = P::shifted ? (T)p.rho0 + r : r;
-        mom[k] = Mom4<T>{r, (jx - (T)(0.5 * rx.g[0])) / rho, (jy - (T)(0.5 * rx.g[1])) / rho,
-                         L::D == 3 ? (jz - (T)(0.5 * rx.g[2])) / rho : (T)0};
+        const T rho = P::shifted ? par<T>(p.rho0, p.rho0_f) + r : r;
+        mom[k] = Mom4<T>{r, (jx - par<T>(0.5 * rx.g[0], rx.hg_f[0])) / rho,
+                         (jy - par<T>(0.5 * rx.g[1], rx.hg_f[1])) / rho,
+                         L::D == 3 ? (jz - par<T>(0.5 * rx.g[2], rx.hg_f[2])) / rho : (T)0};
       }
       dt = collide_adjoint<L, P>(f, lam, mu, p, rx);
 #pragma unroll
@@ -320,7 +321,8 @@ __device__ __forceinline__ void adj_link(int64_t k, const DirTable<typename P::T
     om += c;
     atomic_add_real(lam + (size_t)ip * S + kf, c);
   }
-  const T wall = -(T)6 * w * (T)p.rho0 * (ex * uw0 + ey * uw1 + ez * uw2);
+  const T rho0 = par<T>(p.rho0, p.rho0_f);
+  const T wall = -(T)6 * w * rho0 * (ex * uw0 + ey * uw1 + ez * uw2);
   const T fpf = f[(size_t)ip * S + kf];
   const T two_q = (T)2 * q;
   double dLdq = 0.0;
@@ -352,11 +354,11 @@ __device__ __forceinline__ void adj_link(int64_t k, const DirTable<typename P::T
   } else {
     const T fpff = f[(size_t)ip * S + kff];
     const Mom4<T> mf = mom[kf], mff = mom[kff];
-    const T rhof = P::shifted ? (T)p.rho0 + mf.r : mf.r;
-    const T rhoff = P::shifted ? (T)p.rho0 + mff.r : mff.r;
+    const T rhof = P::shifted ? rho0 + mf.r : mf.r;
+    const T rhoff = P::shifted ? rho0 + mff.r : mff.r;
     const bool local = p.vibb_local_rho && q > (T)0.5;
     const T rd = local ? mf.r : two_q * mf.r + ((T)1 - two_q) * mff.r;
-    const T rhod = P::shifted ? (T)p.rho0 + rd : rd;
+    const T rhod = P::shifted ? rho0 + rd : rd;
     const T euf = ex * mf.ux + ey * mf.uy + ez * mf.uz;
     const T euff = ex * mff.ux + ey * mff.uy + ez * mff.uz;
     const T polyf = (T)3 * euf + (T)4.5 * euf * euf - (T)1.5 * (mf.ux * mf.ux + mf.uy * mf.uy + mf.uz * mf.uz);

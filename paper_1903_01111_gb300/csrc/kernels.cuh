@@ -83,13 +83,25 @@ struct DomPar {
   double g[3];
   double inlet_umax, inlet_y0, inlet_y1;  // inlet rows relative to lo
   int32_t lo, has_force;  // first row (y in 2-D, z in 3-D) of the domain
+  float omega_f, fpre3_f, g_f[3], hg_f[3], omega2_f;  // float copies, as in Params
 };
 
 // Collision parameters of one node, from Params or from its domain.
 struct Relax {
   double omega, fpre3, g[3];
   int has_force;
+  float omega_f, fpre3_f, g_f[3], hg_f[3], omega2_f;
 };
+
+// A run parameter in the storage precision: the double, or its float copy
+// rounded on the host (the same value as a conversion on the device).
+template <class T>
+__host__ __device__ __forceinline__ T par(double d, float f) {
+  if constexpr (sizeof(T) == sizeof(float))
+    return f;
+  else
+    return d;
+}
 
 // Neighbour-row slots by source-row offset (dy, dz).  D2Q9: (1,0), (-1,0).
 // D3Q19: (1,0), (-1,0), (0,1), (0,-1), (1,1), (-1,-1), (1,-1), (-1,1).
@@ -113,12 +125,16 @@ struct Layout {
 };
 
 __device__ __forceinline__ Relax relax_params(const Params& p) {
-  return Relax{p.omega, p.fpre3, {p.g[0], p.g[1], p.g[2]}, p.has_force};
+  return Relax{p.omega,   p.fpre3,   {p.g[0], p.g[1], p.g[2]},          p.has_force,
+               p.omega_f, p.fpre3_f, {p.g_f[0], p.g_f[1], p.g_f[2]}, {p.hg_f[0], p.hg_f[1], p.hg_f[2]},
+               p.omega2_f};
 }
 
 __device__ __forceinline__ Relax relax_domain(const DomPar* __restrict__ dp, int d) {
   const DomPar& q = dp[d];
-  return Relax{q.omega, q.fpre3, {q.g[0], q.g[1], q.g[2]}, q.has_force};
+  return Relax{q.omega,   q.fpre3,   {q.g[0], q.g[1], q.g[2]},          q.has_force,
+               q.omega_f, q.fpre3_f, {q.g_f[0], q.g_f[1], q.g_f[2]}, {q.hg_f[0], q.hg_f[1], q.hg_f[2]},
+               q.omega2_f};
 }
 
 // Relaxation of a node of fluid run `run` (any kernel but the bulk one,
@@ -194,13 +210,13 @@ __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Pa
       if (L::cz(i) < 0) jz -= f[i];
     }
   }
-  const T rho = P::shifted ? (T)p.rho0 + r : r;
-  const T gx = (T)rx.g[0], gy = (T)rx.g[1], gz = (T)rx.g[2];
+  const T rho = P::shifted ? par<T>(p.rho0, p.rho0_f) + r : r;
+  const T gx = par<T>(rx.g[0], rx.g_f[0]), gy = par<T>(rx.g[1], rx.g_f[1]), gz = par<T>(rx.g[2], rx.g_f[2]);
   const T inv = (T)1 / rho;
   // Guo forcing: velocity shifted by half the body force
   const T ux = (jx + (T)0.5 * gx) * inv, uy = (jy + (T)0.5 * gy) * inv, uz = (jz + (T)0.5 * gz) * inv;
   if (cache && keep) mom[n_] = Mom4<T>{r, ux, uy, L::D == 3 ? uz : (T)0};
-  const T omega = (T)rx.omega;
+  const T omega = par<T>(rx.omega, rx.omega_f);
   const T uu15 = (T)1.5 * (ux * ux + uy * uy + uz * uz);
   if constexpr (L::Q == 9) {
     if (p.collision == 1) {
@@ -247,7 +263,7 @@ __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Pa
   }
   // BGK with the Guo source (1 - 1/(2 tau)) w_i [3 (e_i - u).g + 9 (e_i.u)(e_i.g)]
   //   = 3 (1 - 1/(2 tau)) w_i [(e_i.g)(1 + 3 e_i.u) - u.g].
-  const T fpre3 = (T)rx.fpre3;
+  const T fpre3 = par<T>(rx.fpre3, rx.fpre3_f);
   const T ug = ux * gx + uy * gy + uz * gz;
   if constexpr (P::shifted) {
     // Shifted FP32 storage: each direction keeps its own equilibrium
@@ -590,10 +606,11 @@ __device__ __forceinline__ typename P::T link_value(int rule, typename P::T q, t
                                                     typename P::T ey, typename P::T ez, typename P::T fpf,
                                                     typename P::T fpff, typename P::T fpi, const Mom4<typename P::T>& mf,
                                                     const Mom4<typename P::T>& mff, typename P::T uw0,
-                                                    typename P::T uw1, typename P::T uw2, double rho0, int local_rho) {
+                                                    typename P::T uw1, typename P::T uw2, typename P::T rho0,
+                                                    int local_rho) {
   using T = typename P::T;
   // 6 w_i' rho0 (e_i . u_w) with e_i = -e_i'
-  const T wall = -(T)6 * w * (T)rho0 * (ex * uw0 + ey * uw1 + ez * uw2);
+  const T wall = -(T)6 * w * rho0 * (ex * uw0 + ey * uw1 + ez * uw2);
   const T two_q = (T)2 * q;
   if (rule == 0) return fpf + wall;
   if (rule == 1) {
@@ -608,11 +625,11 @@ __device__ __forceinline__ typename P::T link_value(int rule, typename P::T q, t
     const T i1q = (T)1 / ((T)1 + q);
     return (q * fpf + ((T)1 - q) * fpff + wall) * i1q + q * i1q * fpi;
   }
-  const T rhof = P::shifted ? (T)rho0 + mf.r : mf.r;
-  const T rhoff = P::shifted ? (T)rho0 + mff.r : mff.r;
+  const T rhof = P::shifted ? rho0 + mf.r : mf.r;
+  const T rhoff = P::shifted ? rho0 + mff.r : mff.r;
   // Eq. (rhod) in storage form; optionally rho_d = rho_f when q > 1/2
   const T rd = (local_rho && q > (T)0.5) ? mf.r : two_q * mf.r + ((T)1 - two_q) * mff.r;
-  const T rhod = P::shifted ? (T)rho0 + rd : rd;
+  const T rhod = P::shifted ? rho0 + rd : rd;
   const T neq_f = fpf - eq_dir<P>(w, ex, ey, ez, mf.r, rhof, mf.ux, mf.uy, mf.uz);
   const T neq_ff = fpff - eq_dir<P>(w, ex, ey, ez, mff.r, rhoff, mff.ux, mff.uy, mff.uz);
   // fneq at d, each term rescaled by its density ratio
@@ -686,7 +703,8 @@ __device__ __forceinline__ typename P::T eval_link(const DirTable<typename P::T,
     fpff = f[(size_t)ip * N + ff];
     fpi = f[(size_t)i * N + node];
   }
-  return link_value<P>(rule, q, w, ex, ey, ez, fpf, fpff, fpi, mf, mff, uw0, uw1, uw2, p.rho0, p.vibb_local_rho);
+  return link_value<P>(rule, q, w, ex, ey, ez, fpf, fpff, fpi, mf, mff, uw0, uw1, uw2, par<T>(p.rho0, p.rho0_f),
+                       p.vibb_local_rho);
 }
 
 // One thread per link.  recs: storage indices and metadata; qv: q in
@@ -1014,7 +1032,7 @@ __global__ void k_open(typename P::T* __restrict__ f, const Mom4<typename P::T>*
     if (k0 >= 0 && (lay.word[k0] & W_OPEN)) {
       const uint32_t k1 = (uint32_t)k0 + 1;
       const Mom4<T> m1 = mom[k1];
-      const T rho1 = P::shifted ? (T)p.rho0 + m1.r : m1.r;
+      const T rho1 = P::shifted ? par<T>(p.rho0, p.rho0_f) + m1.r : m1.r;
       T v[L::Q];
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) v[i] = f[i * S + k1];
@@ -1118,9 +1136,9 @@ __global__ void k_refresh(const typename P::T* __restrict__ f, Layout lay, Mom4<
     jy += (T)L::cy(i) * v;
     jz += (T)L::cz(i) * v;
   }
-  const T rho = P::shifted ? (T)p.rho0 + r : r;
-  mom[k] = Mom4<T>{r, (jx - (T)(0.5 * rx.g[0])) / rho, (jy - (T)(0.5 * rx.g[1])) / rho,
-                   L::D == 3 ? (jz - (T)(0.5 * rx.g[2])) / rho : (T)0};
+  const T rho = P::shifted ? par<T>(p.rho0, p.rho0_f) + r : r;
+  mom[k] = Mom4<T>{r, (jx - par<T>(0.5 * rx.g[0], rx.hg_f[0])) / rho, (jy - par<T>(0.5 * rx.g[1], rx.hg_f[1])) / rho,
+                   L::D == 3 ? (jz - par<T>(0.5 * rx.g[2], rx.hg_f[2])) / rho : (T)0};
 }
 
 template <class L>

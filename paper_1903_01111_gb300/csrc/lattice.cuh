@@ -78,7 +78,23 @@ struct Params {
   int vibb_local_rho;   // rho_d = rho_f when q > 1/2
   int periodic[3];
   int nbody;            // force accumulators per slot (max body id + 1, >= 1)
+  // rho0, omega, fpre3, g, g/2 and omega^2 rounded once to float: the FP32
+  // kernels read these copies (set by round_params), because a double ->
+  // float conversion on every node or link costs FP64-pipe time
+  float rho0_f, omega_f, fpre3_f, g_f[3], hg_f[3], omega2_f;
 };
+
+// Fills the float copies of Params from its doubles (after any change).
+inline void round_params(Params& p) {
+  p.rho0_f = (float)p.rho0;
+  p.omega_f = (float)p.omega;
+  p.fpre3_f = (float)p.fpre3;
+  p.omega2_f = (float)(p.omega * p.omega);
+  for (int a = 0; a < 3; ++a) {
+    p.g_f[a] = (float)p.g[a];
+    p.hg_f[a] = (float)(0.5 * p.g[a]);
+  }
+}
 
 // Error message shared by every translation unit of the library (set by a
 // failing entry point, read through lbm_last_error).

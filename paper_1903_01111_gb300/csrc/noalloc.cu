@@ -204,6 +204,7 @@ extern "C" lbm_status lbm_force_noalloc(const lbm_config* cfg, const double* f_p
   p.inlet = c.inlet ? 1 : 0;
   p.outlet = c.outlet ? 1 : 0;
   p.vibb_local_rho = c.vibb_density == LBM_VIBB_RHO_LOCAL ? 1 : 0;
+  lbm::round_params(p);
   cudaStream_t s = (cudaStream_t)c.cuda_stream;
   const int nb = (int)((n_links + kBlock - 1) / kBlock);
   if (nb > 0) {
