@@ -84,6 +84,7 @@ struct DomPar {
   double inlet_umax, inlet_y0, inlet_y1;  // inlet rows relative to lo
   int32_t lo, has_force;  // first row (y in 2-D, z in 3-D) of the domain
   float omega_f, fpre3_f, g_f[3], hg_f[3], omega2_f;  // float copies, as in Params
+  Folded kc;              // collision constants, as in Params
 };
 
 // Collision parameters of one node, from Params or from its domain.
@@ -173,8 +174,30 @@ __device__ __forceinline__ int src_coord(int c, int x, int xm, int xp) { return 
 // or open slot in the bulk pass): the same instructions store zeros and the
 // moment cache is not written, so that a warp mixing fluid and ghost slots
 // issues one store per direction instead of two divergent store sequences.
+// Weight class of direction i: 0 rest, 1 |e| = 1, 2 diagonal.
+template <class L>
+__host__ __device__ constexpr int weight_class(int i) {
+  return i == 0 ? 0 : (L::w(i) == L::w(1) ? 1 : 2);
+}
+
+// The node's collision constants folded on the host: the lattice's (Params)
+// or its domain's (DomPar), both filled by fold.
+template <bool MULTI>
+__device__ __forceinline__ const Folded& folded_of(const Params& p, const Layout& lay, int dom) {
+  if constexpr (MULTI)
+    return lay.dom[dom].kc;
+  else
+    return p.kc;
+}
+
+// Collision and store of one node: moments of f, Guo-forced BGK (or D2Q9
+// MRT) with the run parameters rx and the folded constants kc, the node's
+// moment cache entry when flagged.
+#define LBM_K(name) par<T>(kc.name, kc.name##_f)
+#define LBM_KI(name, i) par<T>(kc.name[i], kc.name##_f[i])
 template <class L, class P>
 __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Params& p, const Relax& rx,
+                                              const Folded& kc,
                                               typename P::T* __restrict__ fout, size_t S, uint32_t n_,
                                               Mom4<typename P::T>* __restrict__ mom, bool cache, bool keep = true) {
   using T = typename P::T;
@@ -214,7 +237,8 @@ __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Pa
   const T gx = par<T>(rx.g[0], rx.g_f[0]), gy = par<T>(rx.g[1], rx.g_f[1]), gz = par<T>(rx.g[2], rx.g_f[2]);
   const T inv = (T)1 / rho;
   // Guo forcing: velocity shifted by half the body force
-  const T ux = (jx + (T)0.5 * gx) * inv, uy = (jy + (T)0.5 * gy) * inv, uz = (jz + (T)0.5 * gz) * inv;
+  const T hx = LBM_KI(hg, 0), hy = LBM_KI(hg, 1), hz = LBM_KI(hg, 2);
+  const T ux = (jx + hx) * inv, uy = (jy + hy) * inv, uz = (jz + hz) * inv;
   if (cache && keep) mom[n_] = Mom4<T>{r, ux, uy, L::D == 3 ? uz : (T)0};
   const T omega = par<T>(rx.omega, rx.omega_f);
   const T uu15 = (T)1.5 * (ux * ux + uy * uy + uz * uz);
@@ -263,18 +287,22 @@ __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Pa
   }
   // BGK with the Guo source (1 - 1/(2 tau)) w_i [3 (e_i - u).g + 9 (e_i.u)(e_i.g)]
   //   = 3 (1 - 1/(2 tau)) w_i [(e_i.g)(1 + 3 e_i.u) - u.g].
-  const T fpre3 = par<T>(rx.fpre3, rx.fpre3_f);
-  const T ug = ux * gx + uy * gy + uz * gz;
+  const T ug = rx.has_force ? ux * gx + uy * gy + uz * gz : (T)0;
   if constexpr (P::shifted) {
     // Shifted FP32 storage: each direction keeps its own equilibrium
     // feq_i = w (r + rho poly_i) and relaxes in the difference form
     // f + omega (feq - f), so that rounding falls on the small
     // non-equilibrium part; opposite directions (i, j = opp(i), e_j = -e_i)
     // share e.u, the symmetric part 4.5 (e.u)^2 - 1.5 u.u of the polynomial
-    // and the two parts of the source, Sc +- So (Sc, So as in the FP64 form
-    // below).  (Relaxing the pair's symmetric and antisymmetric parts
-    // separately, as FP64 does, measured 5x larger FP32 errors in drag and in
-    // the adjoint's dJ/dtau.)
+    // and the two parts of the source, Sc +- So with Sc = kt_i (e_i.u) -
+    // kf_c (u.g) and So = ke_i from the folded constants.  (Relaxing the
+    // pair's symmetric and antisymmetric parts separately, as FP64 does,
+    // measured 5x larger FP32 errors in drag and in the adjoint's dJ/dtau.)
+    T sc[3] = {0, 0, 0};
+    if (rx.has_force) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) sc[c] = LBM_KI(kf, c) * ug;
+    }
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
       const int j = L::opp(i);
@@ -286,10 +314,8 @@ __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Pa
       T oi = f[i] + omega * (feqi - f[i]);
       T Sc = 0, So = 0;
       if (rx.has_force) {
-        const T eg = (T)L::cx(i) * gx + (T)L::cy(i) * gy + (T)L::cz(i) * gz;
-        const T fw = fpre3 * w;
-        Sc = fw * ((T)3 * eg * eu - ug);
-        So = fw * eg;
+        Sc = LBM_KI(kt, i) * eu - sc[weight_class<L>(i)];
+        So = LBM_KI(ke, i);
         oi += Sc + So;
       }
       fout[(size_t)i * S + n_] = keep ? oi : (T)0;
@@ -301,51 +327,45 @@ __device__ __forceinline__ void collide_store(typename P::T (&f)[L::Q], const Pa
       }
     }
   } else {
-    // FP64 (bound by the FP64 pipe): per pair of opposite directions
-    // (i, j = opp(i)), e_j = -e_i turns the equilibria into A +- B and the
-    // sources into Sc +- So with
-    //   A  = w rho (1 + 4.5 (e_i.u)^2 - 1.5 u.u),   B = 3 w rho (e_i.u),
-    //   Sc = fpre3 w (3 (e_i.g)(e_i.u) - u.g),     So = fpre3 w (e_i.g),
-    // so that f+_i,j = (1 - omega) f_i,j + (omega A + Sc) +- (omega B + So).
-    // The factors that depend only on the weight class (omega w rho and its
-    // products, fpre3 w and its products) are formed once per node, so that
-    // a pair costs two FMAs and a multiply for omega A and omega B, an FMA
-    // and a multiply for the source, two adds and two FMAs for the outputs.
-    const T om1 = (T)1 - omega;
+    // FP64 (bound by the FP64 pipe, where every add, multiply or FMA takes
+    // one issue slot): per pair of opposite directions (i, j = opp(i)),
+    // e_j = -e_i turns the equilibria into A +- B and the sources into
+    // Sc +- So, so that with the folded constants
+    //   a_c = ko_c rho (1 - 1.5 u.u) - kf_c (u.g),  h_c = kh_c rho,  b_c = kb_c rho,
+    //   P = (h_c eu + kt_i) eu + a_c = omega A + Sc,  M = b_c eu + ke_i = omega B + So,
+    //   f+_i,j = (1 - omega) f_i,j + (P +- M):
+    // the source's symmetric part joins the FMAs of the equilibrium's, its
+    // antisymmetric part the FMA of M, and a pair costs an FMA and a multiply
+    // for P, an FMA for M and two adds and two FMAs for the outputs.
+    const T om1 = LBM_K(om1);
     const T c0 = (T)1 - uu15;
     {
-      const T w = (T)L::w(0);
-      T out = om1 * f[0] + omega * ((w * rho) * c0);
-      if (rx.has_force) out -= fpre3 * w * ug;
+      const T out = om1 * f[0] + ((LBM_KI(ko, 0) * rho) * c0 - LBM_KI(kf, 0) * ug);
       fout[n_] = keep ? out : (T)0;
     }
-    // per weight class k (1: |e| = 1, 2: |e| = sqrt 2): omega w rho and the
-    // products the pairs use
-    const T owr1 = omega * ((T)L::w(1) * rho), owr2 = omega * ((T)L::w(L::Q == 9 ? 5 : 7) * rho);
-    const T a1 = owr1 * c0, a2 = owr2 * c0;                       // omega A at e.u = 0
-    const T h1 = (T)4.5 * owr1, h2 = (T)4.5 * owr2;               // coefficient of (e.u)^2
-    const T b1 = (T)3 * owr1, b2 = (T)3 * owr2;                   // omega B / (e.u)
-    const T fw1 = fpre3 * (T)L::w(1), fw2 = fpre3 * (T)L::w(L::Q == 9 ? 5 : 7);
-    const T s1 = fw1 * ug, s2 = fw2 * ug;                         // fpre3 w (u.g)
-    const T t1 = (T)3 * fw1, t2 = (T)3 * fw2;
+    T a[3], h[3], b[3];
+#pragma unroll
+    for (int c = 1; c < 3; ++c) {
+      a[c] = (LBM_KI(ko, c) * rho) * c0 - LBM_KI(kf, c) * ug;
+      h[c] = LBM_KI(kh, c) * rho;
+      b[c] = LBM_KI(kb, c) * rho;
+    }
 #pragma unroll
     for (int i = 1; i < L::Q; ++i) {
       const int j = L::opp(i);
       if (j < i) continue;
-      const bool diag = L::w(i) < L::w(1);
+      const int c = weight_class<L>(i);
       const T eu = (T)L::cx(i) * ux + (T)L::cy(i) * uy + (T)L::cz(i) * uz;
-      T Pv = diag ? (h2 * eu) * eu + a2 : (h1 * eu) * eu + a1;
-      T Mv = (diag ? b2 : b1) * eu;
-      if (rx.has_force) {
-        const T eg = (T)L::cx(i) * gx + (T)L::cy(i) * gy + (T)L::cz(i) * gz;
-        Pv += (diag ? t2 : t1) * eg * eu - (diag ? s2 : s1);
-        Mv += (diag ? fw2 : fw1) * eg;
-      }
+      const T Pv = (h[c] * eu + LBM_KI(kt, i)) * eu + a[c];
+      const T Mv = b[c] * eu + LBM_KI(ke, i);
       fout[(size_t)i * S + n_] = keep ? om1 * f[i] + (Pv + Mv) : (T)0;
       fout[(size_t)j * S + n_] = keep ? om1 * f[j] + (Pv - Mv) : (T)0;
     }
   }
 }
+
+#undef LBM_K
+#undef LBM_KI
 
 // Storage indices of the pull sources x - e_i of fluid node k of run `run`.
 template <class L>
@@ -491,7 +511,8 @@ __global__ void __launch_bounds__(BT, (bulk_blocks_per_sm<L, P, BT, NPT>())) k_b
       for (int i = 0; i < L::Q; ++i) f[j][i] = P::shifted ? (T)0 : (T)L::w(i);
     }
     const Relax rx = MULTI ? relax_domain(lay.dom, dom[j]) : relax_params(p);
-    collide_store<L, P>(f[j], p, rx, fout, S, k[j], mom, (w[j] & W_CACHE) != 0, fl);
+    collide_store<L, P>(f[j], p, rx, folded_of<MULTI>(p, lay, dom[j]), fout, S, k[j], mom, (w[j] & W_CACHE) != 0,
+                        fl);
   }
 }
 
@@ -565,7 +586,7 @@ __global__ void __launch_bounds__(BT, (bulk_seq_blocks_per_sm<P, BT>())) k_bulk_
       for (int i = 0; i < L::Q; ++i) fout[(size_t)i * S + k] = (T)0;
     } else {
       const Relax rx = MULTI ? relax_domain(lay.dom, run.dom) : relax_params(p);
-      collide_store<L, P>(f, p, rx, fout, S, k, mom, (w & W_CACHE) != 0);
+      collide_store<L, P>(f, p, rx, folded_of<MULTI>(p, lay, run.dom), fout, S, k, mom, (w & W_CACHE) != 0);
     }
     // the next node's run record, loaded before its pulls are needed
     w = w2;
@@ -990,7 +1011,7 @@ __global__ void __launch_bounds__(BT, (fused_blocks_per_sm<L, P, BT>())) k_fused
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) f[i] = col[i][lane];
     const Relax rx = MULTI ? relax_domain(lay.dom, dom) : relax_params(p);
-    collide_store<L, P>(f, p, rx, fout, S, k, mom_out, (w & W_CACHE) != 0, fluid);
+    collide_store<L, P>(f, p, rx, folded_of<MULTI>(p, lay, dom), fout, S, k, mom_out, (w & W_CACHE) != 0, fluid);
   }
 }
 
@@ -1086,7 +1107,11 @@ __global__ void k_init(typename P::T* __restrict__ f, Mom4<typename P::T>* __res
     const double poly = 3.0 * eu + 4.5 * eu * eu - 1.5 * (ux * ux + uy * uy + uz * uz);
     fl[i] = P::shifted ? (T)(L::w(i) * ((rho - p.rho0) + rho * poly)) : (T)(L::w(i) * rho * (1.0 + poly));
   }
-  collide_store<L, P>(fl, p, rx, f, S, (uint32_t)k, mom, (w & W_CACHE) != 0);
+  // one inlined collision for both cases (the lattice's constants or the
+  // domain's), so that a domain's initial state has the same bits alone and
+  // in a batch
+  const Folded* kc = lay.ndom > 1 ? &lay.dom[lay.runs[w & W_RUN].dom].kc : &p.kc;
+  collide_store<L, P>(fl, p, rx, *kc, f, S, (uint32_t)k, mom, (w & W_CACHE) != 0);
 }
 
 // rho = sum f+, u = (sum f+ e - g/2)/rho of the post-collision state (the

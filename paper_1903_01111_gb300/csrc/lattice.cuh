@@ -63,6 +63,49 @@ struct D3Q19 {
   __host__ __device__ static constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
 };
 
+// Collision constants folded on the host from omega, fpre3 and g for a
+// stencil's weights, the same for every node of a domain: per weight class
+// c (0 rest, 1 |e| = 1, 2 diagonal) ko = omega w_c, kh = 4.5 omega w_c,
+// kb = 3 omega w_c, kf = fpre3 w_c; per direction kt = 3 fpre3 w_i (e_i.g),
+// ke = fpre3 w_i (e_i.g); om1 = 1 - omega; hg = g/2.  The float copies
+// serve the FP32 kernels.  One function (fold) fills them for a lattice and
+// for each domain of a batch, so that a domain collides with the same bits
+// alone and in a batch.
+struct Folded {
+  double ko[3], kh[3], kb[3], kf[3], kt[19], ke[19], om1, hg[3];
+  float ko_f[3], kh_f[3], kb_f[3], kf_f[3], kt_f[19], ke_f[19], om1_f, hg_f[3];
+};
+
+template <class L>
+inline void fold(Folded& k, double omega, double fpre3, const double g[3]) {
+  const double wc[3] = {L::w(0), L::w(1), L::w(L::Q == 9 ? 5 : 7)};
+  for (int c = 0; c < 3; ++c) {
+    k.ko[c] = omega * wc[c];
+    k.kh[c] = 4.5 * omega * wc[c];
+    k.kb[c] = 3.0 * omega * wc[c];
+    k.kf[c] = fpre3 * wc[c];
+    k.ko_f[c] = (float)k.ko[c];
+    k.kh_f[c] = (float)k.kh[c];
+    k.kb_f[c] = (float)k.kb[c];
+    k.kf_f[c] = (float)k.kf[c];
+  }
+  for (int i = 0; i < 19; ++i) {
+    // e_i.g with integer e_i: every product exact, whatever the contraction
+    const double eg = i < L::Q ? L::cx(i) * g[0] + L::cy(i) * g[1] + L::cz(i) * g[2] : 0.0;
+    const double fw = i < L::Q ? fpre3 * L::w(i) : 0.0;
+    k.kt[i] = 3.0 * fw * eg;
+    k.ke[i] = fw * eg;
+    k.kt_f[i] = (float)k.kt[i];
+    k.ke_f[i] = (float)k.ke[i];
+  }
+  k.om1 = 1.0 - omega;
+  k.om1_f = (float)k.om1;
+  for (int a = 0; a < 3; ++a) {
+    k.hg[a] = 0.5 * g[a];
+    k.hg_f[a] = (float)k.hg[a];
+  }
+}
+
 // Run parameters handed to every kernel by value.
 struct Params {
   int nx, ny, nz;
@@ -82,6 +125,7 @@ struct Params {
   // kernels read these copies (set by round_params), because a double ->
   // float conversion on every node or link costs FP64-pipe time
   float rho0_f, omega_f, fpre3_f, g_f[3], hg_f[3], omega2_f;
+  Folded kc;            // collision constants (fold_params)
 };
 
 // Fills the float copies of Params from its doubles (after any change).
@@ -94,6 +138,14 @@ inline void round_params(Params& p) {
     p.g_f[a] = (float)p.g[a];
     p.hg_f[a] = (float)(0.5 * p.g[a]);
   }
+}
+
+// Fills the folded collision constants and every float copy of Params for
+// stencil L (after any change of omega, fpre3 or g).
+template <class L>
+inline void fold_params(Params& p) {
+  fold<L>(p.kc, p.omega, p.fpre3, p.g);
+  round_params(p);
 }
 
 // Error message shared by every translation unit of the library (set by a

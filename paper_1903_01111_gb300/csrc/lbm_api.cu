@@ -406,7 +406,10 @@ lbm_status lbm_create_lattice(const lbm_config* cfg, lbm_handle* out) {
   p.fpre3 = 3.0 * (1.0 - 0.5 / c.tau);
   for (int a = 0; a < 3; ++a) p.g[a] = (a < h->D) ? c.g[a] : 0.0;
   p.has_force = (p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0);
-  round_params(p);
+  if (h->Q == 9)
+    fold_params<D2Q9>(p);
+  else
+    fold_params<D3Q19>(p);
   p.collision = c.collision;
   p.inlet = c.inlet ? 1 : 0;
   p.outlet = c.outlet ? 1 : 0;
@@ -1002,6 +1005,10 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
       dp[k].fpre3 = 3.0 * (1.0 - 0.5 / q.tau);
       for (int a = 0; a < 3; ++a) dp[k].g[a] = a < D ? q.g[a] : 0.0;
       dp[k].has_force = (dp[k].g[0] != 0.0 || dp[k].g[1] != 0.0 || dp[k].g[2] != 0.0) ? 1 : 0;
+      if (Q == 9)
+        fold<D2Q9>(dp[k].kc, dp[k].omega, dp[k].fpre3, dp[k].g);
+      else
+        fold<D3Q19>(dp[k].kc, dp[k].omega, dp[k].fpre3, dp[k].g);
       dp[k].omega_f = (float)dp[k].omega;
       dp[k].fpre3_f = (float)dp[k].fpre3;
       dp[k].omega2_f = (float)(dp[k].omega * dp[k].omega);
@@ -1066,7 +1073,10 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
   p.fpre3 = 3.0 * (1.0 - 0.5 / d0.tau);
   for (int a = 0; a < 3; ++a) p.g[a] = a < D ? d0.g[a] : 0.0;
   p.has_force = (p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0);
-  round_params(p);
+  if (h->Q == 9)
+    fold_params<D2Q9>(p);
+  else
+    fold_params<D3Q19>(p);
   p.inlet_umax = d0.inlet_umax;
   p.inlet_y0 = d0.inlet_y0;
   p.inlet_y1 = d0.inlet_y1;
