@@ -653,21 +653,29 @@ __device__ __forceinline__ typename P::T link_value(int rule, typename P::T q, t
   const T rhod = P::shifted ? rho0 + rd : rd;
   const T neq_f = fpf - eq_dir<P>(w, ex, ey, ez, mf.r, rhof, mf.ux, mf.uy, mf.uz);
   const T neq_ff = fpff - eq_dir<P>(w, ex, ey, ez, mff.r, rhoff, mff.ux, mff.uy, mff.uz);
+  // every quotient of the rule from one reciprocal, r = 1/(rho_f rho_ff D)
+  // with D = q (1 + q) (q > 1/2) or 1 + q: 1/(rho_f rho_ff) = D r,
+  // 1/D = rho_f rho_ff r, 1/(1 + q) and 1/q from 1/D
+  const bool far = q > (T)0.5;
+  const T D = far ? q * ((T)1 + q) : (T)1 + q;
+  const T rr = rhof * rhoff;
+  const T r = (T)1 / (rr * D);
+  const T iD = rr * r;
+  const T i1q = far ? q * iD : iD;
   // fneq at d, each term rescaled by its density ratio
-  const T nd = rhod * (two_q * neq_f / rhof + ((T)1 - two_q) * neq_ff / rhoff);
+  const T nd = rhod * (two_q * neq_f * rhoff + ((T)1 - two_q) * neq_ff * rhof) * (D * r);
   // u*_d (piecewise linear), u**_d (between x_ff and the wall), weighted 1/3 : 2/3
   T af, aff, aw;
-  if (q <= (T)0.5) {
+  if (!far) {
     af = two_q;
     aff = (T)1 - two_q;
     aw = 0;
   } else {
-    const T iq = (T)1 / q;
+    const T iq = ((T)1 + q) * iD;
     af = ((T)1 - q) * iq;
     aff = 0;
     aw = (two_q - (T)1) * iq;
   }
-  const T i1q = (T)1 / ((T)1 + q);
   const T bff = ((T)1 - q) * i1q, bw = two_q * i1q;
   const T third = (T)(1.0 / 3.0), two_thirds = (T)(2.0 / 3.0);
   const T cf = third * af, cff = third * aff + two_thirds * bff, cw = third * aw + two_thirds * bw;
