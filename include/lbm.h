@@ -169,7 +169,8 @@ typedef struct {
  *                 then (128,1) with each thread walking 4 or 8 nodes in
  *                 sequence over the grid, the next node's addressing loaded
  *                 while the current node's pulls are in flight;
- *                 3..7 are D2Q9 only.  -1 on input: the stencil's default.
+ *                 3..7 are D2Q9 only.  -1 on input: the stencil's default,
+ *                 3 for D2Q9 and 1 for D3Q19 (the shape a new lattice has).
  *  link_threads   64, 128 or 256 threads per block of the link kernel.
  *  graph_steps    time steps per CUDA graph replayed by lbm_step (even,
  *                 2..64).
@@ -261,6 +262,19 @@ lbm_status lbm_force(lbm_handle h, int32_t body, double F[3]);
 /* Forces on bodies 0..n-1 as lbm_force, in one copy: F[b*3 + a] (host);
  * bodies without links give 0.  Errors: STATE, INVALID_ARG, CUDA. */
 lbm_status lbm_forces(lbm_handle h, int32_t n, double* F);
+
+/* n >= 0 steps as lbm_step, with the force on body `body` after each of
+ * them (lbm_force of that step) written to F[3*k + a], k = 0 .. n-1: a
+ * monitoring loop without a host synchronisation per step.  Each step's
+ * force is copied behind that step on the lattice's stream into a pinned
+ * staging buffer the lattice owns (grown to at most 4096 steps x 3
+ * doubles), so the device runs the steps back to back; the call waits once
+ * per 4096 steps and returns when every value has landed.  Steps run one
+ * launch sequence each (no multi-step graphs), so states and forces are
+ * those of lbm_step(1) repeated, bit for bit.  F: 3 n doubles on the host;
+ * a body without links gives zeros.
+ * Errors: STATE (no state), INVALID_ARG, OOM, CUDA. */
+lbm_status lbm_step_forces(lbm_handle h, int64_t n, int32_t body, double* F);
 
 /* Copy the state out as FP64 post-collision populations f+_i(x,t), [Q][N]
  * on the host (solid and open-column nodes get 0).  Synchronises.

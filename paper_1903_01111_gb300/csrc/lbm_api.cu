@@ -1251,6 +1251,45 @@ lbm_status lbm_forces(lbm_handle h, int32_t n, double* F) {
   return LBM_OK;
 }
 
+lbm_status lbm_step_forces(lbm_handle h, int64_t n, int32_t body, double* F) {
+  g_msg[0] = 0;
+  NvtxRange range("lbm_step_forces");
+  if (!h || n < 0 || (n > 0 && !F)) return fail(LBM_ERR_INVALID_ARG, "null or negative argument");
+  if (body < 0 || body >= MAX_BODIES) return fail(LBM_ERR_INVALID_ARG, "body %d out of range", body);
+  if (!h->has_state) return fail(LBM_ERR_STATE, "initialise the state first");
+  constexpr int64_t kChunk = 4096;
+  const bool has = body < h->nbody;
+  double* pinned = nullptr;
+  if (n > 0) {
+    lbm_status st = force_host_buffer(h, 3 * (size_t)std::min(n, kChunk), &pinned);
+    if (st != LBM_OK) return st;
+  }
+  for (int64_t k0 = 0; k0 < n; k0 += kChunk) {
+    const int64_t m = std::min(kChunk, n - k0);
+    for (int64_t k = 0; k < m; ++k) {
+      lbm_status st = enqueue_step(h, h->cur, h->step, h->profiling);
+      if (st != LBM_OK) return st;
+      h->cur ^= 1;
+      ++h->step;
+      // this step's slot: the next step clears the other one, the step
+      // after it this one, so the copy (queued before both) reads it whole
+      if (has) {
+        const double* slot = (const double*)h->force.p + 3 * (int64_t)h->nbody * ((h->step - 1) & 1) + 3 * body;
+        CUDA_TRY(cudaMemcpyAsync(pinned + 3 * k, slot, sizeof(double) * 3, cudaMemcpyDeviceToHost, h->stream));
+      }
+      if (h->profiling && h->ev_used > (1u << 16)) {
+        st = harvest_events(h);
+        if (st != LBM_OK) return st;
+      }
+    }
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    for (int64_t k = 0; k < m; ++k)
+      for (int a = 0; a < 3; ++a)
+        F[3 * (k0 + k) + a] = has ? pinned[3 * k + a] + h->force_rest[3 * body + a] : 0.0;
+  }
+  return LBM_OK;
+}
+
 lbm_status lbm_get_distributions(lbm_handle h, double* f) {
   g_msg[0] = 0;
   if (!h || !f) return fail(LBM_ERR_INVALID_ARG, "null argument");

@@ -148,6 +148,7 @@ _sig = {
                          _P(ctypes.c_double), _vp, _vp, _P(ctypes.c_double)],
     "lbm_set_domains": [_H, _vp, ctypes.c_int32],
     "lbm_forces": [_H, ctypes.c_int32, _vp],
+    "lbm_step_forces": [_H, ctypes.c_int64, ctypes.c_int32, _vp],
     "lbm_set_tuning": [_H, _P(lbm_tuning)],
     "lbm_get_tuning": [_H, _P(lbm_tuning)],
     "lbm_autotune": [_H, ctypes.c_int32, _P(lbm_tuning), _P(ctypes.c_double)],
@@ -314,6 +315,14 @@ def lbm_forces(h, n: int) -> np.ndarray:
     return out[:n]
 
 
+def lbm_step_forces(h, n: int, body: int = 0) -> np.ndarray:
+    """n steps, and the force (n, 3) on `body` after each of them (copied
+    behind each step, one synchronisation per 4096 steps)."""
+    out = np.zeros((max(int(n), 1), 3))
+    _check(_lib.lbm_step_forces(h, int(n), int(body), out.ctypes.data))
+    return out[:int(n)]
+
+
 def lbm_set_tuning(h, bulk_shape=-1, link_threads=256, graph_steps=2, link_seq=1, fused=1) -> None:
     t = lbm_tuning(int(bulk_shape), int(link_threads), int(graph_steps), int(link_seq), int(fused))
     _check(_lib.lbm_set_tuning(h, ctypes.byref(t)))
@@ -451,6 +460,10 @@ class Lattice:
 
     def step(self, n=1):
         lbm_step(self.h, n)
+
+    def step_forces(self, n, body=0):
+        """n steps with the force on `body` after each one, (n, 3)."""
+        return lbm_step_forces(self.h, n, body)
 
     def moments(self, rho=None, u=None):
         info = self.info()

@@ -218,6 +218,36 @@ def test_step_chunks_and_profiling_are_bitwise_equal(L, fused):
         np.testing.assert_allclose(F, outs[0][1], rtol=1e-12, atol=1e-18)
 
 
+@pytest.mark.parametrize("fused", [0, 1])
+def test_step_forces_equals_step_and_force_per_step(L, fused):
+    """lbm_step_forces(n) gives the state of n x lbm_step(1) bit for bit and
+    the force lbm_force reports after each of those steps (the force's FP64
+    block sums meet in atomics, whose order may vary: to rounding); a call
+    may end in the middle of a graph-sized run of steps; n = 0 runs nothing;
+    a body without links gives zeros."""
+    geo = G.build(0, (45, 33, 1), (1, 1, 1), [G.ball((20.37, 15.61, 0), 6.3, omega=(0, 0, 0.004))])
+    outs = []
+    for mode in ("loop", "series"):
+        lat = L.Lattice(geo, tau=0.7, g=(2e-5, 1e-5, 0), bc=2)
+        lat.set_tuning(fused=fused, graph_steps=8)
+        lat.init_equilibrium()
+        if mode == "loop":
+            F = []
+            for _ in range(37):
+                lat.step(1)
+                F.append(lat.force(0))
+            F = np.array(F)
+        else:
+            F = np.vstack([lat.step_forces(30), lat.step_forces(0), lat.step_forces(7)])
+        outs.append((lat.distributions(), F))
+        if mode == "series":
+            assert np.array_equal(lat.step_forces(3, body=5), np.zeros((3, 3)))
+        lat.close()
+    assert outs[1][1].shape == (37, 3)
+    assert np.array_equal(outs[1][0], outs[0][0])
+    np.testing.assert_allclose(outs[1][1], outs[0][1], rtol=1e-12, atol=1e-18)
+
+
 @pytest.mark.parametrize("prec", PRECISIONS)
 def test_fused_and_split_steps_agree_on_a_moving_pack(L, prec):
     """The fused step and the link-kernel step on a D3Q19 pack with moving
