@@ -266,7 +266,7 @@ def run_precision(lbm, torch, geo, precision, steps, warmup, dist, peak):
 # grows with the fluid node count, so a full launch moves this figure times
 # its fluid nodes.  k_bulk<D3Q19, F32S, 0, 256, 1>: 575.5 MB per launch for
 # 2.83M fluid nodes; k_fused<D3Q19, F32S, 0, 128>: 713.8 MB.
-TRAFFIC_PER_FLUID_NODE_PACK_FP32 = {"k_bulk": 204.1, "k_fused": 253.0}
+TRAFFIC_PER_FLUID_NODE_PACK_FP32 = {"k_bulk": 204.4, "k_fused": 253.1}
 
 
 def LINK_BYTES(s):
@@ -846,10 +846,12 @@ def run_e2e(lbm, torch, geo, steps):
             "gpu_launches": steps * per_step_launches + 2}
 
 
-def run_oracle(n, steps):
+def run_oracle(n, target_s=15.0, single_target_s=8.0):
     """The FP64 CPU oracle on an n^3 sub-case of the same recipe, on every
     host core (OpenMP over its per-node passes; the result does not depend
-    on the thread count) and on one thread."""
+    on the thread count) and on one thread.  Each run's step count is set
+    from a two-step timing so that it takes about target_s (all cores) or
+    single_target_s (one thread) of CPU time."""
     import oracle as O
 
     geo = geometry(n)
@@ -857,29 +859,34 @@ def run_oracle(n, steps):
                         vibb_density=1)
     nf = geo.fluid_count()
     out = {}
-    for threads in (os.cpu_count() or 1, 1):
+    for threads, target in ((os.cpu_count() or 1, target_s), (1, single_target_s)):
         used = O.set_threads(threads)
         st = O.init(cfg, geo.solid)
         O.run(cfg, geo.solid, geo.links, st, 1)
         t0 = time.perf_counter()
+        O.run(cfg, geo.solid, geo.links, st, 2)
+        per_step = (time.perf_counter() - t0) / 2
+        steps = int(max(2, min(5000, target / max(per_step, 1e-9))))
+        t0 = time.perf_counter()
         O.run(cfg, geo.solid, geo.links, st, steps)
         dt = time.perf_counter() - t0
-        out[threads] = (nf * steps / dt / 1e6, used, dt)
-    v, used, dt = out[os.cpu_count() or 1]
-    v1, _, dt1 = out[1]
+        out[threads] = (nf * steps / dt / 1e6, used, dt, steps)
+    v, used, dt, steps = out[os.cpu_count() or 1]
+    v1, _, dt1, steps1 = out[1]
     return {"value": v, "unit": "MLUPS", "cores": used, "kind": "oracle",
             "sample": f"{n}^3 sub-case of the same sphere-pack recipe ({nf} fluid nodes, {len(geo.links)} links), "
                       f"{steps} steps, FP64 oracle, {used} OpenMP threads (nproc), {dt:.1f} s",
-            "single_thread": {"value": v1, "unit": "MLUPS", "cores": 1, "seconds": dt1}}
+            "single_thread": {"value": v1, "unit": "MLUPS", "cores": 1, "steps": steps1, "seconds": dt1}}
 
 
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    # sample sized so that the whole --steps run stays within about a minute
-    n = int(round((20e6 / (0.4 * max(args.steps, 1))) ** (1 / 3)))
-    n = max(32, min(96, n))
+    # sample sized so that the whole --steps run is about 6e8 fluid-node
+    # updates (some 30 s on 16 cores at the oracle's 20 MLUPS)
+    n = int(round((6e8 / (0.4 * max(args.steps, 1))) ** (1 / 3)))
+    n = max(32, min(160, n))
     import oracle as O
 
     cores = O.set_threads(os.cpu_count() or 1)
@@ -1011,7 +1018,7 @@ def main():
                     run_cylinder(lbm, torch, 100, args.cylinder_steps)]
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cpu = run_oracle(96, 24)
+        cpu = run_oracle(128)
     if rank != 0:
         return 0
     world = dist.get_world_size() if dist is not None else 1
