@@ -341,9 +341,9 @@ lbm_status lbm_query(lbm_handle h, lbm_info* info);
 lbm_status lbm_set_profiling(lbm_handle h, int32_t on);
 lbm_status lbm_kernel_times(lbm_handle h, int64_t launches[3], double ms[3]);
 
-/* For callers that cannot allocate device memory (code inside a CUDA graph
- * capture or on a real-time path, or a framework whose own pool owns all
- * device memory): the momentum-exchange force on `body` of the step that
+/* For callers that cannot allocate device memory (code on a real-time path,
+ * or a framework whose own pool owns all device memory): the
+ * momentum-exchange force on `body` of the step that
  * follows a given state, computed from memory the caller owns.  No
  * counterpart in the paper: it is a packaging of lbm_force for such callers.
  *  cfg      the lattice's configuration (stencil, sizes, periodic axes,
@@ -369,8 +369,7 @@ lbm_status lbm_kernel_times(lbm_handle h, int64_t launches[3], double ms[3]);
  * (1.5 MiB, held by every GPU that loads the library until exit), so
  * n_links is limited to LBM_NOALLOC_MAX_LINKS; larger counts return
  * LBM_ERR_INVALID_ARG.  The first call on a device looks up that array's
- * device address (make it before any stream capture) and keeps it for the
- * process: it assumes the device's primary context is not reset
+ * device address and keeps it for the process: it assumes the device's primary context is not reset
  * (cudaDeviceReset) afterwards.  All calls share the
  * array: calls that overlap on the GPU race; calls ordered on one stream do
  * not, and each call overwrites every entry it reads.  Deterministic: the

@@ -1,9 +1,8 @@
 // lbm_force_noalloc: the momentum-exchange force of one step, for callers
 // that cannot allocate device memory.
 //
-// Some callers may not call cudaMalloc at all: code that runs inside a CUDA
-// graph capture or on a real-time path, or a framework that owns every byte
-// of device memory through its own pool.  lbm_create_lattice allocates the
+// Some callers may not call cudaMalloc at all: code on a real-time path, or
+// a framework that owns every byte of device memory through its own pool.  lbm_create_lattice allocates the
 // whole lattice state, so it is of no use to them.  This entry point needs
 // only memory the caller already owns (populations, mask, links, output).
 // Its one piece of scratch -- one FP64 partial sum per thread block -- lives

@@ -1,6 +1,6 @@
 """lbm_force_noalloc: the momentum-exchange force from caller-owned device
-memory, for callers that cannot allocate device memory (graph-capture or
-real-time code, frameworks whose pool owns all device memory).
+memory, for callers that cannot allocate device memory (real-time code,
+frameworks whose pool owns all device memory).
 
 Checked through the C ABI against the allocating path (lbm_step(1) followed
 by lbm_force on a lattice) on two calls in a row, with the same FP64
