@@ -543,32 +543,45 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
   const int64_t len[3] = {nx, ny, nz};
   for (int a = 0; a < 3; ++a) {
     if (c.periodic[a] || (a == 2 && D == 2)) continue;
-    for (int64_t n = 0; n < N; ++n) {
-      const int64_t x[3] = {n % nx, (n / nx) % ny, n / (nx * ny)};
-      if ((x[a] == 0 || x[a] == len[a] - 1) && !(m[n] & (H_SOLID | H_OPEN)))
-        return fail(LBM_ERR_INVALID_ARG,
-                    "node (%lld,%lld,%lld) on a face of non-periodic axis %d is fluid: add a solid layer",
-                    (long long)x[0], (long long)x[1], (long long)x[2], a);
-    }
+    // the two faces x_a = 0 and x_a = len_a - 1, node by node
+    const int b = a == 0 ? 1 : 0, e = a == 2 ? 1 : 2;  // the other two axes
+    for (int64_t side : {(int64_t)0, len[a] - 1})
+      for (int64_t v = 0; v < len[e]; ++v)
+        for (int64_t u = 0; u < len[b]; ++u) {
+          int64_t x[3];
+          x[a] = side;
+          x[b] = u;
+          x[e] = v;
+          const int64_t n = x[0] + nx * (x[1] + ny * x[2]);
+          if (!(m[n] & (H_SOLID | H_OPEN)))
+            return fail(LBM_ERR_INVALID_ARG,
+                        "node (%lld,%lld,%lld) on a face of non-periodic axis %d is fluid: add a solid layer",
+                        (long long)x[0], (long long)x[1], (long long)x[2], a);
+        }
   }
-  auto coords = [&](int64_t n, int64_t x[3]) {
-    x[0] = n % nx;
-    x[1] = (n / nx) % ny;
-    x[2] = n / (nx * ny);
-  };
-  // neighbour n + s e_d with wrap; -1 if it leaves through a non-periodic face
-  auto neighbour = [&](int64_t n, int d, int s) -> int64_t {
-    int64_t x[3];
-    coords(n, x);
+  // the neighbours n + e_d and n - e_d with wrap (-1 where one leaves through
+  // a non-periodic face): one split of n into coordinates for both
+  auto neighbours = [&](int64_t n, int d, int64_t& plus, int64_t& minus) {
+    const int64_t xy = nx * ny;
+    const int64_t z = n / xy, rem = n - z * xy, y = rem / nx;
+    const int64_t x[3] = {rem - y * nx, y, z};
     const int e[3] = {cx_of(h, d), cy_of(h, d), cz_of(h, d)};
+    int64_t p[3], q[3];
+    bool pout = false, qout = false;
     for (int a = 0; a < 3; ++a) {
-      x[a] += s * e[a];
-      if (x[a] < 0 || x[a] >= len[a]) {
-        if (!c.periodic[a]) return -1;
-        x[a] = (x[a] + len[a]) % len[a];
+      p[a] = x[a] + e[a];
+      q[a] = x[a] - e[a];
+      if (p[a] < 0 || p[a] >= len[a]) {
+        pout |= !c.periodic[a];
+        p[a] = (p[a] + len[a]) % len[a];
+      }
+      if (q[a] < 0 || q[a] >= len[a]) {
+        qout |= !c.periodic[a];
+        q[a] = (q[a] + len[a]) % len[a];
       }
     }
-    return x[0] + nx * (x[1] + ny * x[2]);
+    plus = pout ? -1 : p[0] + nx * (p[1] + ny * p[2]);
+    minus = qout ? -1 : q[0] + nx * (q[1] + ny * q[2]);
   };
   // links: checks, second fluid node, cache flags.  The checks run in
   // parallel; the first failing link is reported.
@@ -584,17 +597,24 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
     if (L.body < -1 || L.body >= MAX_BODIES) return 6;
     for (int a = 0; a < 3; ++a)
       if (!std::isfinite(L.uw[a])) return 7;
-    s = neighbour(L.node, L.dir, 1);
+    neighbours(L.node, L.dir, s, ff);
     if (s < 0 || !(m[s] & H_SOLID)) return 8;
-    ff = neighbour(L.node, L.dir, -1);
     if (ff < 0 || (m[ff] & (H_SOLID | H_OPEN))) ff = L.node;  // no second fluid node: use x_f
     rule = L.bc >= 0 ? L.bc : c.bc;
     return 0;
   };
-  int64_t first_bad = n_links;
+  // moment-cache nodes (x_f, x_ff of VIBB links: fluid) and ghost nodes
+  // (x_s: solid) are disjoint, so one mark per node records both: every
+  // writer stores the same byte (an atomic write, no read-modify-write), and
+  // the class of the node tells which flag the mark stands for.  The marks
+  // are written by the check pass (they matter only if every link passes).
+  raw_vec<uint8_t> mark(N);
+  par_fill(mark, (uint8_t)0);
+  auto nodedir = [&](int64_t k) { return (uint64_t)links[k].node * 32 + (uint64_t)links[k].dir; };
+  int64_t first_bad = n_links, unsorted = 0, first_eq = n_links;
   int nbody = 1, moving_i = 0, min_body = MAX_BODIES, max_body = -1;
-#pragma omp parallel for schedule(static) reduction(min : first_bad, min_body) reduction(max : nbody, max_body) \
-    reduction(| : moving_i)
+#pragma omp parallel for schedule(static) reduction(min : first_bad, min_body, first_eq) \
+    reduction(max : nbody, max_body) reduction(| : moving_i) reduction(+ : unsorted)
   for (int64_t k = 0; k < n_links; ++k) {
     int64_t s = 0, ff = 0;
     int rule = 0;
@@ -610,6 +630,21 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
     lk_s[k] = s;
     lk_ff[k] = ff;
     lk_rule[k] = rule;
+    if (rule == LBM_BC_VIBB) {
+#pragma omp atomic write
+      mark[L.node] = 1;
+#pragma omp atomic write
+      mark[ff] = 1;
+    }
+#pragma omp atomic write
+    mark[s] = 1;
+    // input order: (node, dir) increasing, and equal neighbours (duplicates
+    // when it is)
+    if (k > 0) {
+      const uint64_t a = nodedir(k - 1), b = nodedir(k);
+      unsorted += a < b ? 0 : 1;
+      if (a == b) first_eq = std::min(first_eq, k);
+    }
   }
   if (first_bad < n_links) {
     const int64_t k = first_bad;
@@ -630,28 +665,9 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
     }
   }
   const bool moving = moving_i != 0;
-  // moment-cache nodes (x_f, x_ff of VIBB links: fluid) and ghost nodes
-  // (x_s: solid) are disjoint, so one mark per node records both: every
-  // writer stores the same byte (an atomic write, no read-modify-write), and
-  // the class of the node tells which flag the mark stands for
-  {
-    raw_vec<uint8_t> mark(N);
-    par_fill(mark, (uint8_t)0);
 #pragma omp parallel for schedule(static)
-    for (int64_t k = 0; k < n_links; ++k) {
-      if (lk_rule[k] == LBM_BC_VIBB) {
-#pragma omp atomic write
-        mark[links[k].node] = 1;
-#pragma omp atomic write
-        mark[lk_ff[k]] = 1;
-      }
-#pragma omp atomic write
-      mark[lk_s[k]] = 1;
-    }
-#pragma omp parallel for schedule(static)
-    for (int64_t n = 0; n < N; ++n)
-      if (mark[n]) m[n] |= (m[n] & H_SOLID) ? H_GHOST : H_CACHE;
-  }
+  for (int64_t n = 0; n < N; ++n)
+    if (mark[n]) m[n] |= (m[n] & H_SOLID) ? H_GHOST : H_CACHE;
   // open inlet reads the moments of the first fluid column
   if (c.inlet)
     for (int64_t y = 0; y < ny; ++y)
@@ -674,21 +690,18 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
   raw_vec<int64_t> order(n_links);
 #pragma omp parallel for schedule(static)
   for (int64_t k = 0; k < n_links; ++k) order[k] = k;
-  auto nodedir = [&](int64_t k) { return (uint64_t)links[k].node * 32 + (uint64_t)links[k].dir; };
-  int64_t unsorted = 0;
-#pragma omp parallel for schedule(static) reduction(+ : unsorted)
-  for (int64_t k = 1; k < n_links; ++k) unsorted += nodedir(k - 1) < nodedir(k) ? 0 : 1;
   const bool sorted = unsorted == 0;
+  // sorted input: a duplicate is an equal neighbour (found by the check pass)
+  int64_t first_dup = sorted ? first_eq : n_links;
   if (!sorted) {
     std::vector<std::pair<uint64_t, int64_t>> tmp(n_links);
     for (int64_t k = 0; k < n_links; ++k) tmp[k] = {nodedir(k), k};
     std::sort(tmp.begin(), tmp.end());
     for (int64_t k = 0; k < n_links; ++k) order[k] = tmp[k].second;
-  }
-  int64_t first_dup = n_links;
 #pragma omp parallel for schedule(static) reduction(min : first_dup)
-  for (int64_t k = 1; k < n_links; ++k)
-    if (nodedir(order[k]) == nodedir(order[k - 1])) first_dup = std::min(first_dup, k);
+    for (int64_t k = 1; k < n_links; ++k)
+      if (nodedir(order[k]) == nodedir(order[k - 1])) first_dup = std::min(first_dup, k);
+  }
   if (first_dup < n_links)
     return fail(LBM_ERR_INVALID_ARG, "duplicate link at node %lld direction %d",
                 (long long)(nodedir(order[first_dup]) / 32), (int)(nodedir(order[first_dup]) % 32));
@@ -710,36 +723,54 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
   // neighbour outside a non-periodic face is skipped: only open columns can
   // sit there (faces are solid otherwise).
   int64_t expected = 0, n_fluid = 0;
-#pragma omp parallel for schedule(static) reduction(+ : expected, n_fluid)
-  for (int64_t r = 0; r < rows; ++r) {
-    const int64_t y = r % ny, z = r / ny;
-    int64_t nrow[32];  // first node of the neighbour row of each direction, -1: outside
-    for (int d = 1; d < Q; ++d) {
-      int64_t yy = y + cy_of(h, d), zz = z + cz_of(h, d);
-      bool out = false;
-      if (yy < 0 || yy >= ny) {
-        if (!c.periodic[1]) out = true;
-        yy = (yy + ny) % ny;
-      }
-      if (zz < 0 || zz >= nz) {
-        if (!c.periodic[2]) out = true;
-        zz = (zz + nz) % nz;
-      }
-      nrow[d] = out ? -1 : nx * (yy + ny * zz);
-    }
-    const uint8_t* mr = m.data() + nx * r;
-    for (int64_t x = 0; x < nx; ++x) {
-      if (mr[x] & (H_SOLID | H_OPEN)) continue;
-      ++n_fluid;
-      for (int d = 1; d < Q; ++d) {
-        if (nrow[d] < 0) continue;
-        int64_t xx = x + cx_of(h, d);
-        if (xx < 0 || xx >= nx) {
-          if (!c.periodic[0]) continue;
-          xx = (xx + nx) % nx;
+  {
+    // a row with no solid node stands for a neighbour row outside a
+    // non-periodic face; nodes away from the x ends need no wrap
+    raw_vec<uint8_t> open_row(nx);
+    par_fill(open_row, (uint8_t)0);
+    auto count_row = [&](auto stencil, int64_t r, int64_t& exp, int64_t& nf) {
+      using L = decltype(stencil);
+      const int64_t y = r % ny, z = r / ny;
+      const uint8_t* nrow[L::Q];
+      nrow[0] = nullptr;
+      for (int d = 1; d < L::Q; ++d) {
+        int64_t yy = y + L::cy(d), zz = z + L::cz(d);
+        bool out = false;
+        if (yy < 0 || yy >= ny) {
+          if (!c.periodic[1]) out = true;
+          yy = (yy + ny) % ny;
         }
-        if (m[nrow[d] + xx] & H_SOLID) ++expected;
+        if (zz < 0 || zz >= nz) {
+          if (!c.periodic[2]) out = true;
+          zz = (zz + nz) % nz;
+        }
+        nrow[d] = out ? open_row.data() : m.data() + nx * (yy + ny * zz);
       }
+      const uint8_t* mr = m.data() + nx * r;
+      for (int64_t x = 0; x < nx; ++x) {
+        if (mr[x] & (H_SOLID | H_OPEN)) continue;
+        ++nf;
+        if (x > 0 && x < nx - 1) {
+#pragma unroll
+          for (int d = 1; d < L::Q; ++d) exp += (nrow[d][x + L::cx(d)] & H_SOLID) ? 1 : 0;
+        } else {
+          for (int d = 1; d < L::Q; ++d) {
+            int64_t xx = x + L::cx(d);
+            if (xx < 0 || xx >= nx) {
+              if (!c.periodic[0]) continue;
+              xx = (xx + nx) % nx;
+            }
+            exp += (nrow[d][xx] & H_SOLID) ? 1 : 0;
+          }
+        }
+      }
+    };
+    if (Q == 9) {
+#pragma omp parallel for schedule(static) reduction(+ : expected, n_fluid)
+      for (int64_t r = 0; r < rows; ++r) count_row(D2Q9{}, r, expected, n_fluid);
+    } else {
+#pragma omp parallel for schedule(static) reduction(+ : expected, n_fluid)
+      for (int64_t r = 0; r < rows; ++r) count_row(D3Q19{}, r, expected, n_fluid);
     }
   }
   if (expected != n_links)
@@ -919,26 +950,12 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
         rest[3 * b + 2] += t * cz_of(h, d);
       }
   }
-  // link records in the chosen order
+  // link records: the split form's in `order`, the fused kernel's in
+  // (node, dir) order (`ond`); with one body the two orders are the same and
+  // one pass fills both
   raw_vec<LinkRec> recs(n_links);  // these three: written in full below
   raw_vec<double> qs(n_links);
   raw_vec<double> uws(moving ? (size_t)D * n_links : 0);
-#pragma omp parallel for schedule(static)
-  for (int64_t j = 0; j < n_links; ++j) {
-    const int64_t k = order[j];
-    const lbm_link& L = links[k];
-    recs[j].kf = (uint32_t)sidx[L.node];
-    recs[j].kff = (uint32_t)sidx[lk_ff[k]];
-    recs[j].ks = (uint32_t)sidx[lk_s[k]];
-    recs[j].meta = (uint32_t)L.dir | ((uint32_t)lk_rule[k] << 5) | ((uint32_t)(L.body + 1) << 7);
-    qs[j] = L.q;
-    if (moving)
-      for (int a = 0; a < D; ++a) uws[a * n_links + j] = L.uw[a];
-  }
-
-  // fused-kernel link arrays in (node, dir) order: storage indices of x_f
-  // are non-decreasing along it, so the first link of each 32-node group is
-  // a lower bound
   const int64_t ngroups = (S + 31) / 32;
   raw_vec<int32_t> ffirst((size_t)ngroups + 1);
   raw_vec<uint32_t> fmask((size_t)S);
@@ -946,34 +963,53 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
   raw_vec<FusedRec> frec(n_links);  // written in full below
   raw_vec<double> fq(h->rb == 8 ? n_links : 0);
   raw_vec<double> fuw(moving ? (size_t)D * n_links : 0);
-  auto kf_of = [&](int64_t j) -> int64_t { return sidx[links[ond[j]].node]; };
-#pragma omp parallel for schedule(static)
-  for (int64_t g = 0; g <= ngroups; ++g) {
-    int64_t lo = 0, hi = n_links;  // first j with kf_of(j) >= 32 g
-    while (lo < hi) {
-      const int64_t mid = lo + (hi - lo) / 2;
-      if (kf_of(mid) < 32 * g)
-        lo = mid + 1;
-      else
-        hi = mid;
-    }
-    ffirst[g] = (int32_t)lo;
-  }
+  const bool same_order = ond == order.data();
+  auto split_rec = [&](int64_t j, int64_t k, uint32_t kf, uint32_t kff) {
+    const lbm_link& L = links[k];
+    recs[j].kf = kf;
+    recs[j].kff = kff;
+    recs[j].ks = (uint32_t)sidx[lk_s[k]];
+    recs[j].meta = (uint32_t)L.dir | ((uint32_t)lk_rule[k] << 5) | ((uint32_t)(L.body + 1) << 7);
+    qs[j] = L.q;
+    if (moving)
+      for (int a = 0; a < D; ++a) uws[a * n_links + j] = L.uw[a];
+  };
 #pragma omp parallel for schedule(static)
   for (int64_t j = 0; j < n_links; ++j) {
     const int64_t k = ond[j];
     const lbm_link& L = links[k];
-    const uint32_t kf = (uint32_t)sidx[L.node];
+    const uint32_t kf = (uint32_t)sidx[L.node], kff = (uint32_t)sidx[lk_ff[k]];
 #pragma omp atomic update
     fmask[kf] |= 1u << L.dir;
     const float q32 = (float)L.q;
     uint32_t qbits;
     memcpy(&qbits, &q32, 4);
-    frec[j] = FusedRec{kf, (uint32_t)sidx[lk_ff[k]],
-                       (uint32_t)L.dir | ((uint32_t)lk_rule[k] << 5) | ((uint32_t)(L.body + 1) << 8), qbits};
+    frec[j] = FusedRec{kf, kff, (uint32_t)L.dir | ((uint32_t)lk_rule[k] << 5) | ((uint32_t)(L.body + 1) << 8), qbits};
     if (h->rb == 8) fq[j] = L.q;
     if (moving)
       for (int a = 0; a < D; ++a) fuw[a * n_links + j] = L.uw[a];
+    if (same_order) split_rec(j, k, kf, kff);
+  }
+  if (!same_order) {
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < n_links; ++j) {
+      const int64_t k = order[j];
+      split_rec(j, k, (uint32_t)sidx[links[k].node], (uint32_t)sidx[lk_ff[k]]);
+    }
+  }
+  // first link of each 32-node group: storage indices of x_f are
+  // non-decreasing along (node, dir) order, so ffirst[g] (the first j with
+  // kf_j >= 32 g) is j for every g in (kf_{j-1} / 32, kf_j / 32], and n_links
+  // after the last link's group
+#pragma omp parallel for schedule(static)
+  for (int64_t j = 0; j < n_links; ++j) {
+    const int64_t g = frec[j].kf >> 5, gp = j > 0 ? (int64_t)(frec[j - 1].kf >> 5) : -1;
+    for (int64_t t = gp + 1; t <= g; ++t) ffirst[t] = (int32_t)j;
+  }
+  {
+    const int64_t glast = n_links > 0 ? (int64_t)(frec[n_links - 1].kf >> 5) : -1;
+#pragma omp parallel for schedule(static)
+    for (int64_t t = glast + 1; t <= ngroups; ++t) ffirst[t] = (int32_t)n_links;
   }
 
   // ---- device

@@ -273,6 +273,27 @@ def test_fused_and_split_steps_agree_on_a_moving_pack(L, prec):
     assert np.abs(out[1][1] - out[0][1]).max() <= (1e-12 if prec == "fp64" else 1e-5) * scale
 
 
+@pytest.mark.parametrize("fused", [0, 1])
+def test_link_input_order_does_not_change_the_result(L, fused):
+    """lbm_set_geometry puts the links in its own order: the same links given
+    in a shuffled order, with two bodies (so the link kernel's body-sorted
+    order differs from the fused kernel's node order), give the same
+    populations bit for bit and the same per-body forces (to the order of
+    their FP64 block sums)."""
+    import copy
+
+    geo = G.sphere_pack(24, porosity=0.5, rmin=2.5, rmax=4.5, seed=3)
+    links = geo.links.copy()
+    links["body"] = np.random.default_rng(2).integers(0, 2, len(links))
+    geo.links = links
+    shuffled = copy.copy(geo)
+    shuffled.links = links[np.random.default_rng(1).permutation(len(links))]
+    out = [_run_gpu(L, g, 25, L.LBM_FP64, nbody=2, fused=fused, tau=0.7, g=(1e-5, 0, 0), bc=2)[:2]
+           for g in (geo, shuffled)]
+    assert np.array_equal(out[0][0], out[1][0])
+    np.testing.assert_allclose(out[1][1], out[0][1], rtol=1e-12, atol=1e-15)
+
+
 def test_moments_device_pointers(L):
     import torch
 
