@@ -231,7 +231,9 @@ def run_precision(lbm, torch, geo, precision, steps, warmup, dist, peak):
     link_bytes = nl * LINK_BYTES(s)
     fused_bytes = bulk_bytes + nl * FUSED_LINK_BYTES(s) + info.n_cached * 4 * s
     main_bytes = fused_bytes if fused else bulk_bytes
-    name = "k_fused" if fused else "k_bulk"
+    # FP64 one-node bulk shapes run over the fluid-node list (k_bulk_list)
+    one_node = tuning.as_dict()["bulk_nodes_per_thread"] == 1 and tuning.as_dict()["bulk_sequential_nodes"] == 1
+    name = "k_fused" if fused else ("k_bulk_list" if s == 8 and one_node else "k_bulk")
     traffic = TRAFFIC_PER_FLUID_NODE_PACK_FP32.get(name) if s == 4 else None
     kernels = {name: {"launches": n_launch[2], "avg_ms": main_ms, "share": kms[2] / max(sum(kms), 1e-30),
                       "gbs": main_bytes / (main_ms * 1e-3) / 1e9, "bytes_per_launch": main_bytes}}

@@ -123,6 +123,8 @@ struct Layout {
   const DomPar* dom;           // [ndom] when ndom > 1, else null
   const int32_t* row_dom;      // [ny*nz] domain of each row when ndom > 1
   int32_t ndom;
+  const uint32_t* fluid;       // [nfluid] storage indices of the fluid nodes (FP64 lattices), else null
+  int64_t nfluid;
 };
 
 __device__ __forceinline__ Relax relax_params(const Params& p) {
@@ -517,6 +519,38 @@ __global__ void __launch_bounds__(BT, (bulk_blocks_per_sm<L, P, BT, NPT>())) k_b
     collide_store<L, P>(f[j], p, rx, folded_of<MULTI>(p, lay, dom[j]), fout, S, k[j], mom, (w[j] & W_CACHE) != 0,
                         fl);
   }
+}
+
+// FP64 bulk pass over the fluid nodes alone, one thread per entry of the
+// layout's fluid list, otherwise as k_bulk.  An FP64 warp instruction holds
+// the FP64 pipe for the same time whatever its active lanes, so the ghost
+// and open slots that k_bulk's warps carry (23 % of a porous pack's storage)
+// cost as much as fluid nodes there; this pass has no such lanes.  It leaves
+// the ghost and open slots of the output unwritten: a ghost slot is read
+// only in its link's direction after the link kernel of the next step has
+// written it, and the open-column kernel rewrites the open slots before they
+// are pulled.
+template <class L, class P, bool MULTI, int BT>
+__global__ void __launch_bounds__(BT, (bulk_blocks_per_sm<L, P, BT, 1>())) k_bulk_list(
+    const typename P::T* __restrict__ fin, typename P::T* __restrict__ fout, Layout lay,
+    Mom4<typename P::T>* __restrict__ mom, double* __restrict__ force_next, Params p) {
+  using T = typename P::T;
+  if (force_next && blockIdx.x == 0)
+    for (int t = threadIdx.x; t < 3 * p.nbody; t += BT) force_next[t] = 0.0;
+  const int64_t t = (int64_t)blockIdx.x * BT + threadIdx.x;
+  if (t >= lay.nfluid) return;
+  const size_t S = (size_t)lay.S;
+  const uint32_t k = __ldg(lay.fluid + t);
+  const uint32_t w = __ldg(lay.word + k);
+  const RunRec run = lay.runs[w & W_RUN];
+  int d[L::Q];
+  pull_offsets<L>(k, run, lay, p, d);
+  T f[L::Q];
+  const T* __restrict__ fk = fin + k;
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) f[i] = __ldg(fk + ((ptrdiff_t)i * (ptrdiff_t)S + d[i]));
+  const Relax rx = MULTI ? relax_domain(lay.dom, run.dom) : relax_params(p);
+  collide_store<L, P>(f, p, rx, folded_of<MULTI>(p, lay, run.dom), fout, S, k, mom, (w & W_CACHE) != 0);
 }
 
 // Resident blocks per SM of the sequential walk (it keeps the next node's
@@ -1284,6 +1318,13 @@ struct Launch {
   template <bool M, int BT, int NPT>
   static void bulk_shape(const void* fin, void* fout, const Layout& lay, void* mom, double* force_next,
                          const Params& p, cudaStream_t s) {
+    if constexpr (!P::shifted && NPT == 1) {
+      if (lay.fluid) {
+        k_bulk_list<L, P, M, BT><<<blocks_for(lay.nfluid > 0 ? lay.nfluid : 1, BT), BT, 0, s>>>(
+            (const T*)fin, (T*)fout, lay, (Mom4<T>*)mom, force_next, p);
+        return;
+      }
+    }
     k_bulk<L, P, M, BT, NPT><<<blocks_for((lay.S + NPT - 1) / NPT, BT), BT, 0, s>>>((const T*)fin, (T*)fout, lay,
                                                                                    (Mom4<T>*)mom, force_next, p);
   }

@@ -130,6 +130,7 @@ struct lbm_lattice_s {
   DeviceBuf recs, q, uw;
   // links of the fused step kernel, in (node, dir) order (FusedLinks)
   DeviceBuf lfirst, lmask, lrec, lqd, luw;
+  DeviceBuf fidx;  // FP64: storage indices of the fluid nodes (the bulk pass's thread map)
   int64_t n_links = 0, n_fluid = 0, n_cached = 0, n_runs = 0;
   DeviceBuf force;  // [2][nbody][3]
   // shifted storage: sum over each body's links of 2 w_i' rho0 e_i' (FP64),
@@ -163,7 +164,7 @@ int64_t device_bytes(const lbm_handle h) {
   const DeviceBuf* all[] = {&h->f[0],     &h->f[1],     &h->mom[0],   &h->mom[1], &h->word,  &h->node_of,
                             &h->runs,     &h->row_first, &h->row_last, &h->row_in1, &h->row_out1, &h->recs,
                             &h->q,        &h->uw,       &h->lfirst, &h->lmask, &h->lrec,
-                            &h->lqd,      &h->luw,      &h->force,    &h->dom,    &h->row_dom};
+                            &h->lqd,      &h->luw,      &h->force,    &h->dom,    &h->row_dom, &h->fidx};
   int64_t s = 0;
   for (auto* b : all) s += (int64_t)b->bytes;
   return s;
@@ -207,7 +208,7 @@ void release_geometry(lbm_handle h) {
   DeviceBuf* all[] = {&h->f[0],     &h->f[1],      &h->mom[0],   &h->mom[1], &h->word,  &h->node_of,
                       &h->runs,     &h->row_first, &h->row_last, &h->row_in1, &h->row_out1, &h->recs,
                       &h->q,        &h->uw,        &h->lfirst, &h->lmask, &h->lrec,
-                      &h->lqd,      &h->luw,       &h->dom,      &h->row_dom};
+                      &h->lqd,      &h->luw,       &h->dom,      &h->row_dom, &h->fidx};
   for (auto* b : all) release(*b);
   h->lay = Layout{};
 }
@@ -924,6 +925,28 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
     else
       n_cached += (m[n] & H_CACHE) ? 1 : 0;
   }
+  // FP64: the fluid nodes' storage indices in order (the FP64 bulk pass
+  // maps its threads onto these; per-chunk counts, prefix sums, fill)
+  raw_vec<uint32_t> flist(h->rb == 8 ? (size_t)S : 0);
+  int64_t nflist = 0;
+  if (h->rb == 8 && S > 0) {
+    const int64_t nch = std::max<int64_t>(1, std::min<int64_t>(1024, S / 65536));
+    std::vector<int64_t> cs(nch + 1, 0);
+#pragma omp parallel for schedule(static)
+    for (int64_t ch = 0; ch < nch; ++ch) {
+      int64_t cnt = 0;
+      for (int64_t k = S * ch / nch; k < S * (ch + 1) / nch; ++k) cnt += (word[k] & (W_GHOST | W_OPEN)) ? 0 : 1;
+      cs[ch + 1] = cnt;
+    }
+    for (int64_t ch = 0; ch < nch; ++ch) cs[ch + 1] += cs[ch];
+    nflist = cs[nch];
+#pragma omp parallel for schedule(static)
+    for (int64_t ch = 0; ch < nch; ++ch) {
+      int64_t j = cs[ch];
+      for (int64_t k = S * ch / nch; k < S * (ch + 1) / nch; ++k)
+        if (!(word[k] & (W_GHOST | W_OPEN))) flist[j++] = (uint32_t)k;
+    }
+  }
   // rest part of the momentum exchange per body (shifted storage):
   // sum over the body's links of 2 w_i' rho0 e_i', from the exact count of
   // its links per direction (counted in parallel, summed in a fixed order)
@@ -1033,6 +1056,7 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
   if (st == LBM_OK && n_links > 0) st = upload(h->lmask, fmask.data(), sizeof(uint32_t) * S);
   if (st == LBM_OK) st = upload(h->lrec, frec.data(), sizeof(FusedRec) * n_links);
   if (st == LBM_OK) st = upload(h->lqd, fq.data(), sizeof(double) * fq.size());
+  if (st == LBM_OK && nflist > 0) st = upload(h->fidx, flist.data(), sizeof(uint32_t) * nflist);
   if (st == LBM_OK && ndom > 0) {
     std::vector<DomPar> dp(ndom);
     for (int k = 0; k < ndom; ++k) {
@@ -1100,6 +1124,8 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
   h->lay.dom = ndom > 0 ? (const DomPar*)h->dom.p : nullptr;
   h->lay.row_dom = ndom > 0 ? (const int32_t*)h->row_dom.p : nullptr;
   h->lay.ndom = std::max(ndom, 1);
+  h->lay.fluid = nflist > 0 ? (const uint32_t*)h->fidx.p : nullptr;
+  h->lay.nfluid = nflist;
   // a single domain runs through Params like an unsplit lattice
   Params& p = h->p;
   const lbm_domain one{0, 0, 0, 0, c.tau, {c.g[0], c.g[1], c.g[2]}, c.inlet_umax, c.inlet_y0, c.inlet_y1};
