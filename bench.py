@@ -227,7 +227,9 @@ def run_precision(lbm, torch, geo, precision, steps, warmup, dist, peak):
     fused = bool(tuning.fused) and nl > 0
     main_ms = kms[2] / max(n_launch[2], 1)
     link_ms = kms[0] / max(n_launch[0], 1)
-    bulk_bytes = nf * (2 * Q3 * s + 1)  # algorithmic bytes per bulk launch
+    # algorithmic bytes per bulk launch: pulls, stores and word per fluid
+    # node, and the moment-cache write of every cached node (step A4)
+    bulk_bytes = nf * (2 * Q3 * s + 1) + info.n_cached * 4 * s
     link_bytes = nl * LINK_BYTES(s)
     fused_bytes = bulk_bytes + nl * FUSED_LINK_BYTES(s) + info.n_cached * 4 * s
     main_bytes = fused_bytes if fused else bulk_bytes
@@ -488,7 +490,7 @@ def run_batch(lbm, torch, peak, n_domains=256, seed=0, steps=2000, warmup=10, ad
     fused = bool(tuning.fused) and info.n_links > 0
     main_name = "k_fused" if fused else "k_bulk"
     main_ms = kms[2] / max(nlaunch[2], 1)
-    main_bytes = nf * (2 * 9 * s + 1)
+    main_bytes = nf * (2 * 9 * s + 1) + info.n_cached * 4 * s
     if fused:
         main_bytes += info.n_links * FUSED_LINK_BYTES(s) + info.n_cached * 4 * s
     mlups32 = sharded_mlups(dist, torch, nf, steps - warmup, ms32)
