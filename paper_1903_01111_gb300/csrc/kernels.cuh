@@ -16,7 +16,11 @@
 // fluid node; ghost slots are filled by the link kernel before the bulk
 // kernel pulls them.
 //
-// Step t -> t+1 (three launches on one stream):
+// Step t -> t+1, on one stream, in one of two forms.  Fused (the default on
+// lattices with cut links): k_fused stages each block's pulls in shared
+// memory, evaluates the block's link rules into the staged slots and
+// collides (after k_open where there are open columns).  Split (the
+// adjoint's recompute, and wherever the autotuner finds it faster):
 //   k_links: per cut link (x_f, i'), the missing f_i(x_f, t+1), i = opp(i'),
 //            from f+ and the moment cache at x_f and x_ff (Sec. 3 and 3.1),
 //            written to the ghost slot f[i][k_s] (read only by x_f);
@@ -27,7 +31,8 @@
 //            buffer; rho, u(t+1) into the moment cache where flagged.  Ghost
 //            and open slots of the output get zeros (through the same store
 //            instructions as the fluid slots) so that every written sector
-//            is complete.
+//            is complete.  FP64 one-node shapes run k_bulk_list instead, over
+//            the fluid nodes alone.
 #pragma once
 #include <cuda_runtime.h>
 
