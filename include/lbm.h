@@ -247,7 +247,9 @@ lbm_status lbm_step(lbm_handle h, int64_t n);
  * sums): rho = sum_i f+_i, u = (sum_i f+_i e_i - g/2)/rho, which equals the
  * velocity the last collision used.  rho: N doubles, u: D x N doubles
  * ([component][node]); both host or both device pointers (detected); solid
- * and open-column nodes get 0.  Host outputs synchronise the stream.
+ * and open-column nodes get 0.  Host outputs synchronise the stream (their
+ * pages are first written in parallel on the host cores, while the device
+ * computes, so that a fresh allocation's page faults do not serialise the copy).
  * Errors: STATE, INVALID_ARG, OOM, CUDA. */
 lbm_status lbm_moments(lbm_handle h, double* rho, double* u);
 
