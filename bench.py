@@ -1054,7 +1054,8 @@ def main():
     if r64 is not None:
         line["fp64"] = {"value": r64["mlups"], "unit": "MLUPS", "ms_per_step": r64["ms_per_step"],
                         "roofline": r64["roofline"], "kernels": r64["kernels"],
-                        "step_gbs": r64["step_gbs"], "gpu_launches": r64["launches"], "clocks": r64["clocks"]}
+                        "step_gbs": r64["step_gbs"], "gpu_launches": r64["launches"], "tuning": r64["tuning"],
+                        "clocks": r64["clocks"]}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -472,23 +472,25 @@ def _sampled_step_check(L, lat, geo, sample, tau, g, bc, vibb_density, shifted):
     return err.max(), tol
 
 
-@pytest.mark.parametrize("arm", ["fp64", "fp32s_bench"])
+@pytest.mark.parametrize("arm", ["fp64", "fp64_split", "fp32s_bench"])
 def test_full_size_sphere_pack_sampled_nodes(L, arm):
     """The 384^3 workload: after three steps from rest, f+(t+1) at sampled
     fluid nodes (150 with links, 50 anywhere) equals the oracle's pull + link
     rules + collision computed node by node from the gathered f+(t).  The
     fp32s arm is the bench's configuration: FP32 shifted storage, VIBB with
-    rho_d = rho_f for q > 1/2, the autotuner's launch shapes (one node per
-    thread in 256-thread blocks, 128-thread link blocks with 4 links per
-    thread)."""
+    rho_d = rho_f for q > 1/2, the fused step in 128-thread blocks; the
+    fp64_split arm the split form the autotuner picks in FP64 (link kernel,
+    then the bulk pass over the fluid-node list)."""
     geo = G.sphere_pack(384, seed=0)
     tau, g = 0.7, (1e-6, 0.0, 0.0)
-    if arm == "fp64":
+    if arm in ("fp64", "fp64_split"):
         lat = L.Lattice(geo, tau=tau, g=g, bc=2)
+        if arm == "fp64_split":
+            lat.set_tuning(bulk_shape=1, link_threads=128, link_seq=1, graph_steps=8, fused=0)
         vd, shifted = 0, False
     else:
         lat = L.Lattice(geo, precision=L.LBM_FP32_SHIFTED, tau=tau, g=g, bc=2, vibb_density=L.LBM_VIBB_RHO_LOCAL)
-        lat.set_tuning(bulk_shape=0, link_threads=128, link_seq=4, graph_steps=8, fused=1)
+        lat.set_tuning(bulk_shape=1, link_threads=128, link_seq=4, graph_steps=8, fused=1)
         vd, shifted = 1, True
     lat.init_equilibrium()
     lat.step(3)  # non-uniform state near the walls
