@@ -670,10 +670,13 @@ __device__ __forceinline__ typename P::T link_value(int rule, typename P::T q, t
                                                     typename P::T fpff, typename P::T fpi, const Mom4<typename P::T>& mf,
                                                     const Mom4<typename P::T>& mff, typename P::T uw0,
                                                     typename P::T uw1, typename P::T uw2, typename P::T rho0,
-                                                    int local_rho) {
+                                                    int local_rho, bool moving = true) {
   using T = typename P::T;
-  // 6 w_i' rho0 (e_i . u_w) with e_i = -e_i'
-  const T wall = -(T)6 * w * rho0 * (ex * uw0 + ey * uw1 + ez * uw2);
+  // 6 w_i' rho0 (e_i . u_w) with e_i = -e_i'.  FP64 skips it when no wall
+  // of the lattice moves (the same for every link of a launch: five FP64
+  // instructions of about a hundred per link); FP32 forms it always (the
+  // branch moved registers of the fused kernel into spills and cost 2 %)
+  const T wall = (P::shifted || moving) ? -(T)6 * w * rho0 * (ex * uw0 + ey * uw1 + ez * uw2) : (T)0;
   const T two_q = (T)2 * q;
   if (rule == 0) return fpf + wall;
   if (rule == 1) {
@@ -753,7 +756,7 @@ __device__ __forceinline__ typename P::T eval_link(const DirTable<typename P::T,
                                                    const Mom4<typename P::T>* __restrict__ mom, size_t N, int ip,
                                                    int rule, typename P::T q, uint32_t node, uint32_t ff,
                                                    typename P::T uw0, typename P::T uw1, typename P::T uw2,
-                                                   const Params& p, typename P::T& fpf) {
+                                                   const Params& p, typename P::T& fpf, bool moving) {
   using T = typename P::T;
   const int i = tab.opp[ip];
   const T ex = tab.e[ip][0], ey = tab.e[ip][1], ez = tab.e[ip][2];
@@ -775,7 +778,7 @@ __device__ __forceinline__ typename P::T eval_link(const DirTable<typename P::T,
     fpi = f[(size_t)i * N + node];
   }
   return link_value<P>(rule, q, w, ex, ey, ez, fpf, fpff, fpi, mf, mff, uw0, uw1, uw2, par<T>(p.rho0, p.rho0_f),
-                       p.vibb_local_rho);
+                       p.vibb_local_rho, moving);
 }
 
 // One thread per link.  recs: storage indices and metadata; qv: q in
@@ -838,7 +841,8 @@ __global__ void __launch_bounds__(256) k_links(typename P::T* __restrict__ f, co
         if (L::D == 3) uw2 = uwv[2 * nl + k];
       }
       T fpf;
-      const T val = eval_link<L, P>(tab, f, mom, N, ip, rule, q, rec.kf, rec.kff, uw0, uw1, uw2, p, fpf);
+      const T val = eval_link<L, P>(tab, f, mom, N, ip, rule, q, rec.kf, rec.kff, uw0, uw1, uw2, p, fpf,
+                                    uwv != nullptr);
       f[(size_t)tab.opp[ip] * N + rec.ks] = val;
       if (body >= 0) {
         // momentum exchange (f+_i'(x_f,t) + f_i(x_f,t+1)) e_i'.  In shifted
@@ -1017,7 +1021,8 @@ __global__ void __launch_bounds__(BT, (fused_blocks_per_sm<L, P, BT>())) k_fused
       if (L::D == 3) uw2 = fl.uw[2 * fl.nl + li];
     }
     T fpf;
-    const T val = eval_link<L, P>(tab, fin, mom_in, S, ip, rule, q, r.kf, r.kff, uw0, uw1, uw2, p, fpf);
+    const T val = eval_link<L, P>(tab, fin, mom_in, S, ip, rule, q, r.kf, r.kff, uw0, uw1, uw2, p, fpf,
+                                  fl.uw != nullptr);
     const uint32_t o = r.kf - base;  // the node's place in the block
     stage[o >> 5][tab.opp[ip]][o & 31] = val;
     if (body >= 0) {
