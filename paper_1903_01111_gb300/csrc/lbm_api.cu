@@ -764,7 +764,6 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
         if (mr[x] & (H_SOLID | H_OPEN)) continue;
         ++nf;
         if (x > 0 && x < nx - 1) {
-#pragma unroll
           for (int d = 1; d < L::Q; ++d) exp += (nrow[d][x + L::cx(d)] & H_SOLID) ? 1 : 0;
         } else {
           for (int d = 1; d < L::Q; ++d) {
