@@ -781,6 +781,42 @@ __device__ __forceinline__ typename P::T eval_link(const DirTable<typename P::T,
                        p.vibb_local_rho, moving);
 }
 
+// VIBB (Sec. 3.1) with the velocity interpolation weights of the link given:
+// u_d = cf u_f + cff u_ff + cw u_w, where (cf, cff, cw) are the 1/3 : 2/3
+// blend of u*_d and u**_d and depend on q alone (the FP64 link kernel takes
+// them from a per-link array the host fills, instead of forming them from
+// 1/q and 1/(1+q) per link and step).  Otherwise as link_value's VIBB branch.
+template <class L, class P>
+__device__ __forceinline__ typename P::T vibb_weighted(const DirTable<typename P::T, L::Q>& tab,
+                                                       const typename P::T* __restrict__ f,
+                                                       const Mom4<typename P::T>* __restrict__ mom, size_t N, int ip,
+                                                       typename P::T q, uint32_t node, uint32_t ff, typename P::T uw0,
+                                                       typename P::T uw1, typename P::T uw2, const Params& p,
+                                                       typename P::T& fpf, bool moving, typename P::T cf,
+                                                       typename P::T cff, typename P::T cw) {
+  using T = typename P::T;
+  const T ex = tab.e[ip][0], ey = tab.e[ip][1], ez = tab.e[ip][2];
+  const T w = tab.w[ip];
+  fpf = f[(size_t)ip * N + node];
+  const T fpff = f[(size_t)ip * N + ff];
+  const Mom4<T> mf = mom[node], mff = mom[ff];
+  const T rho0 = par<T>(p.rho0, p.rho0_f);
+  const T wall = (P::shifted || moving) ? -(T)6 * w * rho0 * (ex * uw0 + ey * uw1 + ez * uw2) : (T)0;
+  const T two_q = (T)2 * q;
+  const T rhof = P::shifted ? rho0 + mf.r : mf.r;
+  const T rhoff = P::shifted ? rho0 + mff.r : mff.r;
+  const T rd = (p.vibb_local_rho && q > (T)0.5) ? mf.r : two_q * mf.r + ((T)1 - two_q) * mff.r;
+  const T rhod = P::shifted ? rho0 + rd : rd;
+  const T neq_f = fpf - eq_dir<P>(w, ex, ey, ez, mf.r, rhof, mf.ux, mf.uy, mf.uz);
+  const T neq_ff = fpff - eq_dir<P>(w, ex, ey, ez, mff.r, rhoff, mff.ux, mff.uy, mff.uz);
+  // fneq at d, each term rescaled by its density ratio
+  const T nd = rhod * (two_q * neq_f * rhoff + ((T)1 - two_q) * neq_ff * rhof) / (rhof * rhoff);
+  const T udx = cf * mf.ux + cff * mff.ux + cw * uw0;
+  const T udy = cf * mf.uy + cff * mff.uy + cw * uw1;
+  const T udz = cf * mf.uz + cff * mff.uz + cw * uw2;
+  return eq_dir<P>(w, ex, ey, ez, rd, rhod, udx, udy, udz) + nd + wall;
+}
+
 // One thread per link.  recs: storage indices and metadata; qv: q in
 // storage precision; uw: [D][nl] wall velocities or null.  force: the step's
 // accumulator slot [MAX_BODIES][3] (FP64).
@@ -796,7 +832,8 @@ __device__ __forceinline__ typename P::T eval_link(const DirTable<typename P::T,
 template <class L, class P, int SEQ>
 __global__ void __launch_bounds__(256) k_links(typename P::T* __restrict__ f, const Mom4<typename P::T>* __restrict__ mom,
                                                const LinkRec* __restrict__ recs, const typename P::T* __restrict__ qv,
-                                               const typename P::T* __restrict__ uwv, int64_t nl,
+                                               const typename P::T* __restrict__ uwv,
+                                               const typename P::T* __restrict__ qcv, int64_t nl,
                                                double* __restrict__ force, Params p, int64_t S_) {
   using T = typename P::T;
   __shared__ DirTable<T, L::Q> tab;
@@ -840,9 +877,13 @@ __global__ void __launch_bounds__(256) k_links(typename P::T* __restrict__ f, co
         uw1 = uwv[nl + k];
         if (L::D == 3) uw2 = uwv[2 * nl + k];
       }
-      T fpf;
-      const T val = eval_link<L, P>(tab, f, mom, N, ip, rule, q, rec.kf, rec.kff, uw0, uw1, uw2, p, fpf,
-                                    uwv != nullptr);
+      T fpf, val;
+      if (qcv && rule == 2)
+        val = vibb_weighted<L, P>(tab, f, mom, N, ip, q, rec.kf, rec.kff, uw0, uw1, uw2, p, fpf, uwv != nullptr,
+                                  qcv[k], qcv[nl + k], qcv[2 * nl + k]);
+      else
+        val = eval_link<L, P>(tab, f, mom, N, ip, rule, q, rec.kf, rec.kff, uw0, uw1, uw2, p, fpf,
+                              uwv != nullptr);
       f[(size_t)tab.opp[ip] * N + rec.ks] = val;
       if (body >= 0) {
         // momentum exchange (f+_i'(x_f,t) + f_i(x_f,t+1)) e_i'.  In shifted
@@ -1302,8 +1343,8 @@ struct KernelOps {
   // 256); seq: links per thread of the link kernel (1 or 4)
   void (*bulk)(const void* fin, void* fout, const Layout& lay, void* mom, double* force_next, const Params& p,
                int shape, cudaStream_t s);
-  void (*links)(void* f, const void* mom, const LinkRec* recs, const void* q, const void* uw, int64_t nl,
-                double* force, const Params& p, int64_t S, int threads, int seq, cudaStream_t s);
+  void (*links)(void* f, const void* mom, const LinkRec* recs, const void* q, const void* uw, const void* qc,
+                int64_t nl, double* force, const Params& p, int64_t S, int threads, int seq, cudaStream_t s);
   // fused step (threads per block 128, 256 or 512; 512 runs as 256 for
   // FP64 D3Q19, whose link buffer would not fit the static shared memory)
   void (*fused)(const void* fin, void* fout, const Layout& lay, const FusedRaw& fl, const void* mom_in,
@@ -1372,16 +1413,16 @@ struct Launch {
     else
       bulk_m<false>(fin, fout, lay, mom, force_next, p, shape, s);
   }
-  static void links(void* f, const void* mom, const LinkRec* recs, const void* q, const void* uw, int64_t nl,
-                    double* force, const Params& p, int64_t S, int threads, int seq, cudaStream_t s) {
+  static void links(void* f, const void* mom, const LinkRec* recs, const void* q, const void* uw, const void* qc,
+                    int64_t nl, double* force, const Params& p, int64_t S, int threads, int seq, cudaStream_t s) {
     if (nl == 0) return;
     const int bt = (threads == 64 || threads == 128) ? threads : 256;
     if (seq == 4)
       k_links<L, P, 4><<<blocks_for(nl, 4 * bt), bt, 0, s>>>((T*)f, (const Mom4<T>*)mom, recs, (const T*)q,
-                                                             (const T*)uw, nl, force, p, S);
+                                                             (const T*)uw, (const T*)qc, nl, force, p, S);
     else
       k_links<L, P, 1><<<blocks_for(nl, bt), bt, 0, s>>>((T*)f, (const Mom4<T>*)mom, recs, (const T*)q,
-                                                         (const T*)uw, nl, force, p, S);
+                                                         (const T*)uw, (const T*)qc, nl, force, p, S);
   }
   template <bool M, int BT>
   static void fused_shape(const void* fin, void* fout, const Layout& lay, const FusedRaw& r, const void* mom_in,

@@ -131,6 +131,7 @@ struct lbm_lattice_s {
   // links of the fused step kernel, in (node, dir) order (FusedLinks)
   DeviceBuf lfirst, lmask, lrec, lqd, luw;
   DeviceBuf fidx;  // FP64: storage indices of the fluid nodes (the bulk pass's thread map)
+  DeviceBuf lqc;   // FP64: per-link VIBB velocity weights [3][n_links] in the link kernel's order
   int64_t n_links = 0, n_fluid = 0, n_cached = 0, n_runs = 0;
   DeviceBuf force;  // [2][nbody][3]
   // shifted storage: sum over each body's links of 2 w_i' rho0 e_i' (FP64),
@@ -164,7 +165,7 @@ int64_t device_bytes(const lbm_handle h) {
   const DeviceBuf* all[] = {&h->f[0],     &h->f[1],     &h->mom[0],   &h->mom[1], &h->word,  &h->node_of,
                             &h->runs,     &h->row_first, &h->row_last, &h->row_in1, &h->row_out1, &h->recs,
                             &h->q,        &h->uw,       &h->lfirst, &h->lmask, &h->lrec,
-                            &h->lqd,      &h->luw,      &h->force,    &h->dom,    &h->row_dom, &h->fidx};
+                            &h->lqd,      &h->luw,      &h->force,    &h->dom,    &h->row_dom, &h->fidx, &h->lqc};
   int64_t s = 0;
   for (auto* b : all) s += (int64_t)b->bytes;
   return s;
@@ -220,7 +221,7 @@ void release_geometry(lbm_handle h) {
   DeviceBuf* all[] = {&h->f[0],     &h->f[1],      &h->mom[0],   &h->mom[1], &h->word,  &h->node_of,
                       &h->runs,     &h->row_first, &h->row_last, &h->row_in1, &h->row_out1, &h->recs,
                       &h->q,        &h->uw,        &h->lfirst, &h->lmask, &h->lrec,
-                      &h->lqd,      &h->luw,       &h->dom,      &h->row_dom, &h->fidx};
+                      &h->lqd,      &h->luw,       &h->dom,      &h->row_dom, &h->fidx, &h->lqc};
   for (auto* b : all) release(*b);
   h->lay = Layout{};
 }
@@ -283,7 +284,7 @@ lbm_status enqueue_step_buf(lbm_handle h, void* fc, void* fn, void* mc, void* mn
   lbm_status st;
   if (!fused) {
     st = timed_launch(0, [&] {
-      h->ops.links(fc, mc, (const LinkRec*)h->recs.p, h->q.p, h->uw.p, h->n_links, slot, h->p, h->lay.S,
+      h->ops.links(fc, mc, (const LinkRec*)h->recs.p, h->q.p, h->uw.p, h->lqc.p, h->n_links, slot, h->p, h->lay.S,
                    h->tune.link_threads, h->tune.link_seq, h->stream);
     });
     if (st != LBM_OK) return st;
@@ -1031,6 +1032,33 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
       split_rec(j, k, (uint32_t)sidx[links[k].node], (uint32_t)sidx[lk_ff[k]]);
     }
   }
+  // FP64: the VIBB velocity weights of each link in the link kernel's order
+  // (u*_d's and u**_d's weights of Sec. 3.1 blended 1/3 : 2/3; q alone
+  // fixes them)
+  raw_vec<double> qcw(h->rb == 8 ? 3 * (size_t)n_links : 0);
+  if (h->rb == 8) {
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < n_links; ++j) {
+      const double q = links[order[j]].q, two_q = 2.0 * q;
+      double af, aff, aw;
+      if (q <= 0.5) {
+        af = two_q;
+        aff = 1.0 - two_q;
+        aw = 0.0;
+      } else {
+        const double iq = 1.0 / q;
+        af = (1.0 - q) * iq;
+        aff = 0.0;
+        aw = (two_q - 1.0) * iq;
+      }
+      const double i1q = 1.0 / (1.0 + q);
+      const double bff = (1.0 - q) * i1q, bw = two_q * i1q;
+      const double third = 1.0 / 3.0, two_thirds = 2.0 / 3.0;
+      qcw[j] = third * af;
+      qcw[n_links + j] = third * aff + two_thirds * bff;
+      qcw[2 * n_links + j] = third * aw + two_thirds * bw;
+    }
+  }
   // first link of each 32-node group: storage indices of x_f are
   // non-decreasing along (node, dir) order, so ffirst[g] (the first j with
   // kf_j >= 32 g) is j for every g in (kf_{j-1} / 32, kf_j / 32], and n_links
@@ -1068,6 +1096,7 @@ lbm_status lbm_set_geometry(lbm_handle h, const uint8_t* solid, const lbm_link* 
   if (st == LBM_OK) st = upload(h->lrec, frec.data(), sizeof(FusedRec) * n_links);
   if (st == LBM_OK) st = upload(h->lqd, fq.data(), sizeof(double) * fq.size());
   if (st == LBM_OK && nflist > 0) st = upload(h->fidx, flist.data(), sizeof(uint32_t) * nflist);
+  if (st == LBM_OK && h->rb == 8 && n_links > 0) st = upload(h->lqc, qcw.data(), sizeof(double) * 3 * n_links);
   if (st == LBM_OK && ndom > 0) {
     std::vector<DomPar> dp(ndom);
     for (int k = 0; k < ndom; ++k) {
@@ -1587,7 +1616,7 @@ lbm_status lbm_adjoint_step(lbm_handle h, int32_t body, const double dJ_dF[3], i
         // cache holds the moments the recompute's last step wrote for it,
         // those its forward step used (a one-state segment: the refresh of
         // the recompute)
-        h->ops.links(state, am, (const LinkRec*)h->recs.p, h->q.p, h->uw.p, nl, fslot, h->p, S,
+        h->ops.links(state, am, (const LinkRec*)h->recs.p, h->q.p, h->uw.p, h->lqc.p, nl, fslot, h->p, S,
                      h->tune.link_threads, h->tune.link_seq, h->stream);
         if (open) h->ops.open(state, am, h->lay, h->p, h->stream);
       }
