@@ -878,12 +878,20 @@ __global__ void __launch_bounds__(256) k_links(typename P::T* __restrict__ f, co
         if (L::D == 3) uw2 = uwv[2 * nl + k];
       }
       T fpf, val;
-      if (qcv && rule == 2)
-        val = vibb_weighted<L, P>(tab, f, mom, N, ip, q, rec.kf, rec.kff, uw0, uw1, uw2, p, fpf, uwv != nullptr,
-                                  qcv[k], qcv[nl + k], qcv[2 * nl + k]);
-      else
+      // FP64 VIBB links take their velocity weights from qcv; the FP32 kernel
+      // keeps the one evaluation path (its rounding of the rule is what the
+      // FP32 adjoint's accuracy was measured with)
+      if constexpr (!P::shifted) {
+        if (qcv && rule == 2)
+          val = vibb_weighted<L, P>(tab, f, mom, N, ip, q, rec.kf, rec.kff, uw0, uw1, uw2, p, fpf, uwv != nullptr,
+                                    qcv[k], qcv[nl + k], qcv[2 * nl + k]);
+        else
+          val = eval_link<L, P>(tab, f, mom, N, ip, rule, q, rec.kf, rec.kff, uw0, uw1, uw2, p, fpf,
+                                uwv != nullptr);
+      } else {
         val = eval_link<L, P>(tab, f, mom, N, ip, rule, q, rec.kf, rec.kff, uw0, uw1, uw2, p, fpf,
                               uwv != nullptr);
+      }
       f[(size_t)tab.opp[ip] * N + rec.ks] = val;
       if (body >= 0) {
         // momentum exchange (f+_i'(x_f,t) + f_i(x_f,t+1)) e_i'.  In shifted
