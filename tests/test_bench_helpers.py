@@ -60,3 +60,17 @@ def test_darcy_permeability_normalisation():
     u[0, :4] = 2e-4
     k = bench.darcy_permeability(Geo(), u, 0.1, 1e-6)
     assert abs(k - 0.1 * 1e-4 / 1e-6) < 1e-9
+
+
+def test_oracle_baseline_is_timed_on_all_cores_and_on_one():
+    """run_oracle (the bench's cpu_baseline): the FP64 oracle on a cube of the
+    workload's recipe, every host core and then one thread, each run's step
+    count set from a two-step timing; the entry carries the contract's keys."""
+    import os
+
+    out = bench.run_oracle(16, target_s=0.05, single_target_s=0.05)
+    assert out["kind"] == "oracle" and out["unit"] == "MLUPS"
+    assert out["value"] > 0 and out["cores"] == (os.cpu_count() or 1)
+    assert out["single_thread"]["cores"] == 1 and out["single_thread"]["value"] > 0
+    assert out["single_thread"]["steps"] >= 2
+    assert "16^3 sub-case" in out["sample"] and "OpenMP threads" in out["sample"]
