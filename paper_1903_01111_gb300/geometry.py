@@ -168,6 +168,18 @@ def _mask_from_bodies(stencil, shape, periodic, bodies):
 def _links(stencil, shape, periodic, bodies, mask, open_x):
     nx, ny, nz = shape
     per = np.asarray(periodic, np.int32)
+    # The wall crossing of a link is searched on each ball's nearest periodic
+    # image as seen from x_f; the node classes use the nearest image as seen
+    # from each node.  The two agree for x_f and its neighbours when every
+    # point within one lattice step of the ball lies within half a period of
+    # its centre: radius below half the period minus one on each periodic
+    # axis.  A larger ball would leave a solid neighbour without a crossing.
+    for b in bodies[(bodies["kind"] == BALL) | (bodies["kind"] == CAVITY)]:
+        for a in range(3 if stencil == D3Q19 else 2):
+            if periodic[a] and not (b["r"] < shape[a] / 2.0 - 1.0):
+                raise ValueError(f"ball of radius {float(b['r']):g} at {tuple(float(v) for v in b['c'])}: on the "
+                                 f"periodic axis {a} (period {shape[a]}) the radius must be below "
+                                 f"{shape[a] / 2.0 - 1.0:g}, half the period minus one")
     # cavities are handled by the C builder as balls with the entry root
     # replaced by the exit root; do that here in Python: split the work.
     lib = _load()
@@ -182,6 +194,8 @@ def _links(stencil, shape, periodic, bodies, mask, open_x):
         out = np.zeros(n, LINK_DTYPE)
         n2 = lib.geom_links(stencil, nx, ny, nz, per.ctypes.data, rest.ctypes.data, int(rest.size),
                             mask.ctypes.data, int(open_x[0]), int(open_x[1]), out.ctypes.data, ctypes.byref(err))
+        if n2 < 0:  # the filling pass's crossing search failed
+            raise ValueError(_link_error(n2, err.value, shape))
         assert n2 == n
         return out
     return _links_python(stencil, shape, periodic, bodies, mask, open_x)

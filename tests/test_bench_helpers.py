@@ -68,9 +68,9 @@ def test_oracle_baseline_is_timed_on_all_cores_and_on_one():
     count set from a two-step timing; the entry carries the contract's keys."""
     import os
 
-    out = bench.run_oracle(16, target_s=0.05, single_target_s=0.05)
+    out = bench.run_oracle(32, target_s=0.05, single_target_s=0.05)
     assert out["kind"] == "oracle" and out["unit"] == "MLUPS"
     assert out["value"] > 0 and out["cores"] == (os.cpu_count() or 1)
     assert out["single_thread"]["cores"] == 1 and out["single_thread"]["value"] > 0
     assert out["single_thread"]["steps"] >= 2
-    assert "16^3 sub-case" in out["sample"] and "OpenMP threads" in out["sample"]
+    assert "32^3 sub-case" in out["sample"] and "OpenMP threads" in out["sample"]

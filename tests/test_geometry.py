@@ -127,3 +127,22 @@ def test_open_channel_has_no_links_on_open_columns():
 def test_nonperiodic_face_without_solid_layer_is_rejected():
     with pytest.raises(ValueError):
         G.build(0, (8, 6, 1), (1, 0, 1), [])
+
+
+def test_ball_wider_than_half_a_period_is_rejected():
+    """On a periodic axis the link builder sees each ball through its nearest
+    image from x_f; a ball whose radius reaches half the period minus one
+    could leave a solid neighbour without a wall crossing, so it is rejected
+    with the limit in the message (a sphere-pack cube smaller than its
+    largest sphere allows, here 16^3 for radii up to 14, is the usual way to
+    meet it); just below the limit the build succeeds."""
+    with pytest.raises(ValueError, match="half the period minus one"):
+        G.sphere_pack(16, porosity=0.40, rmin=6.0, rmax=14.0, seed=0)
+    with pytest.raises(ValueError, match="half the period minus one"):
+        G.build(0, (20, 30, 1), (1, 1, 1), [G.ball((10.3, 15.2, 0), 9.0)])
+    g = G.build(0, (20, 30, 1), (1, 1, 1), [G.ball((10.3, 15.2, 0), 8.9)])
+    assert len(g.links) > 0
+    # a non-periodic axis imposes no such limit
+    walls = [G.halfspace((0, -1), -0.5), G.halfspace((0, 1), 18.5)]  # solid at y <= 0.5 and y >= 18.5
+    g = G.build(0, (40, 20, 1), (1, 0, 1), [G.ball((20.3, 10.2, 0), 8.0)] + walls)
+    assert len(g.links) > 0
