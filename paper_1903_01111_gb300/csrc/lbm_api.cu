@@ -1402,7 +1402,7 @@ lbm_status lbm_get_distributions(lbm_handle h, double* f) {
   const int64_t N = h->N;
   double* tmp = nullptr;
   CUDA_TRY(cudaMalloc(&tmp, sizeof(double) * N));
-  touch_host_output(f, sizeof(double) * h->Q * N);
+  if (!is_device_pointer(f)) touch_host_output(f, sizeof(double) * h->Q * N);
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < h->Q && e == cudaSuccess; ++i) {
     e = cudaMemsetAsync(tmp, 0, sizeof(double) * N, h->stream);
